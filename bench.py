@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Event-simulation throughput on GB300: pixel-frames/s at 1080p, adaptive vs
+exhaustive weighted local regression, with the roofline of the dominant kernel.
+
+One step = one frame through the whole hot path (ingest and log brightness,
+Proposition-1 test with compaction, regression of flagged pixels, event
+emission and the ordered event writer).  Inputs are seeded synthetic frames
+(moving textured rectangles, 1 spp-equivalent Gamma noise) generated on the
+device before timing; each step reads a distinct ~83 MB frame of a 240-frame
+sequence (about 20 GB), so no step's input is cache-resident.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank simulates its own independent sequence (no
+collectives on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "event-sim pixel-frames/s and % HBM roofline at 1080p (adaptive vs exhaustive WLR)"
+UNIT = "pixel-frames/s"
+
+WORKLOADS = {
+    "rects1080p": dict(scene="rects1080p", r=7, T=5, C=0.1, rgb=True,
+                       desc="1920x1080 RGB, 240 frames, 1 spp Gamma noise, 15x15x5 window, C=0.1"),
+    "rects720p": dict(scene="rects720p", r=7, T=5, C=0.15, rgb=True,
+                      desc="1280x720 RGB, 120 frames, 4 spp Gamma noise, 15x15x5 window, C=0.15"),
+}
+
+# Algorithmic FP32 work of the regression (counted from the method, see DESIGN):
+# per (pixel, neighbour) pair: 7 scaled feature differences (14), squared
+# distance (18), exp (1), w*z and w*y (10), Gram update 55 entries (100),
+# right-hand side 10 entries (19) -> 162 flop; per regressed pixel, the ridge,
+# equilibration and 10x10 Cholesky solve -> 700 flop.
+FLOP_PER_NEIGHBOUR = 162
+FLOP_PER_SOLVE = 700
+FP32_LANES_PER_SM = 128
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the regression
+# kernel from one ncu capture, valid only while wlr.cu is unchanged (the
+# capture's workload and scaling are recorded under profiles/).
+NCU_TRAFFIC = {}   # {sha256(wlr.cu)[:16]: bytes per launch at the bench workload}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    rank = int(os.environ.get("RANK", "0"))
+    return rank, ws, dist if ws > 1 else None
+
+
+def _gen_frames(scene, n, device):
+    frames = []
+    for t in range(n):
+        f = scene.frame(t, device)
+        frames.append({k: f[k] for k in ("radiance", "normal", "albedo", "depth")})
+    return frames
+
+
+def _timed_run(sim, frames, W, K, stream):
+    """W untimed warm-up steps, then exactly K timed steps (frame index wraps
+    with a reset to frame 0).  Returns (ms, profile, events) where the profile
+    carries the regression work counted inside the timed region."""
+    import torch
+    F = len(frames)
+    acc = {"nb": 0, "reg": 0}
+    base = {"nb": 0, "reg": 0}
+
+    def step(s, timed):
+        idx = s % F
+        if idx == 0 and s > 0:
+            if timed:
+                p = sim.profile()
+                acc["nb"] += p["neighbours"] - base["nb"]
+                acc["reg"] += p["regressions"] - base["reg"]
+                base["nb"] = base["reg"] = 0
+            sim.reset()
+        sim.push(frames[idx])
+
+    for s in range(W):
+        step(s, False)
+    sim.events()
+    torch.cuda.synchronize()
+    p0 = sim.profile()
+    base["nb"], base["reg"] = p0["neighbours"], p0["regressions"]
+    sim.profile(True)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for s in range(W, W + K):
+        step(s, True)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    prof = sim.profile()
+    prof["neighbours_timed"] = acc["nb"] + prof["neighbours"] - base["nb"]
+    prof["regressions_timed"] = acc["reg"] + prof["regressions"] - base["reg"]
+    n_ev = len(sim.events())
+    return ms, prof, n_ev
+
+
+def _cpu_baseline(frames_cpu, wl, budget_s=12.0, rows=None):
+    """The FP64 oracle, as it stands, on a band of rows of the same workload."""
+    import oracle
+    from oracle import ADAPTIVE, Oracle, OracleConfig
+    H, Wd = frames_cpu[0]["depth"].shape
+    r0, r1 = rows or (H // 2 - 8, H // 2 + 8)
+    orc = Oracle(OracleConfig(Wd, H, radius=wl["r"], frames=wl["T"], channels=3 if wl["rgb"] else 1,
+                              mode=ADAPTIVE, contrast=wl["C"]))
+    t0 = time.perf_counter()
+    n = 0
+    for fr in frames_cpu:
+        orc.push(fr, (r0, r1))
+        n += 1
+        if time.perf_counter() - t0 > budget_s and n >= 3:
+            break
+    dt = time.perf_counter() - t0
+    px = (r1 - r0) * Wd
+    return {"value": px * n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"rows {r0}-{r1 - 1} ({px} px) of the {Wd}x{H} workload, frames 0-{n - 1}, "
+                      f"adaptive, FP64 C oracle with OpenMP", "seconds": round(dt, 2)}
+
+
+def run_ours(args):
+    import torch
+    from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, ESIM_AD_EXHAUSTIVE, SimConfig, Simulator
+    from scenes import Scene, preset
+
+    rank, ws, dist = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    scfg = preset(wl["scene"], seq=rank, seed=rank)
+    scene = Scene(scfg)
+    Wd, H = scfg.width, scfg.height
+    N = Wd * H
+    F = scfg.frames
+    n_gen = min(F, args.warmup + args.steps)
+    frames = _gen_frames(scene, n_gen, dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def make(mode):
+        return Simulator(SimConfig(width=Wd, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
+                                   mode=mode, rgb=wl["rgb"], event_capacity=1 << 26), stream)
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_index = vis.split(",")[local] if vis else str(local)
+    with ClockSampler(gpu_index) as clk:
+        sim_a = make(ESIM_AD_ADAPTIVE)
+        if dist:
+            dist.barrier()
+        ms_a, prof_a, ev_a = _timed_run(sim_a, frames, args.warmup, args.steps, stream)
+        stats_a = sim_a.stats()
+        sim_a.close()
+        sim_e = make(ESIM_AD_EXHAUSTIVE)
+        if dist:
+            dist.barrier()
+        ms_e, prof_e, ev_e = _timed_run(sim_e, frames, args.warmup, args.steps, stream)
+        sim_e.close()
+    clocks = clk.summary()
+
+    if dist:
+        t = torch.tensor([ms_a, ms_e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_a, ms_e = float(t[0]), float(t[1])
+    K = args.steps
+    value = ws * N * K / (ms_a * 1e-3)
+    value_e = ws * N * K / (ms_e * 1e-3)
+
+    peaks, peak_src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
+
+    def wlr_roof(prof):
+        n_launch = prof["launches"]["wlr_emit"]
+        wlr_ms = prof["ms"]["wlr_emit"]
+        return n_launch, wlr_ms
+
+    # neighbour and regression counts of the timed region only
+    n_launch, wlr_ms = wlr_roof(prof_a)
+    flops = prof_a["neighbours_timed"] * FLOP_PER_NEIGHBOUR + prof_a["regressions_timed"] * FLOP_PER_SOLVE \
+        if "neighbours_timed" in prof_a else None
+    src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2303_02608_gb300", "csrc", "wlr.cu"),
+                                   "rb").read()).hexdigest()[:16]
+    roof = {"kernel": "wlr_kernel (regression + emission, adaptive queue)", "bound": "alu",
+            "unit": "TFLOP/s", "peak": round(fp32_peak, 2),
+            "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                           f"(max SM clock, {peak_src} peaks file)",
+            "traffic": NCU_TRAFFIC.get(src_hash)}
+    if flops is not None and wlr_ms > 0:
+        per_launch_flops = flops / n_launch
+        per_launch_s = wlr_ms * 1e-3 / n_launch
+        roof["achieved"] = round(per_launch_flops / per_launch_s / 1e12, 3)
+        roof["frac"] = round(roof["achieved"] / fp32_peak, 4)
+        roof["flops_per_launch"] = per_launch_flops
+        roof["launch_ms"] = round(wlr_ms / n_launch, 4)
+        if roof["traffic"] is not None:
+            roof["traffic_per_launch_bytes"] = roof["traffic"]
+
+    # path-level HBM accounting (adaptive): fused minimum bytes per pixel-frame
+    phi = prof_a["regressions_timed"] / (N * K) if "regressions_timed" in prof_a else None
+    bytes_pf = 40 + 32 + 64 + 1 + 4 + 4 + 4          # inputs, ring write, model read, flag, count, 2 reads
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    path_bytes = bytes_pf * N * K + (phi or 0) * N * K * (4 + 64) + ev_a * 12
+    hbm_path = {"bytes_per_pixel_frame_min": bytes_pf, "achieved_gbs": round(path_bytes / (ms_a * 1e-3) / 1e9, 1),
+                "peak_gbs": hbm_gbs, "frac": round(path_bytes / (ms_a * 1e-3) / 1e9 / hbm_gbs, 4)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms_a / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "mode": "adaptive",
+                   "width": Wd, "height": H, "radius": wl["r"], "T": wl["T"], "C": wl["C"],
+                   "spp": scfg.spp, "sequence_frames": F,
+                   "l2": "inputs larger than L2: each step reads a distinct 83 MB frame; ring 330 MB"},
+        "exhaustive": {"value": round(value_e, 1), "unit": UNIT, "ms_per_step": round(ms_e / K, 4),
+                       "speedup_adaptive": round(value / value_e, 3),
+                       "wlr_launch_ms": round(prof_e["ms"]["wlr_emit"] / max(1, prof_e["launches"]["wlr_emit"]), 4)},
+        "flagged_fraction": round(phi, 4) if phi is not None else None,
+        "events_per_step": round(ev_a / K, 1),
+        "kernel_ms_per_step": {k: round(v / K, 4) for k, v in prof_a["ms"].items()},
+        "roofline": roof,
+        "hbm_path": hbm_path,
+        "gpu_launches": int(prof_a["launches"]["ingest_test"] + prof_a["launches"]["wlr_emit"]
+                            + 2 * prof_a["launches"]["event_write"]),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = _e2e(args, scene, wl, N, stream)
+    if rank == 0 and not args.no_cpu_baseline:
+        nb = min(len(frames), 16)
+        frames_cpu = [{k: v.cpu() for k, v in f.items()} for f in frames[:nb]]
+        line["cpu_baseline"] = _cpu_baseline(frames_cpu, wl)
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _e2e(args, scene, wl, N, stream):
+    """Same metric through the public API with pinned host buffers: every step
+    copies its frame in (inside esim_ad_push_frame) and drains its events to
+    the host (esim_ad_events)."""
+    import torch
+    from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, SimConfig, Simulator
+    W = args.warmup
+    K = min(args.steps, args.e2e_steps)
+    n = min(scene.cfg.frames, W + K)
+    host = []
+    for t in range(n):
+        f = scene.frame(t, "cuda")
+        host.append({k: f[k].cpu().pin_memory() for k in ("radiance", "normal", "albedo", "depth")})
+    Wd, H = scene.cfg.width, scene.cfg.height
+    sim = Simulator(SimConfig(width=Wd, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
+                              mode=ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=1 << 24), stream)
+    for s in range(W):
+        sim.push(host[s % n])
+        sim.events()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for s in range(W, W + K):
+        idx = s % n
+        if idx == 0:
+            sim.reset()
+        sim.push(host[idx])
+        d2h += len(sim.events()) * 12 + 64
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    h2d = sum(v.numel() * 4 for v in host[0].values())
+    return {"value": round(N * K / dt, 1), "unit": UNIT, "steps": K, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": int(d2h / K), "ms_per_step": round(dt * 1e3 / K, 3)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: FP64 CPU, on host cores, each step one
+    frame of a band of rows of the same workload."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from oracle import ADAPTIVE, Oracle, OracleConfig
+    from scenes import Scene, preset
+    wl = WORKLOADS[args.workload]
+    scfg = preset(wl["scene"])
+    scene = Scene(scfg)
+    Wd, H = scfg.width, scfg.height
+    r0, r1 = H // 2 - 4, H // 2 + 4
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    orc = Oracle(OracleConfig(Wd, H, radius=wl["r"], frames=wl["T"], channels=3 if wl["rgb"] else 1,
+                              mode=ADAPTIVE, contrast=wl["C"]))
+    F = scfg.frames
+    total = 0.0
+    s_all = args.warmup + args.steps
+    for s in range(s_all):
+        idx = s % F
+        if idx == 0 and s > 0:
+            orc = Oracle(orc.cfg)
+        f = scene.frame(idx, dev)
+        fr = {k: f[k].cpu() for k in ("radiance", "normal", "albedo", "depth")}
+        t0 = time.perf_counter()
+        orc.push(fr, (r0, r1))
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            total += dt
+    px = (r1 - r0) * Wd
+    value = px * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "mode": "adaptive"},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"each step: rows {r0}-{r1 - 1} ({px} px) of one frame, in sequence order"},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=237)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rects1080p")
+    ap.add_argument("--e2e-steps", type=int, default=61)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * esim_ad.h - C ABI of the GB300 (sm_103a) event-camera simulator with adaptive
+ * weighted-local-regression denoising (Tsuji, Yatagawa, Kubo, Morishima,
+ * "Event-based Camera Simulation using Monte Carlo Path Tracing with Adaptive
+ * Denoising", arXiv 2303.02608).
+ *
+ * The library turns noisy path-traced frames (radiance plus first-bounce
+ * normal, depth and albedo buffers, Section 3) into DVS events (Eq. 1).  Per
+ * pixel and frame it
+ *   1. converts radiance to log brightness y = ln(Y + eps) (Section 1.1, 2.1),
+ *   2. tests, with the model kept from the pixel's last event, whether the
+ *      brightness change can reach C: Delta R = (beta^T (x^c - xhat^c))^2 >= C^2
+ *      (Proposition 1, Eqs. 6-9),
+ *   3. for flagged pixels only, solves the first-order weighted local
+ *      regression of Eqs. 3-5 over a (2r+1)^2 x T spatio-temporal window,
+ *   4. emits floor(|alpha - L_last| / C) events of polarity sign(alpha - L_last)
+ *      at the frame time (Eq. 1, Section 3 footnote) and, after an event,
+ *      replaces the pixel's model (Fig. 1, Section 3).
+ * In exhaustive mode step 2 is skipped and every pixel is regressed every
+ * frame (the WLR+ESIM baseline of Section 3).
+ *
+ * Conventions for every entry point:
+ *   - All functions return esim_ad_status; output pointers are left untouched
+ *     on error.  No function throws, aborts or prints.
+ *   - Work is enqueued on the CUDA stream given to esim_ad_init and runs
+ *     asynchronously; only the functions documented as synchronising wait for
+ *     it.  Errors raised by asynchronous device work surface at the next
+ *     synchronising call.
+ *   - ESIM_AD_EOVERFLOW (device event buffer overflowed) and ESIM_AD_ETIMEOUT
+ *     (a bounded device wait expired) are sticky: every later call except
+ *     esim_ad_stats, esim_ad_reset and esim_ad_destroy returns ESIM_AD_ESTATE.
+ *   - Planar image buffers are [channel][height][width], row-major, densely
+ *     packed (row pitch = width elements).
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef ESIM_AD_H
+#define ESIM_AD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct esim_ad_ctx esim_ad_ctx;   /* opaque, owned by the library */
+
+typedef enum esim_ad_status {
+    ESIM_AD_OK = 0,
+    ESIM_AD_EINVAL = -1,      /* bad argument or configuration                 */
+    ESIM_AD_ENOMEM = -2,      /* device or host allocation failed              */
+    ESIM_AD_ECUDA = -3,       /* a CUDA runtime/driver call failed             */
+    ESIM_AD_EOVERFLOW = -4,   /* device event buffer overflowed (sticky)       */
+    ESIM_AD_ETIMEOUT = -5,    /* a bounded device wait expired (sticky)        */
+    ESIM_AD_ESTATE = -6,      /* context unusable after a sticky error         */
+    ESIM_AD_ENOSPACE = -7     /* caller's buffer too small; *n_out = required  */
+} esim_ad_status;
+
+enum { ESIM_AD_ADAPTIVE = 0, ESIM_AD_EXHAUSTIVE = 1 };
+enum { ESIM_AD_LUMA_F32 = 0, ESIM_AD_RGB_F32 = 1 };
+
+/*
+ * Simulation parameters.  Paper symbols: C (Eq. 1), h and b_j (Eq. 5), the
+ * window Omega_c (Eq. 4, Fig. 1).  Choices the paper leaves open are fixed as:
+ *   - image-coordinate regressors are the pixel offset divided by radius, with
+ *     coordinate bandwidth 1 (h still applies);
+ *   - the window spans frames t-T+1..t (truncated at the sequence start) and is
+ *     clipped at the image border;
+ *   - the regression adds ridge * W * |beta|^2 to the unnormalised objective
+ *     (ridge on the slopes only, so Proposition 1 stays an identity);
+ *   - kernel w(u) = exp(-u^2/2).
+ * The paper's experiments use h = 1 and b_j = 1 (Section 3, bandwidth
+ * optimisation).
+ */
+typedef struct esim_ad_config {
+    uint32_t struct_size;    /* = sizeof(esim_ad_config); ABI versioning        */
+    int32_t  width;          /* W >= 1                                          */
+    int32_t  height;         /* H >= 1                                          */
+    int32_t  radius;         /* r in [1, 15]: (2r+1)^2 spatial window           */
+    int32_t  frames;         /* T in [1, 16]: temporal window                   */
+    int32_t  mode;           /* ESIM_AD_ADAPTIVE | ESIM_AD_EXHAUSTIVE           */
+    int32_t  radiance_fmt;   /* ESIM_AD_LUMA_F32 (1 plane) | ESIM_AD_RGB_F32 (3) */
+    int32_t  reserved0;
+    float    contrast;       /* C > 0                                           */
+    float    h;              /* global bandwidth h > 0                          */
+    float    bandwidth[7];   /* b_j > 0: normal x,y,z, depth, albedo r,g,b      */
+    float    log_eps;        /* eps >= 0 in y = ln(Y + eps)                     */
+    float    ridge;          /* lambda > 0                                      */
+    uint64_t event_capacity; /* device event buffer size in events, >= 1        */
+} esim_ad_config;
+
+/*
+ * One input frame: the renderer's noisy radiance and first-bounce features.
+ * Pointers are device memory, or host memory when on_host != 0 (the library
+ * then copies them in on its stream; host memory should be pinned for the copy
+ * to be asynchronous).  The caller keeps ownership; buffers are read in stream
+ * order and may be reused once later work on the same stream has been
+ * enqueued and completed.
+ */
+typedef struct esim_ad_frame {
+    const float* radiance;   /* [1 or 3][H][W] float32 (radiance_fmt)           */
+    const float* variance;   /* [H][W] sample variance, may be NULL (unused by
+                                the method; carried for callers' bookkeeping)  */
+    const float* normal;     /* [3][H][W]                                       */
+    const float* albedo;     /* [3][H][W]                                       */
+    const float* depth;      /* [H][W]                                          */
+    int32_t      on_host;    /* 0: device pointers, 1: host pointers            */
+    int32_t      reserved0;
+} esim_ad_frame;
+
+/* One DVS event e = (q_k, t_l, p_k) of Eq. 1; 12 bytes. */
+typedef struct esim_ad_event {
+    uint32_t frame;          /* frame index t (fixed-interval timestamps)       */
+    uint16_t x, y;           /* pixel q_k                                       */
+    int8_t   polarity;       /* p_k in {-1, +1}                                 */
+    uint8_t  pad[3];
+} esim_ad_event;
+
+typedef struct esim_ad_stats {
+    uint64_t frames;         /* frames pushed since init/reset                  */
+    uint64_t regressions;    /* pixels regressed (all frames); exhaustive: W*H*frames */
+    uint64_t events;         /* events emitted since init/reset                 */
+    uint64_t pixels;         /* W*H                                             */
+} esim_ad_stats;
+
+/*
+ * Create a simulator context bound to `cuda_stream` (a cudaStream_t; NULL =
+ * legacy default stream) on the current CUDA device.  Allocates the frame
+ * ring, per-pixel model state, work queues and the event buffer in device
+ * memory (owned by the context).  Returns EINVAL for a NULL or malformed
+ * config (struct_size mismatch, out-of-range sizes or parameters), ENOMEM on
+ * allocation failure, ECUDA if no usable device.  *out is set only on success.
+ */
+esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_ad_ctx** out);
+
+/*
+ * Push the next frame (index t = frames pushed so far) and enqueue the hot
+ * path for it on the context's stream: ingest to log brightness, the
+ * Proposition-1 test with stream compaction of flagged pixels (adaptive mode,
+ * t >= 1), the weighted local regression of flagged pixels (every pixel at
+ * t = 0 and in exhaustive mode), and event emission with the last-event update
+ * (Eq. 1).  Frame 0 only initialises L_last and the models and emits no events.
+ * Does not synchronise unless frame->on_host (then it waits for its own
+ * host-to-device copies only).  EINVAL on NULL/missing planes, ESTATE after a
+ * sticky error, ECUDA if a launch fails.
+ */
+esim_ad_status esim_ad_push_frame(esim_ad_ctx* ctx, const esim_ad_frame* frame);
+
+/*
+ * Drain the events emitted since the last drain into `dst` (device memory if
+ * dst_is_device, else host), in canonical order: frame, then row y, then
+ * column x, repeated events of a pixel adjacent.  Synchronises the stream.
+ * *n_out receives the number of events.  If cap is smaller than that number,
+ * nothing is drained, *n_out holds the required count and ENOSPACE is
+ * returned.  If the device buffer (event_capacity) overflowed since the last
+ * drain, events were lost: returns EOVERFLOW (sticky) with *n_out = the
+ * number of events that were produced.  dst may be NULL when cap == 0 (query).
+ */
+esim_ad_status esim_ad_events(esim_ad_ctx* ctx, esim_ad_event* dst, uint64_t cap,
+                              uint64_t* n_out, int dst_is_device);
+
+/*
+ * Copy the last frame's per-pixel results: alpha = f(x^c) of Eq. 4 (denoised
+ * log brightness, [H][W] float32; pixels not regressed in that frame keep the
+ * value of their last regression) and flags ([H][W] uint8, 1 where the
+ * regression ran in that frame).  Either pointer may be NULL.  Device or host
+ * destination per dst_is_device.  Synchronises the stream.
+ */
+esim_ad_status esim_ad_denoised(esim_ad_ctx* ctx, float* alpha, uint8_t* flags, int dst_is_device);
+
+/*
+ * Read (get) or overwrite (set) the per-pixel model kept since each pixel's
+ * last event (Fig. 1): l_last [H*W] = brightness reference L(t - Delta t) of
+ * Eq. 1, beta [H*W][7] = feature slopes of Eq. 3 (normal xyz, depth, albedo
+ * rgb), xc [H*W][7] = the centre feature x^c at the last event.  Host
+ * pointers; any may be NULL to skip.  Both synchronise the stream.  Used for
+ * checkpoint/resume and for lock-step comparison against a reference.
+ */
+esim_ad_status esim_ad_get_state(esim_ad_ctx* ctx, float* l_last, float* beta, float* xc);
+esim_ad_status esim_ad_set_state(esim_ad_ctx* ctx, const float* l_last, const float* beta,
+                                 const float* xc);
+
+/*
+ * Kernel timing for tracing and roofline accounting (no paper counterpart:
+ * instrumentation).  While enabled, every kernel launch of esim_ad_push_frame
+ * is bracketed by CUDA events on the context's stream.  Classes: 0 = ingest +
+ * Proposition-1 test, 1 = weighted local regression + emission, 2 = ordered
+ * event writer.  `neighbours` counts (pixel, window neighbour) pairs
+ * accumulated by the regression since init/reset, the unit of its arithmetic.
+ * esim_ad_profile_enable(ctx, 1) clears the timings; esim_ad_profile_get
+ * synchronises and returns totals since then.
+ */
+typedef struct esim_ad_profile {
+    uint64_t launches[3];    /* launches per kernel class                        */
+    double   ms[3];          /* summed device time per class, milliseconds       */
+    uint64_t neighbours;     /* (pixel, neighbour) pairs regressed since init     */
+    uint64_t regressions;    /* pixels regressed since init/reset                */
+} esim_ad_profile;
+
+esim_ad_status esim_ad_profile_enable(esim_ad_ctx* ctx, int on);
+esim_ad_status esim_ad_profile_get(esim_ad_ctx* ctx, esim_ad_profile* out);
+
+/* Restart the sequence at frame 0 and clear events, counters and sticky errors. */
+esim_ad_status esim_ad_reset(esim_ad_ctx* ctx);
+
+/* Counters since init/reset; synchronises the stream. */
+esim_ad_status esim_ad_stats_get(esim_ad_ctx* ctx, esim_ad_stats* out);
+
+/* Release every resource of the context (synchronises its stream). NULL is a no-op. */
+void esim_ad_destroy(esim_ad_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* esim_ad_status_string(esim_ad_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESIM_AD_H */

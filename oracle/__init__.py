@@ -65,6 +65,7 @@ def _load():
         lib.or_take_events.argtypes = [P, P, ctypes.c_int64]
         lib.or_get_state.argtypes = [P, P, P, P]
         lib.or_set_state_pixel.argtypes = [P, ctypes.c_int64, ctypes.c_double, P, P]
+        lib.or_set_state.argtypes = [P, P, P, P]
         lib.or_wlr_at.restype = ctypes.c_int
         lib.or_wlr_at.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P]
         lib.or_threads.restype = ctypes.c_int32
@@ -162,6 +163,14 @@ class Oracle:
         b = np.ascontiguousarray(beta9, np.float64)
         x = np.ascontiguousarray(xc7, np.float64)
         self._lib.or_set_state_pixel(self._h, int(idx), float(l_last), _ptr(b), _ptr(x))
+
+    def set_state(self, l_last, beta9, xc7) -> None:
+        """Overwrite every pixel's model: l_last [n], beta9 [n][9], xc7 [n][7]."""
+        n = self.n
+        lb = np.ascontiguousarray(np.reshape(l_last, n), np.float64)
+        b = np.ascontiguousarray(np.reshape(beta9, (n, 9)), np.float64)
+        x = np.ascontiguousarray(np.reshape(xc7, (n, 7)), np.float64)
+        self._lib.or_set_state(self._h, _ptr(lb), _ptr(b), _ptr(x))
 
     def wlr_at(self, cx: int, cy: int):
         theta = np.empty(10)

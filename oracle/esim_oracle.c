@@ -402,3 +402,11 @@ void or_set_state_pixel(or_sim* s, int64_t idx, double l_last, const double* bet
     if (beta9) for (int j = 0; j < ND; ++j) s->beta[idx * ND + j] = beta9[j];
     if (xc7) for (int j = 0; j < NF; ++j) s->xc[idx * NF + j] = xc7[j];
 }
+
+void or_set_state(or_sim* s, const double* l_last, const double* beta9, const double* xc7)
+{
+    size_t n = (size_t)s->n;
+    if (l_last) memcpy(s->l_last, l_last, n * sizeof(double));
+    if (beta9) memcpy(s->beta, beta9, n * ND * sizeof(double));
+    if (xc7) memcpy(s->xc, xc7, n * NF * sizeof(double));
+}

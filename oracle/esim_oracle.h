@@ -65,6 +65,8 @@ int64_t or_take_events(or_sim* s, int32_t* dst, int64_t cap);
 void    or_get_state(const or_sim* s, double* l_last, double* beta9, double* xc7);
 void    or_set_state_pixel(or_sim* s, int64_t idx, double l_last, const double* beta9,
                            const double* xc7);
+/* Overwrite the model of every pixel (any pointer may be NULL to keep that part). */
+void    or_set_state(or_sim* s, const double* l_last, const double* beta9, const double* xc7);
 
 /* The regression of Eqs. 4-5 at pixel (cx, cy) of the last pushed frame:
  * theta = (alpha, beta_1..beta_9), R of Eq. 4, W of Eq. 5. Returns 0 or -1. */

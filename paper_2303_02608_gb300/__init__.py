@@ -1,0 +1,333 @@
+"""Python binding of libesim_ad (the C ABI in include/esim_ad.h).
+
+Argument marshalling only: every step of the simulator runs in the CUDA
+library.  The functions keep the C names; ``Simulator`` wraps a context with
+torch tensors for device memory and streams.  Importing this module does not
+touch the GPU; the first call loads ``libesim_ad.so`` from this directory and
+raises if it has not been built (``python -m paper_2303_02608_gb300.build``).
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libesim_ad.so")
+
+ESIM_AD_OK = 0
+ESIM_AD_EINVAL = -1
+ESIM_AD_ENOMEM = -2
+ESIM_AD_ECUDA = -3
+ESIM_AD_EOVERFLOW = -4
+ESIM_AD_ETIMEOUT = -5
+ESIM_AD_ESTATE = -6
+ESIM_AD_ENOSPACE = -7
+
+ESIM_AD_ADAPTIVE = 0
+ESIM_AD_EXHAUSTIVE = 1
+ESIM_AD_LUMA_F32 = 0
+ESIM_AD_RGB_F32 = 1
+
+# Every exported symbol of the library, as declared in include/esim_ad.h.
+EXPORTS = (
+    "esim_ad_init", "esim_ad_push_frame", "esim_ad_events", "esim_ad_denoised",
+    "esim_ad_get_state", "esim_ad_set_state", "esim_ad_reset", "esim_ad_stats_get",
+    "esim_ad_destroy", "esim_ad_status_string", "esim_ad_profile_enable", "esim_ad_profile_get",
+)
+
+
+class esim_ad_config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("radius", ctypes.c_int32), ("frames", ctypes.c_int32), ("mode", ctypes.c_int32),
+        ("radiance_fmt", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("contrast", ctypes.c_float), ("h", ctypes.c_float), ("bandwidth", ctypes.c_float * 7),
+        ("log_eps", ctypes.c_float), ("ridge", ctypes.c_float), ("event_capacity", ctypes.c_uint64),
+    ]
+
+
+class esim_ad_frame(ctypes.Structure):
+    _fields_ = [
+        ("radiance", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+        ("albedo", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("on_host", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+    ]
+
+
+class esim_ad_stats(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_uint64), ("regressions", ctypes.c_uint64),
+                ("events", ctypes.c_uint64), ("pixels", ctypes.c_uint64)]
+
+
+class esim_ad_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 3), ("ms", ctypes.c_double * 3),
+                ("neighbours", ctypes.c_uint64), ("regressions", ctypes.c_uint64)]
+
+
+EVENT_DTYPE = np.dtype({"names": ["frame", "x", "y", "polarity"],
+                        "formats": ["<u4", "<u2", "<u2", "i1"],
+                        "offsets": [0, 4, 6, 8], "itemsize": 12})
+
+
+class EsimError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def load_library():
+    """Load libesim_ad.so from this package directory (fails loudly if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2303_02608_gb300.build`"
+                          " (the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    st = ctypes.c_int
+    lib.esim_ad_init.restype = st
+    lib.esim_ad_init.argtypes = [ctypes.POINTER(esim_ad_config), P, ctypes.POINTER(P)]
+    lib.esim_ad_push_frame.restype = st
+    lib.esim_ad_push_frame.argtypes = [P, ctypes.POINTER(esim_ad_frame)]
+    lib.esim_ad_events.restype = st
+    lib.esim_ad_events.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+    lib.esim_ad_denoised.restype = st
+    lib.esim_ad_denoised.argtypes = [P, P, P, ctypes.c_int]
+    lib.esim_ad_get_state.restype = st
+    lib.esim_ad_get_state.argtypes = [P, P, P, P]
+    lib.esim_ad_set_state.restype = st
+    lib.esim_ad_set_state.argtypes = [P, P, P, P]
+    lib.esim_ad_reset.restype = st
+    lib.esim_ad_reset.argtypes = [P]
+    lib.esim_ad_stats_get.restype = st
+    lib.esim_ad_stats_get.argtypes = [P, ctypes.POINTER(esim_ad_stats)]
+    lib.esim_ad_destroy.restype = None
+    lib.esim_ad_destroy.argtypes = [P]
+    lib.esim_ad_profile_enable.restype = st
+    lib.esim_ad_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.esim_ad_profile_get.restype = st
+    lib.esim_ad_profile_get.argtypes = [P, ctypes.POINTER(esim_ad_profile)]
+    lib.esim_ad_status_string.restype = ctypes.c_char_p
+    lib.esim_ad_status_string.argtypes = [st]
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().esim_ad_status_string(int(status)).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def _check(status: int, what: str) -> None:
+    if status != ESIM_AD_OK:
+        raise EsimError(status, what)
+
+
+# ------------------------------------------------------------- C-named calls
+
+def make_config(width: int, height: int, radius: int = 7, frames: int = 5, contrast: float = 0.15,
+                mode: int = ESIM_AD_ADAPTIVE, rgb: bool = True, h: float = 1.0, bandwidth=None,
+                log_eps: float = 1e-3, ridge: float = 1e-4, event_capacity: int = 1 << 22) -> esim_ad_config:
+    c = esim_ad_config()
+    c.struct_size = ctypes.sizeof(esim_ad_config)
+    c.width, c.height, c.radius, c.frames = width, height, radius, frames
+    c.mode = mode
+    c.radiance_fmt = ESIM_AD_RGB_F32 if rgb else ESIM_AD_LUMA_F32
+    c.contrast, c.h, c.log_eps, c.ridge = contrast, h, log_eps, ridge
+    bw = [1.0] * 7 if bandwidth is None else list(bandwidth)
+    for j in range(7):
+        c.bandwidth[j] = float(bw[j])
+    c.event_capacity = int(event_capacity)
+    return c
+
+
+def esim_ad_init(cfg: esim_ad_config, cuda_stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().esim_ad_init(ctypes.byref(cfg), ctypes.c_void_p(cuda_stream or None),
+                                        ctypes.byref(h)), "esim_ad_init")
+    return h.value
+
+
+def esim_ad_push_frame(ctx: int, radiance: int, normal: int, albedo: int, depth: int,
+                       variance: int = 0, on_host: bool = False) -> None:
+    f = esim_ad_frame(radiance, variance or None, normal, albedo, depth, int(on_host), 0)
+    _check(load_library().esim_ad_push_frame(ctypes.c_void_p(ctx), ctypes.byref(f)), "esim_ad_push_frame")
+
+
+def esim_ad_events(ctx: int, dst: int, cap: int, dst_is_device: bool = False) -> tuple[int, int]:
+    """Returns (status, n).  Status is returned, not raised, because ENOSPACE
+    and EOVERFLOW carry a count."""
+    n = ctypes.c_uint64(0)
+    st = load_library().esim_ad_events(ctypes.c_void_p(ctx), ctypes.c_void_p(dst or None),
+                                       ctypes.c_uint64(cap), ctypes.byref(n), int(dst_is_device))
+    return st, n.value
+
+
+def esim_ad_denoised(ctx: int, alpha: int, flags: int, dst_is_device: bool = True) -> None:
+    _check(load_library().esim_ad_denoised(ctypes.c_void_p(ctx), ctypes.c_void_p(alpha or None),
+                                           ctypes.c_void_p(flags or None), int(dst_is_device)),
+           "esim_ad_denoised")
+
+
+def esim_ad_get_state(ctx: int, l_last: int, beta: int, xc: int) -> None:
+    _check(load_library().esim_ad_get_state(ctypes.c_void_p(ctx), ctypes.c_void_p(l_last or None),
+                                            ctypes.c_void_p(beta or None), ctypes.c_void_p(xc or None)),
+           "esim_ad_get_state")
+
+
+def esim_ad_set_state(ctx: int, l_last: int, beta: int, xc: int) -> None:
+    _check(load_library().esim_ad_set_state(ctypes.c_void_p(ctx), ctypes.c_void_p(l_last or None),
+                                            ctypes.c_void_p(beta or None), ctypes.c_void_p(xc or None)),
+           "esim_ad_set_state")
+
+
+def esim_ad_reset(ctx: int) -> None:
+    _check(load_library().esim_ad_reset(ctypes.c_void_p(ctx)), "esim_ad_reset")
+
+
+def esim_ad_stats_get(ctx: int) -> dict:
+    s = esim_ad_stats()
+    _check(load_library().esim_ad_stats_get(ctypes.c_void_p(ctx), ctypes.byref(s)), "esim_ad_stats_get")
+    return {"frames": s.frames, "regressions": s.regressions, "events": s.events, "pixels": s.pixels}
+
+
+def esim_ad_profile_enable(ctx: int, on: bool = True) -> None:
+    _check(load_library().esim_ad_profile_enable(ctypes.c_void_p(ctx), int(on)), "esim_ad_profile_enable")
+
+
+KERNEL_CLASSES = ("ingest_test", "wlr_emit", "event_write")
+
+
+def esim_ad_profile_get(ctx: int) -> dict:
+    p = esim_ad_profile()
+    _check(load_library().esim_ad_profile_get(ctypes.c_void_p(ctx), ctypes.byref(p)), "esim_ad_profile_get")
+    return {"launches": {k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
+            "ms": {k: float(p.ms[i]) for i, k in enumerate(KERNEL_CLASSES)},
+            "neighbours": int(p.neighbours), "regressions": int(p.regressions)}
+
+
+def esim_ad_destroy(ctx: int) -> None:
+    if ctx:
+        load_library().esim_ad_destroy(ctypes.c_void_p(ctx))
+
+
+# ------------------------------------------------------------- convenience
+
+@dataclass
+class SimConfig:
+    width: int
+    height: int
+    radius: int = 7
+    frames: int = 5
+    contrast: float = 0.15
+    mode: int = ESIM_AD_ADAPTIVE
+    rgb: bool = True
+    h: float = 1.0
+    bandwidth: list = field(default_factory=lambda: [1.0] * 7)
+    log_eps: float = 1e-3
+    ridge: float = 1e-4
+    event_capacity: int = 1 << 22
+
+    def c_config(self) -> esim_ad_config:
+        return make_config(self.width, self.height, self.radius, self.frames, self.contrast, self.mode,
+                           self.rgb, self.h, self.bandwidth, self.log_eps, self.ridge, self.event_capacity)
+
+
+class Simulator:
+    """One event-simulation context on the current CUDA device and stream.
+
+    ``push`` accepts a dict with ``radiance`` [C][H][W], ``normal`` [3][H][W],
+    ``albedo`` [3][H][W], ``depth`` [H][W] as contiguous float32 torch tensors,
+    all on the GPU, or all on the host (pinned for asynchronous copies).
+    """
+
+    def __init__(self, cfg: SimConfig, stream=None):
+        import torch
+        self.cfg = cfg
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = esim_ad_init(cfg.c_config(), self.stream.cuda_stream)
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            esim_ad_destroy(self.ctx)
+            self.ctx = None
+
+    __del__ = close
+
+    def push(self, frame: dict) -> None:
+        t = self._torch
+        planes = [frame[k] for k in ("radiance", "normal", "albedo", "depth")]
+        on_host = not planes[0].is_cuda
+        for p in planes:
+            if p.dtype != t.float32 or not p.is_contiguous() or p.is_cuda == on_host:
+                raise ValueError("frame planes must be contiguous float32, all on the GPU or all on the host")
+        rad, nor, alb, dep = (p.data_ptr() for p in planes)
+        esim_ad_push_frame(self.ctx, rad, nor, alb, dep, on_host=on_host)
+        if not on_host:
+            # inputs are read in stream order; keep them alive until the next sync point
+            self._keep.append(planes)
+
+    def events(self) -> np.ndarray:
+        st, n = esim_ad_events(self.ctx, 0, 0)
+        if st not in (ESIM_AD_OK, ESIM_AD_ENOSPACE):
+            raise EsimError(st, "esim_ad_events")
+        out = np.empty(n, EVENT_DTYPE)
+        if n:
+            st, n2 = esim_ad_events(self.ctx, out.ctypes.data, n)
+            _check(st, "esim_ad_events")
+        self._keep.clear()
+        return out
+
+    def events_device(self, dst, cap: int) -> int:
+        st, n = esim_ad_events(self.ctx, dst.data_ptr(), cap, dst_is_device=True)
+        _check(st, "esim_ad_events")
+        self._keep.clear()
+        return n
+
+    def denoised(self):
+        t = self._torch
+        a = t.empty(self.cfg.height, self.cfg.width, dtype=t.float32, device=self.device)
+        f = t.empty(self.cfg.height, self.cfg.width, dtype=t.uint8, device=self.device)
+        esim_ad_denoised(self.ctx, a.data_ptr(), f.data_ptr(), True)
+        return a, f
+
+    def get_state(self) -> dict:
+        n = self.cfg.width * self.cfg.height
+        l_last = np.empty(n, np.float32)
+        beta = np.empty((n, 7), np.float32)
+        xc = np.empty((n, 7), np.float32)
+        esim_ad_get_state(self.ctx, l_last.ctypes.data, beta.ctypes.data, xc.ctypes.data)
+        return {"l_last": l_last, "beta": beta, "xc": xc}
+
+    def set_state(self, l_last, beta, xc) -> None:
+        l_last = np.ascontiguousarray(l_last, np.float32)
+        beta = np.ascontiguousarray(beta, np.float32)
+        xc = np.ascontiguousarray(xc, np.float32)
+        esim_ad_set_state(self.ctx, l_last.ctypes.data, beta.ctypes.data, xc.ctypes.data)
+
+    def reset(self) -> None:
+        esim_ad_reset(self.ctx)
+        self._keep.clear()
+
+    def stats(self) -> dict:
+        return esim_ad_stats_get(self.ctx)
+
+    def profile(self, on: bool | None = None) -> dict | None:
+        """profile(True) starts kernel timing (clearing it); profile() returns totals."""
+        if on is not None:
+            esim_ad_profile_enable(self.ctx, on)
+            return None
+        return esim_ad_profile_get(self.ctx)

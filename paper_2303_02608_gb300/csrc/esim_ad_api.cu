@@ -1,0 +1,597 @@
+// Host side of the C ABI declared in include/esim_ad.h: configuration checks,
+// device memory, the TMA descriptor of the frame ring, and the per-frame
+// launch sequence of the hot path.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace esim;
+
+namespace {
+
+// sqrt(log2(e) / 2): scaling a regressor by k/(h b) turns the product
+// Gaussian exp(-sum (d/(h b))^2 / 2) of Eq. 5 into 2^(-sum u^2).
+const double kExp2Scale = 0.84932180028801904272;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Allocation-failure injection for tests: ESIM_AD_FAULT_ALLOC=<k> makes the
+// k-th device allocation of the process (1-based) fail with ENOMEM.
+int g_alloc_seq = 0;
+
+bool fault_alloc_now()
+{
+    const char* s = getenv("ESIM_AD_FAULT_ALLOC");
+    ++g_alloc_seq;
+    if (!s || !*s) return false;
+    return atoi(s) == g_alloc_seq;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct esim_ad_ctx {
+    esim_ad_config cfg;
+    cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    int device = 0;
+    int W = 0, H = 0;
+    size_t N = 0;
+    int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_chunks = 0;
+    int smem_bytes = 0;
+    float4* ring = nullptr;
+    float4* state = nullptr;
+    float* alpha = nullptr;
+    uint8_t* flag = nullptr;
+    int32_t* nev = nullptr;
+    uint32_t* tile_queue = nullptr;
+    int32_t* tile_nflag = nullptr;
+    uint8_t* tile_pix = nullptr;
+    uint32_t* chunk_cnt = nullptr;
+    unsigned long long* chunk_off = nullptr;
+    esim_ad_event* events = nullptr;
+    Ctrl* ctrl = nullptr;
+    float* staging[2] = {nullptr, nullptr};   // host-frame landing buffers [10][H][W]
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+    int staging_next = 0;
+    CUtensorMap tmap;
+    // kernel timing (esim_ad_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_events;      // pool, pairs (start, stop)
+    std::vector<int> prof_class;               // class of each recorded pair
+    size_t prof_used = 0;                      // pairs recorded
+    uint64_t t = 0;
+    esim_ad_status sticky = ESIM_AD_OK;
+};
+
+namespace {
+
+esim_ad_status dev_alloc(void** p, size_t bytes)
+{
+    if (fault_alloc_now()) return ESIM_AD_ENOMEM;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return ESIM_AD_ENOMEM;
+    }
+    return ESIM_AD_OK;
+}
+
+bool finite_pos(float v) { return isfinite(v) && v > 0.0f; }
+
+esim_ad_status check_config(const esim_ad_config* c)
+{
+    if (!c || c->struct_size != sizeof(esim_ad_config)) return ESIM_AD_EINVAL;
+    if (c->width < 1 || c->height < 1 || c->width > 65535 || c->height > 65535) return ESIM_AD_EINVAL;
+    if (c->radius < 1 || c->radius > kMaxRadius) return ESIM_AD_EINVAL;
+    if (c->frames < 1 || c->frames > kMaxFrames) return ESIM_AD_EINVAL;
+    if (c->mode != ESIM_AD_ADAPTIVE && c->mode != ESIM_AD_EXHAUSTIVE) return ESIM_AD_EINVAL;
+    if (c->radiance_fmt != ESIM_AD_LUMA_F32 && c->radiance_fmt != ESIM_AD_RGB_F32) return ESIM_AD_EINVAL;
+    if (!finite_pos(c->contrast) || !finite_pos(c->h) || !finite_pos(c->ridge)) return ESIM_AD_EINVAL;
+    for (int j = 0; j < 7; ++j)
+        if (!finite_pos(c->bandwidth[j])) return ESIM_AD_EINVAL;
+    if (!isfinite(c->log_eps) || c->log_eps < 0.0f) return ESIM_AD_EINVAL;
+    if (c->event_capacity < 1 || c->event_capacity > (1ull << 36)) return ESIM_AD_EINVAL;
+    return ESIM_AD_OK;
+}
+
+void release(esim_ad_ctx* c)
+{
+    void* ptrs[] = {c->ring, c->state, c->alpha, c->flag, c->nev, c->tile_queue, c->tile_nflag,
+                    c->tile_pix, c->chunk_cnt, c->chunk_off, c->events, c->ctrl,
+                    c->staging[0], c->staging[1]};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+        if (c->ev_consumed[i]) cudaEventDestroy(c->ev_consumed[i]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    c->prof_events.clear();
+}
+
+// Bracket one launch with a pair of pooled events when profiling is on.
+struct ProfScope {
+    esim_ad_ctx* c;
+    size_t pair = (size_t)-1;
+    ProfScope(esim_ad_ctx* ctx, int cls) : c(ctx)
+    {
+        if (!c->prof_on) return;
+        if (2 * c->prof_used + 2 > c->prof_events.size()) {
+            for (int k = 0; k < 2; ++k) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                c->prof_events.push_back(e);
+            }
+        }
+        pair = c->prof_used++;
+        if (c->prof_class.size() < c->prof_used) c->prof_class.resize(c->prof_used);
+        c->prof_class[pair] = cls;
+        cudaEventRecord(c->prof_events[2 * pair], c->stream);
+    }
+    ~ProfScope()
+    {
+        if (pair != (size_t)-1) cudaEventRecord(c->prof_events[2 * pair + 1], c->stream);
+    }
+};
+
+esim_ad_status encode_ring_map(esim_ad_ctx* c)
+{
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return ESIM_AD_ECUDA;
+    // ring viewed as a 4-D tensor: {4 floats, W, H, 2T planes}
+    const cuuint64_t dims[4] = {4, (cuuint64_t)c->W, (cuuint64_t)c->H, (cuuint64_t)(2 * c->cfg.frames)};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)16 * c->W, (cuuint64_t)16 * c->W * c->H};
+    const cuuint32_t box[4] = {4, (cuuint32_t)(kTileX + 2 * c->cfg.radius),
+                               (cuuint32_t)(kTileY + 2 * c->cfg.radius), 2};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = reinterpret_cast<EncodeTiledFn>(fn)(
+        &c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->ring, dims, strides, box, estr,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ESIM_AD_OK : ESIM_AD_ECUDA;
+}
+
+esim_ad_status sync_and_check(esim_ad_ctx* c, Ctrl* host_ctrl)
+{
+    Ctrl tmp;
+    Ctrl* h = host_ctrl ? host_ctrl : &tmp;
+    if (cudaMemcpyAsync(h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    if (h->status & kStatusTimeout) c->sticky = ESIM_AD_ETIMEOUT;
+    else if (h->status & kStatusOverflow) c->sticky = ESIM_AD_EOVERFLOW;
+    return ESIM_AD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* esim_ad_status_string(esim_ad_status s)
+{
+    switch (s) {
+    case ESIM_AD_OK: return "ok";
+    case ESIM_AD_EINVAL: return "invalid argument";
+    case ESIM_AD_ENOMEM: return "out of memory";
+    case ESIM_AD_ECUDA: return "CUDA error";
+    case ESIM_AD_EOVERFLOW: return "event buffer overflow";
+    case ESIM_AD_ETIMEOUT: return "device wait timed out";
+    case ESIM_AD_ESTATE: return "context unusable after an earlier error";
+    case ESIM_AD_ENOSPACE: return "destination buffer too small";
+    }
+    return "unknown status";
+}
+
+esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_ad_ctx** out)
+{
+    if (!out) return ESIM_AD_EINVAL;
+    esim_ad_status st = check_config(cfg);
+    if (st != ESIM_AD_OK) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ESIM_AD_ECUDA;
+    }
+    esim_ad_ctx* c = new (std::nothrow) esim_ad_ctx();
+    if (!c) return ESIM_AD_ENOMEM;
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->device = dev;
+    c->W = cfg->width;
+    c->H = cfg->height;
+    c->N = (size_t)c->W * c->H;
+    c->tiles_x = (c->W + kTileX - 1) / kTileX;
+    c->tiles_y = (c->H + kTileY - 1) / kTileY;
+    c->n_tiles = c->tiles_x * c->tiles_y;
+    c->n_chunks = (int)((c->N + kChunk - 1) / kChunk);
+    c->smem_bytes = (int)wlr_smem_bytes(cfg->radius);
+    const size_t N = c->N, T = (size_t)cfg->frames;
+    struct {
+        void** p;
+        size_t bytes;
+    } allocs[] = {
+        {(void**)&c->ring, 2 * T * N * sizeof(float4)},
+        {(void**)&c->state, 4 * N * sizeof(float4)},
+        {(void**)&c->alpha, N * sizeof(float)},
+        {(void**)&c->flag, N},
+        {(void**)&c->nev, N * sizeof(int32_t)},
+        {(void**)&c->tile_queue, (size_t)c->n_tiles * sizeof(uint32_t)},
+        {(void**)&c->tile_nflag, (size_t)c->n_tiles * sizeof(int32_t)},
+        {(void**)&c->tile_pix, (size_t)c->n_tiles * kTilePix},
+        {(void**)&c->chunk_cnt, (size_t)c->n_chunks * sizeof(uint32_t)},
+        {(void**)&c->chunk_off, (size_t)c->n_chunks * sizeof(unsigned long long)},
+        {(void**)&c->events, (size_t)cfg->event_capacity * sizeof(esim_ad_event)},
+        {(void**)&c->ctrl, sizeof(Ctrl)},
+    };
+    for (auto& a : allocs) {
+        st = dev_alloc(a.p, a.bytes);
+        if (st != ESIM_AD_OK) {
+            release(c);
+            delete c;
+            return st;
+        }
+    }
+    if (cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMemset(c->alpha, 0, N * sizeof(float)) != cudaSuccess ||
+        cudaMemset(c->flag, 0, N) != cudaSuccess || cudaMemset(c->nev, 0, N * sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(c->state, 0, 4 * N * sizeof(float4)) != cudaSuccess) {
+        release(c);
+        delete c;
+        return ESIM_AD_ECUDA;
+    }
+    if (encode_ring_map(c) != ESIM_AD_OK || wlr_prepare(c->smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        release(c);
+        delete c;
+        return ESIM_AD_ECUDA;
+    }
+    *out = c;
+    return ESIM_AD_OK;
+}
+
+// Copy a host frame into one of two device landing buffers on the copy
+// stream, ordered after the kernels that last read that buffer; the compute
+// stream then waits for the copy.  Returns the device-side plane pointers.
+static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, const float** rad,
+                                       const float** nor, const float** alb, const float** dep,
+                                       int* slot_out)
+{
+    const size_t N = c->N;
+    const int s = c->staging_next;
+    if (!c->copy_stream) {
+        if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+        for (int i = 0; i < 2; ++i) {
+            if (cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&c->ev_consumed[i], cudaEventDisableTiming) != cudaSuccess)
+                return ESIM_AD_ECUDA;
+            if (cudaEventRecord(c->ev_consumed[i], c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        }
+    }
+    if (!c->staging[s]) {
+        esim_ad_status st = dev_alloc((void**)&c->staging[s], 10 * N * sizeof(float));
+        if (st != ESIM_AD_OK) return st;
+    }
+    float* base = c->staging[s];
+    const int ch = c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1;
+    if (cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[s], 0) != cudaSuccess) return ESIM_AD_ECUDA;
+    struct {
+        const float* src;
+        size_t off, n;
+    } cp[] = {{f->radiance, 0, ch * N}, {f->normal, 3 * N, 3 * N}, {f->albedo, 6 * N, 3 * N},
+              {f->depth, 9 * N, N}};
+    for (auto& k : cp)
+        if (cudaMemcpyAsync(base + k.off, k.src, k.n * sizeof(float), cudaMemcpyHostToDevice,
+                            c->copy_stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+    if (cudaEventRecord(c->ev_copied[s], c->copy_stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    if (cudaStreamWaitEvent(c->stream, c->ev_copied[s], 0) != cudaSuccess) return ESIM_AD_ECUDA;
+    *rad = base;
+    *nor = base + 3 * N;
+    *alb = base + 6 * N;
+    *dep = base + 9 * N;
+    *slot_out = s;
+    c->staging_next ^= 1;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
+{
+    if (!c || !f || !f->radiance || !f->normal || !f->albedo || !f->depth) return ESIM_AD_EINVAL;
+    if (c->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    DeviceGuard guard(c->device);
+    const float *rad = f->radiance, *nor = f->normal, *alb = f->albedo, *dep = f->depth;
+    int slot = -1;
+    if (f->on_host) {
+        esim_ad_status st = stage_host_frame(c, f, &rad, &nor, &alb, &dep, &slot);
+        if (st != ESIM_AD_OK) return st;
+    }
+    const int t = (int)(c->t % 0x7fffffff);
+    const bool adaptive_test = c->cfg.mode == ESIM_AD_ADAPTIVE && c->t > 0;
+    if (cudaMemsetAsync(c->ctrl, 0, kCtrlPerFrameBytes, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+
+    IngestParams ip;
+    ip.rad = rad;
+    ip.normal = nor;
+    ip.albedo = alb;
+    ip.depth = dep;
+    ip.rad_ch = c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1;
+    ip.W = c->W;
+    ip.H = c->H;
+    ip.tiles_x = c->tiles_x;
+    ip.slot = t % c->cfg.frames;
+    ip.test = adaptive_test ? 1 : 0;
+    ip.log_eps = c->cfg.log_eps;
+    ip.C = c->cfg.contrast;
+    ip.ring = c->ring;
+    ip.state = c->state;
+    ip.flag = c->flag;
+    ip.nev = c->nev;
+    ip.tile_queue = c->tile_queue;
+    ip.tile_nflag = c->tile_nflag;
+    ip.tile_pix = c->tile_pix;
+    ip.ctrl = c->ctrl;
+    {
+        ProfScope ps(c, 0);
+        if (launch_ingest(ip, c->n_tiles, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    }
+    if (slot >= 0 && cudaEventRecord(c->ev_consumed[slot], c->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+
+    WlrParams wp;
+    wp.W = c->W;
+    wp.H = c->H;
+    wp.r = c->cfg.radius;
+    wp.T = c->cfg.frames;
+    wp.t = t;
+    wp.n_tau = (int)((c->t + 1) < (uint64_t)c->cfg.frames ? (c->t + 1) : (uint64_t)c->cfg.frames);
+    wp.tiles_x = c->tiles_x;
+    wp.dense = adaptive_test ? 0 : 1;
+    wp.init = c->t == 0 ? 1 : 0;
+    wp.sw = kTileX + 2 * c->cfg.radius;
+    wp.sh = kTileY + 2 * c->cfg.radius;
+    wp.C = c->cfg.contrast;
+    wp.s_coord = (float)(kExp2Scale / c->cfg.h);
+    wp.s_coord_px = (float)(kExp2Scale / ((double)c->cfg.h * c->cfg.radius));
+    for (int j = 0; j < 7; ++j)
+        wp.s_feat[j] = (float)(kExp2Scale / ((double)c->cfg.h * c->cfg.bandwidth[j]));
+    wp.ridge = c->cfg.ridge;
+    wp.ring = c->ring;
+    wp.state = c->state;
+    wp.alpha = c->alpha;
+    wp.nev = c->nev;
+    wp.tile_queue = c->tile_queue;
+    wp.tile_nflag = c->tile_nflag;
+    wp.tile_pix = c->tile_pix;
+    wp.ctrl = c->ctrl;
+    {
+        ProfScope ps(c, 1);
+        if (launch_wlr(c->tmap, wp, c->n_tiles, c->smem_bytes, c->stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+    }
+
+    if (c->t > 0) {
+        EventParams ep;
+        ep.nev = c->nev;
+        ep.n_pix = (long long)c->N;
+        ep.W = c->W;
+        ep.n_chunks = c->n_chunks;
+        ep.frame = (uint32_t)c->t;
+        ep.chunk_cnt = c->chunk_cnt;
+        ep.chunk_off = c->chunk_off;
+        ep.events = c->events;
+        ep.capacity = c->cfg.event_capacity;
+        ep.ctrl = c->ctrl;
+        ProfScope ps(c, 2);
+        if (launch_events(ep, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    }
+    if (slot >= 0) {
+        // the caller may reuse its host buffers once its copies are done
+        if (cudaEventSynchronize(c->ev_copied[slot]) != cudaSuccess) return ESIM_AD_ECUDA;
+    }
+    c->t += 1;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_events(esim_ad_ctx* c, esim_ad_event* dst, uint64_t cap, uint64_t* n_out,
+                              int dst_is_device)
+{
+    if (!c || !n_out || (cap > 0 && !dst)) return ESIM_AD_EINVAL;
+    if (c->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    DeviceGuard guard(c->device);
+    Ctrl h;
+    if (sync_and_check(c, &h) != ESIM_AD_OK) return ESIM_AD_ECUDA;
+    const unsigned long long total = h.ev_total;
+    if (c->sticky == ESIM_AD_EOVERFLOW) {
+        *n_out = total;
+        return ESIM_AD_EOVERFLOW;
+    }
+    if (c->sticky != ESIM_AD_OK) return c->sticky;
+    *n_out = total;
+    if (cap < total) return ESIM_AD_ENOSPACE;
+    if (total > 0) {
+        if (cudaMemcpyAsync(dst, c->events, total * sizeof(esim_ad_event),
+                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+        if (cudaMemsetAsync(&c->ctrl->ev_total, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    }
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_denoised(esim_ad_ctx* c, float* alpha, uint8_t* flags, int dst_is_device)
+{
+    if (!c) return ESIM_AD_EINVAL;
+    if (c->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    DeviceGuard guard(c->device);
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (alpha && cudaMemcpyAsync(alpha, c->alpha, c->N * sizeof(float), k, c->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    if (flags && cudaMemcpyAsync(flags, c->flag, c->N, k, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    if (sync_and_check(c, nullptr) != ESIM_AD_OK) return ESIM_AD_ECUDA;
+    return c->sticky == ESIM_AD_OK ? ESIM_AD_OK : c->sticky;
+}
+
+esim_ad_status esim_ad_get_state(esim_ad_ctx* c, float* l_last, float* beta, float* xc)
+{
+    if (!c) return ESIM_AD_EINVAL;
+    if (c->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    DeviceGuard guard(c->device);
+    const size_t N = c->N;
+    float4* h = (float4*)malloc(4 * N * sizeof(float4));
+    if (!h) return ESIM_AD_ENOMEM;
+    if (cudaMemcpyAsync(h, c->state, 4 * N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        sync_and_check(c, nullptr) != ESIM_AD_OK) {
+        free(h);
+        return ESIM_AD_ECUDA;
+    }
+    for (size_t i = 0; i < N; ++i) {
+        const float4 b0 = h[i], b1 = h[N + i], x0 = h[2 * N + i], x1 = h[3 * N + i];
+        if (l_last) l_last[i] = b1.w;
+        if (beta) {
+            float* b = beta + 7 * i;
+            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+            b[4] = b1.x; b[5] = b1.y; b[6] = b1.z;
+        }
+        if (xc) {
+            float* x = xc + 7 * i;
+            x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+            x[4] = x1.x; x[5] = x1.y; x[6] = x1.z;
+        }
+    }
+    free(h);
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_set_state(esim_ad_ctx* c, const float* l_last, const float* beta, const float* xc)
+{
+    if (!c) return ESIM_AD_EINVAL;
+    if (c->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    DeviceGuard guard(c->device);
+    const size_t N = c->N;
+    float4* h = (float4*)malloc(4 * N * sizeof(float4));
+    if (!h) return ESIM_AD_ENOMEM;
+    if (cudaMemcpyAsync(h, c->state, 4 * N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        free(h);
+        return ESIM_AD_ECUDA;
+    }
+    for (size_t i = 0; i < N; ++i) {
+        if (l_last) h[N + i].w = l_last[i];
+        if (beta) {
+            const float* b = beta + 7 * i;
+            h[i] = make_float4(b[0], b[1], b[2], b[3]);
+            h[N + i].x = b[4]; h[N + i].y = b[5]; h[N + i].z = b[6];
+        }
+        if (xc) {
+            const float* x = xc + 7 * i;
+            h[2 * N + i] = make_float4(x[0], x[1], x[2], x[3]);
+            h[3 * N + i] = make_float4(x[4], x[5], x[6], 0.0f);
+        }
+    }
+    esim_ad_status st = ESIM_AD_OK;
+    if (cudaMemcpyAsync(c->state, h, 4 * N * sizeof(float4), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        st = ESIM_AD_ECUDA;
+    free(h);
+    return st;
+}
+
+esim_ad_status esim_ad_reset(esim_ad_ctx* c)
+{
+    if (!c) return ESIM_AD_EINVAL;
+    DeviceGuard guard(c->device);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    c->t = 0;
+    c->sticky = ESIM_AD_OK;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_stats_get(esim_ad_ctx* c, esim_ad_stats* out)
+{
+    if (!c || !out) return ESIM_AD_EINVAL;
+    DeviceGuard guard(c->device);
+    Ctrl h;
+    if (sync_and_check(c, &h) != ESIM_AD_OK) return ESIM_AD_ECUDA;
+    out->frames = c->t;
+    out->regressions = h.regressions;
+    out->events = h.ev_cum;
+    out->pixels = c->N;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_profile_enable(esim_ad_ctx* c, int on)
+{
+    if (!c) return ESIM_AD_EINVAL;
+    DeviceGuard guard(c->device);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    c->prof_on = on != 0;
+    c->prof_used = 0;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_profile_get(esim_ad_ctx* c, esim_ad_profile* out)
+{
+    if (!c || !out) return ESIM_AD_EINVAL;
+    DeviceGuard guard(c->device);
+    Ctrl h;
+    if (sync_and_check(c, &h) != ESIM_AD_OK) return ESIM_AD_ECUDA;
+    memset(out, 0, sizeof(*out));
+    for (size_t k = 0; k < c->prof_used; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->prof_events[2 * k], c->prof_events[2 * k + 1]) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+        out->launches[c->prof_class[k]] += 1;
+        out->ms[c->prof_class[k]] += ms;
+    }
+    out->neighbours = h.neighbours;
+    out->regressions = h.regressions;
+    return ESIM_AD_OK;
+}
+
+void esim_ad_destroy(esim_ad_ctx* c)
+{
+    if (!c) return;
+    {
+        DeviceGuard guard(c->device);
+        cudaStreamSynchronize(c->stream);
+        if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+        release(c);
+    }
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Ingest + Proposition-1 test + stream compaction (one kernel, one pass over
+// the frame).
+//
+// Per pixel: luminance -> log brightness y = ln(Y + eps) (Section 1.1,
+// Section 2.1: y := L = log E), write (y, features) into the ring slot of
+// this frame, then, in adaptive mode, evaluate the test of Proposition 1
+// (Eqs. 6-9) with the model kept since the pixel's last event:
+//     Delta R = (beta^T (x^c - xhat^c))^2 >= C^2   ->   flag the pixel.
+// The image-coordinate part of x^c - xhat^c is zero (same pixel), so only the
+// seven feature slopes enter.  Flagged pixels of the CTA's 32x8 tile are
+// compacted in raster order with warp ballots and a block prefix; the tile is
+// appended to the active-tile queue with one atomic per tile.
+//
+// Memory traffic per pixel (fp32 RGB input): 44 B in (radiance 12, normal 12,
+// albedo 12, depth 4; variance is not read), 32 B ring write, 64 B state read
+// (adaptive, t >= 1), 1 B flag + 4 B event-count clear.
+#include "internal.h"
+
+namespace esim {
+
+__global__ void __launch_bounds__(kTilePix) ingest_test_kernel(IngestParams p)
+{
+    const int tile = blockIdx.x;
+    const int lx = threadIdx.x & 31;
+    const int ly = threadIdx.x >> 5;
+    const int x = (tile % p.tiles_x) * kTileX + lx;
+    const int y = (tile / p.tiles_x) * kTileY + ly;
+    const bool inside = x < p.W && y < p.H;
+    const size_t N = (size_t)p.W * p.H;
+    int flag = 0;
+    if (inside) {
+        const size_t i = (size_t)y * p.W + x;
+        float Y;
+        if (p.rad_ch == 3) {
+            // Rec.709 luminance of the RGB radiance
+            Y = 0.2126f * __ldg(p.rad + i) + 0.7152f * __ldg(p.rad + N + i) +
+                0.0722f * __ldg(p.rad + 2 * N + i);
+        } else {
+            Y = __ldg(p.rad + i);
+        }
+        const float yv = logf(Y + p.log_eps);
+        const float n0 = __ldg(p.normal + i), n1 = __ldg(p.normal + N + i),
+                    n2 = __ldg(p.normal + 2 * N + i);
+        const float d = __ldg(p.depth + i);
+        const float a0 = __ldg(p.albedo + i), a1 = __ldg(p.albedo + N + i),
+                    a2 = __ldg(p.albedo + 2 * N + i);
+        p.ring[(size_t)(2 * p.slot) * N + i] = make_float4(yv, n0, n1, n2);
+        p.ring[(size_t)(2 * p.slot + 1) * N + i] = make_float4(d, a0, a1, a2);
+        if (p.test) {
+            const float4 b0 = p.state[i];
+            const float4 b1 = p.state[N + i];
+            const float4 c0 = p.state[2 * N + i];
+            const float4 c1 = p.state[3 * N + i];
+            float s = b0.x * (c0.x - n0);
+            s = fmaf(b0.y, c0.y - n1, s);
+            s = fmaf(b0.z, c0.z - n2, s);
+            s = fmaf(b0.w, c0.w - d, s);
+            s = fmaf(b1.x, c1.x - a0, s);
+            s = fmaf(b1.y, c1.y - a1, s);
+            s = fmaf(b1.z, c1.z - a2, s);
+            flag = (s * s >= p.C * p.C) ? 1 : 0;
+        } else {
+            flag = 1;
+        }
+        p.flag[i] = (uint8_t)flag;
+        p.nev[i] = 0;
+    }
+    if (!p.test) return;  // the regression walks every tile densely
+
+    // Compact flagged pixels of the tile in raster order.
+    __shared__ int warp_cnt[kTilePix / 32];
+    const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+    if (lx == 0) warp_cnt[ly] = __popc(ballot);
+    __syncthreads();
+    int base = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kTilePix / 32; ++w) {
+        const int c = warp_cnt[w];
+        base += (w < ly) ? c : 0;
+        total += c;
+    }
+    if (flag) {
+        const int pos = base + __popc(ballot & ((1u << lx) - 1u));
+        p.tile_pix[(size_t)tile * kTilePix + pos] = (uint8_t)threadIdx.x;
+    }
+    if (threadIdx.x == 0) {
+        p.tile_nflag[tile] = total;
+        if (total > 0) {
+            const uint32_t slot = atomicAdd(&p.ctrl->tile_count, 1u);
+            p.tile_queue[slot] = (uint32_t)tile;
+        }
+    }
+}
+
+cudaError_t launch_ingest(const IngestParams& p, int n_tiles, cudaStream_t s)
+{
+    ingest_test_kernel<<<n_tiles, kTilePix, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace esim

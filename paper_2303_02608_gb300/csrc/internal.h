@@ -1,0 +1,107 @@
+// Internal declarations shared by the CUDA translation units of libesim_ad.
+// Nothing here is part of the public ABI (include/esim_ad.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "esim_ad.h"
+
+namespace esim {
+
+// Pixel tile of one CTA in the ingest/test and regression kernels: 32 x 8
+// pixels, one warp per tile row, so a warp's loads of a ring row are one
+// contiguous 512-byte segment per half-plane.
+constexpr int kTileX = 32;
+constexpr int kTileY = 8;
+constexpr int kTilePix = kTileX * kTileY;  // 256 threads per CTA
+constexpr int kChunk = 2048;               // pixels per event-scan chunk (256 x 8)
+constexpr int kMaxRadius = 15;
+constexpr int kMaxFrames = 16;
+
+// Sticky device status bits.
+constexpr uint32_t kStatusOverflow = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+
+// Device control block.  The first 16 bytes are cleared before every frame.
+struct Ctrl {
+    uint32_t tile_count;            // active tiles queued by the test kernel
+    uint32_t chunk_done;            // ticket of the event-count kernel
+    uint32_t pad0, pad1;
+    unsigned long long ev_total;    // events produced since the last drain
+    unsigned long long ev_cum;      // events since init/reset
+    unsigned long long regressions; // pixels regressed since init/reset
+    unsigned long long neighbours;  // (pixel, neighbour) pairs regressed
+    uint32_t status;                // sticky kStatus* bits
+    uint32_t pad2;
+};
+constexpr size_t kCtrlPerFrameBytes = 16;
+
+// Ring of the last T frames: float4 planes [2T][H][W]; plane 2*slot holds
+// (y, normal xyz), plane 2*slot+1 holds (depth, albedo rgb).
+// Model state: float4 planes [4][H][W]:
+//   0: beta (normal xyz, depth)   1: beta (albedo rgb), L_last
+//   2: x^c (normal xyz, depth)    3: x^c (albedo rgb), 0
+
+struct IngestParams {
+    const float* rad;      // [C][H][W]
+    const float* normal;   // [3][H][W]
+    const float* albedo;   // [3][H][W]
+    const float* depth;    // [H][W]
+    int rad_ch;            // 1 or 3
+    int W, H, tiles_x;
+    int slot;              // ring slot of this frame
+    int test;              // 1: Proposition-1 test; 0: flag every pixel
+    float log_eps, C;
+    float4* ring;
+    const float4* state;
+    uint8_t* flag;
+    int32_t* nev;
+    uint32_t* tile_queue;
+    int32_t* tile_nflag;
+    uint8_t* tile_pix;
+    Ctrl* ctrl;
+};
+
+struct WlrParams {
+    int W, H, r, T, t, n_tau, tiles_x;
+    int dense;             // 1: every tile and pixel; 0: tiles from the queue
+    int init;              // 1: frame 0 (initialise models, no events)
+    int sw, sh;            // staged tile: (32 + 2r) x (8 + 2r) pixels
+    float C;
+    float s_coord_px;      // regressor scale of a one-pixel coordinate offset
+    float s_coord;         // regressor scale of the coordinate unit (offset / r)
+    float s_feat[7];       // regressor scale per feature: k / (h b_j)
+    float ridge;
+    const float4* ring;
+    float4* state;
+    float* alpha;
+    int32_t* nev;
+    const uint32_t* tile_queue;
+    const int32_t* tile_nflag;
+    const uint8_t* tile_pix;
+    Ctrl* ctrl;
+};
+
+struct EventParams {
+    const int32_t* nev;
+    long long n_pix;
+    int W;
+    int n_chunks;
+    uint32_t frame;
+    uint32_t* chunk_cnt;
+    unsigned long long* chunk_off;
+    esim_ad_event* events;
+    unsigned long long capacity;
+    Ctrl* ctrl;
+};
+
+cudaError_t launch_ingest(const IngestParams& p, int n_tiles, cudaStream_t s);
+cudaError_t wlr_prepare(int smem_bytes);
+size_t wlr_smem_bytes(int r);
+cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, int grid, int smem_bytes,
+                       cudaStream_t s);
+cudaError_t launch_events(const EventParams& p, cudaStream_t s);
+
+}  // namespace esim

@@ -1,0 +1,260 @@
+"""The C-ABI boundary: symbols, struct layout, argument checking, ownership
+and error behaviour.  The CPU tests load the library without a GPU; the GPU
+tests cover allocation failure, buffer overflow and draining."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+import tempfile
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "esim_ad.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(esim_ad_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2303_02608_gb300 import build
+    build.build()
+    import paper_2303_02608_gb300 as m
+    return m
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert declared, "no functions parsed from the header"
+    assert set(declared) == set(lib.EXPORTS)
+    so = lib.load_library()
+    for name in declared:
+        assert getattr(so, name) is not None
+
+
+def test_struct_layout_matches_header(lib):
+    """sizeof/offsetof from the C compiler equal the ctypes mirrors."""
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "esim_ad.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(esim_ad_config), offsetof(esim_ad_config, contrast),
+         offsetof(esim_ad_config, event_capacity), sizeof(esim_ad_frame), offsetof(esim_ad_frame, on_host),
+         sizeof(esim_ad_event), sizeof(esim_ad_stats));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    want = [ctypes.sizeof(lib.esim_ad_config), lib.esim_ad_config.contrast.offset,
+            lib.esim_ad_config.event_capacity.offset, ctypes.sizeof(lib.esim_ad_frame),
+            lib.esim_ad_frame.on_host.offset, lib.EVENT_DTYPE.itemsize, ctypes.sizeof(lib.esim_ad_stats)]
+    assert got == want
+
+
+def _bad_configs(lib):
+    ok = lib.make_config(64, 48)
+    yield "struct_size", dict(struct_size=12)
+    for k, v in [("width", 0), ("height", -1), ("width", 70000), ("radius", 0), ("radius", 16),
+                 ("frames", 0), ("frames", 17), ("mode", 2), ("radiance_fmt", 5), ("contrast", 0.0),
+                 ("contrast", float("nan")), ("h", -1.0), ("ridge", 0.0), ("log_eps", -1.0),
+                 ("event_capacity", 0)]:
+        yield k, {k: v}
+    yield "bandwidth", {"bandwidth": 0.0}
+    del ok
+
+
+def test_init_rejects_bad_config_without_touching_gpu(lib):
+    so = lib.load_library()
+    for name, change in _bad_configs(lib):
+        cfg = lib.make_config(64, 48)
+        for k, v in change.items():
+            if k == "bandwidth":
+                cfg.bandwidth[3] = v
+            else:
+                setattr(cfg, k, v)
+        h = ctypes.c_void_p(1234)
+        st = so.esim_ad_init(ctypes.byref(cfg), None, ctypes.byref(h))
+        assert st == lib.ESIM_AD_EINVAL, name
+        assert h.value == 1234, "output pointer must be untouched on error"
+    assert so.esim_ad_init(None, None, ctypes.byref(ctypes.c_void_p())) == lib.ESIM_AD_EINVAL
+    cfg = lib.make_config(64, 48)
+    assert so.esim_ad_init(ctypes.byref(cfg), None, None) == lib.ESIM_AD_EINVAL
+
+
+def test_null_context_calls(lib):
+    so = lib.load_library()
+    n = ctypes.c_uint64()
+    assert so.esim_ad_push_frame(None, None) == lib.ESIM_AD_EINVAL
+    assert so.esim_ad_events(None, None, 0, ctypes.byref(n), 0) == lib.ESIM_AD_EINVAL
+    assert so.esim_ad_denoised(None, None, None, 0) == lib.ESIM_AD_EINVAL
+    assert so.esim_ad_get_state(None, None, None, None) == lib.ESIM_AD_EINVAL
+    assert so.esim_ad_reset(None) == lib.ESIM_AD_EINVAL
+    so.esim_ad_destroy(None)
+    for code in range(-7, 1):
+        assert lib.status_string(code) not in ("unknown status", "")
+
+
+def test_init_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    so = lib.load_library()
+    cfg = lib.make_config(64, 48)
+    h = ctypes.c_void_p()
+    assert so.esim_ad_init(ctypes.byref(cfg), None, ctypes.byref(h)) == lib.ESIM_AD_ECUDA
+    assert h.value is None
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The library package never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2303_02608_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in txt.lower() or f == "__init__.py" and "oracle" not in \
+                    re.sub(r'""".*?"""', "", txt, flags=re.S).lower(), f
+
+
+# ----------------------------------------------------------------- GPU
+
+def _frame(W, H, device="cuda"):
+    import torch
+    g = torch.Generator().manual_seed(0)
+    return {"radiance": torch.rand(3, H, W, generator=g).add_(0.1).to(device),
+            "normal": torch.rand(3, H, W, generator=g).to(device),
+            "albedo": torch.rand(3, H, W, generator=g).to(device),
+            "depth": torch.rand(H, W, generator=g).add_(1).to(device)}
+
+
+@pytest.mark.gpu
+def test_alloc_failure_injection(lib):
+    """ESIM_AD_FAULT_ALLOC=k makes the k-th device allocation fail: init returns
+    ENOMEM, frees what it had, and the process stays usable."""
+    code = (
+        "import ctypes, torch, paper_2303_02608_gb300 as m\n"
+        "torch.cuda.init()\n"
+        "so = m.load_library(); cfg = m.make_config(64, 48); h = ctypes.c_void_p()\n"
+        "print(so.esim_ad_init(ctypes.byref(cfg), None, ctypes.byref(h)), h.value)\n")
+    for k in (1, 5, 12):
+        env = dict(os.environ, ESIM_AD_FAULT_ALLOC=str(k), PYTHONPATH=ROOT)
+        out = subprocess.check_output([sys.executable, "-c", code], env=env, cwd=ROOT).decode().split()
+        assert int(out[0]) == lib.ESIM_AD_ENOMEM and out[1] == "None"
+
+
+@pytest.mark.gpu
+def test_overflow_is_sticky_and_drain_reports_counts(lib):
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    import torch
+    W, H = 64, 48
+    sim = Simulator(SimConfig(width=W, height=H, radius=2, frames=2, contrast=0.05,
+                              mode=lib.ESIM_AD_EXHAUSTIVE, event_capacity=8))
+    f0 = _frame(W, H)
+    f1 = {k: v.clone() for k, v in f0.items()}
+    f1["radiance"] *= 3.0
+    sim.push(f0)
+    sim.push(f1)
+    st, n = lib.esim_ad_events(sim.ctx, 0, 0)
+    assert st == lib.ESIM_AD_EOVERFLOW and n > 8
+    with pytest.raises(lib.EsimError) as e:
+        sim.push(f0)
+    assert e.value.status == lib.ESIM_AD_ESTATE
+    sim.reset()   # clears the sticky state
+    sim.push(f0)
+    assert len(sim.events()) == 0
+    sim.close()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.gpu
+def test_drain_enospace_then_full_drain(lib):
+    from paper_2303_02608_gb300 import EVENT_DTYPE, SimConfig, Simulator
+    W, H = 40, 24
+    sim = Simulator(SimConfig(width=W, height=H, radius=1, frames=1, contrast=0.1,
+                              mode=lib.ESIM_AD_EXHAUSTIVE))
+    f0 = _frame(W, H)
+    f1 = {k: v.clone() for k, v in f0.items()}
+    f1["radiance"] *= 2.0
+    sim.push(f0)
+    sim.push(f1)
+    st, n = lib.esim_ad_events(sim.ctx, 0, 0)
+    assert st == lib.ESIM_AD_ENOSPACE and n >= W * H * 6  # ln 2 / 0.1 -> 6 crossings each
+    small = np.empty(3, EVENT_DTYPE)
+    st2, n2 = lib.esim_ad_events(sim.ctx, small.ctypes.data, 3)
+    assert st2 == lib.ESIM_AD_ENOSPACE and n2 == n     # nothing drained
+    ev = sim.events()
+    assert len(ev) == n and np.all(ev["frame"] == 1) and np.all(ev["polarity"] == 1)
+    assert len(sim.events()) == 0                      # drained
+    st3 = sim.stats()
+    assert st3["frames"] == 2 and st3["events"] == n and st3["regressions"] == 2 * W * H
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_host_frames_match_device_frames(lib):
+    """on_host frames (copied in by the library) give the same events as device frames."""
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    from scenes import Scene, SceneConfig
+    cfg = SceneConfig(kind="rects", width=96, height=64, frames=5, spp=4, seed=11, rgb=True,
+                      n_rects=8, bg_depth=10.0)
+    frames = Scene(cfg).sequence()
+    outs = []
+    for host in (False, True):
+        sim = Simulator(SimConfig(width=96, height=64, radius=3, frames=3, contrast=0.15))
+        evs = []
+        for fr in frames:
+            planes = {k: (fr[k].pin_memory() if host else fr[k].cuda())
+                      for k in ("radiance", "normal", "albedo", "depth")}
+            sim.push(planes)
+            evs.append(sim.events())
+        outs.append(np.concatenate(evs))
+        sim.close()
+    assert len(outs[0]) > 0 and np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.gpu
+def test_state_roundtrip_resume(lib):
+    """Checkpoint/resume: saving the model mid-sequence into a fresh context and
+    continuing gives the same events as an uninterrupted run."""
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    from scenes import Scene, SceneConfig
+    cfg = SceneConfig(kind="rects", width=80, height=48, frames=6, spp=4, seed=12, rgb=True,
+                      n_rects=8, bg_depth=10.0)
+    frames = [{k: v.cuda() for k, v in f.items() if k != "clean"} for f in Scene(cfg).sequence()]
+    sc = SimConfig(width=80, height=48, radius=2, frames=1, contrast=0.15)
+    a = Simulator(sc)
+    ev_a = []
+    for f in frames:
+        a.push(f)
+        ev_a.append(a.events())
+    b = Simulator(sc)
+    for f in frames[:3]:
+        b.push(f)
+        b.events()
+    st = b.get_state()
+    c = Simulator(sc)
+    c.push(frames[2])   # any frame: the ring (T = 1) and the model are replaced below
+    c.events()
+    c.set_state(st["l_last"], st["beta"], st["xc"])
+    ev_c = []
+    for f in frames[3:]:
+        c.push(f)
+        ev_c.append(c.events())
+    got = np.concatenate(ev_c)
+    want = np.concatenate(ev_a[3:])
+    assert len(want) > 0
+    assert np.array_equal(got[["x", "y", "polarity"]], want[["x", "y", "polarity"]])
+    for s in (a, b, c):
+        s.close()

@@ -1,0 +1,99 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Small cases run whole frames (several tiles, ragged right/bottom tiles, image
+borders, tiny and maximal windows); the 720p and 1080p workloads run at full
+size with the CUDA path in its benchmark launch configuration and the oracle
+evaluating a band of rows (it reads the full frames, so windows and borders
+are the real ones).
+"""
+import numpy as np
+import pytest
+
+from lockstep import run
+from oracle import ADAPTIVE, EXHAUSTIVE, Oracle, OracleConfig
+from scenes import Scene, SceneConfig, preset
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim(W, H, r, T, C, mode, rgb, capacity=1 << 22):
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    return Simulator(SimConfig(width=W, height=H, radius=r, frames=T, contrast=C, mode=mode, rgb=rgb,
+                               event_capacity=capacity))
+
+
+def _orc(W, H, r, T, C, mode, rgb):
+    return Oracle(OracleConfig(W, H, radius=r, frames=T, channels=3 if rgb else 1, mode=mode, contrast=C))
+
+
+def _case(scene_cfg, r, T, C, mode, n_frames, rows=None, strict=True):
+    sc = Scene(scene_cfg)
+    frames = sc.sequence(n_frames)
+    W, H, rgb = scene_cfg.width, scene_cfg.height, scene_cfg.rgb
+    sim = _sim(W, H, r, T, C, mode, rgb)
+    orc = _orc(W, H, r, T, C, mode, rgb)
+    rep = run(frames, sim, orc, C, rows=rows, strict=strict, adaptive=(mode == ADAPTIVE))
+    sim.close()
+    return rep
+
+
+@pytest.mark.parametrize("mode", [ADAPTIVE, EXHAUSTIVE])
+@pytest.mark.parametrize("strict", [True, False])
+def test_disc_64(mode, strict):
+    """64x64 disc, 8 frames, 7x7x3 window, C = 0.2, luminance (the tiny workload)."""
+    rep = _case(preset("disc64"), 3, 3, 0.2, mode, 8, strict=strict)
+    assert rep["events"] > 0 and rep["regressed"] > 0
+    total = 64 * 64 * 8
+    assert rep["flag_ambiguous"] + rep["event_ambiguous"] < 0.001 * total + 2
+
+
+@pytest.mark.parametrize("mode", [ADAPTIVE, EXHAUSTIVE])
+def test_ragged_rects(mode):
+    """77x45 RGB rectangles (ragged tiles both ways), 5x5x2 window."""
+    cfg = SceneConfig(kind="rects", width=77, height=45, frames=6, spp=4, seed=3, rgb=True,
+                      n_rects=8, bg_depth=10.0)
+    rep = _case(cfg, 2, 2, 0.15, mode, 6)
+    assert rep["regressed"] > 0
+
+
+@pytest.mark.parametrize("W,H,r,T", [(1, 1, 1, 1), (5, 3, 1, 2), (33, 9, 1, 1), (40, 70, 15, 4),
+                                     (70, 40, 15, 16)])
+def test_edge_shapes(W, H, r, T):
+    """Single pixel, smaller than a tile, radius 1, the maximum radius (15) and
+    temporal window (16)."""
+    cfg = SceneConfig(kind="rects", width=W, height=H, frames=max(3, min(T + 2, 18)), spp=2, seed=5,
+                      rgb=True, n_rects=6, bg_depth=10.0)
+    _case(cfg, r, T, 0.15, ADAPTIVE, cfg.frames)
+    _case(cfg, r, T, 0.15, EXHAUSTIVE, 3)
+
+
+def test_static_scene_no_events():
+    """Noise-free static input: no pixel is flagged after frame 0 and nothing fires."""
+    from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE
+    sc = Scene(preset("disc64", disc_velocity=(0.0, 0.0)))
+    c = sc.clean(0)
+    fr = {k: c[k].float().contiguous().cuda() for k in ("radiance", "normal", "albedo", "depth")}
+    for mode in (ADAPTIVE, EXHAUSTIVE):
+        sim = _sim(64, 64, 3, 3, 0.2, mode, False)
+        for _ in range(5):
+            sim.push(fr)
+        _, flags = sim.denoised()
+        if mode == ESIM_AD_ADAPTIVE:
+            assert int(flags.sum()) == 0
+        assert len(sim.events()) == 0
+        sim.close()
+
+
+@pytest.mark.parametrize("mode,rows", [(ADAPTIVE, (352, 368)), (EXHAUSTIVE, (352, 360)),
+                                       (ADAPTIVE, (0, 8)), (ADAPTIVE, (712, 720))])
+def test_720p_band(mode, rows):
+    """The paper-scale workload at full size (1280x720 RGB, 15x15x5, C = 0.15),
+    7 frames so the temporal window fills; oracle on a band of rows."""
+    rep = _case(preset("rects720p"), 7, 5, 0.15, mode, 7, rows=rows)
+    assert rep["regressed"] > 0
+
+
+def test_1080p_band():
+    """1920x1080, 1 spp-equivalent noise, 15x15x5, C = 0.1 (adaptive); band of rows."""
+    rep = _case(preset("rects1080p"), 7, 5, 0.1, ADAPTIVE, 6, rows=(536, 544))
+    assert rep["regressed"] > 0
