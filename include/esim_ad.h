@@ -200,6 +200,41 @@ typedef struct esim_ad_profile {
 esim_ad_status esim_ad_profile_enable(esim_ad_ctx* ctx, int on);
 esim_ad_status esim_ad_profile_get(esim_ad_ctx* ctx, esim_ad_profile* out);
 
+/*
+ * Write the events of one frame from a map of signed per-pixel event counts
+ * (p*n, as Eq. 1 emission produces), in canonical order (row, column, repeat),
+ * without allocating anything.  The paper has no counterpart: this is a
+ * deployment entry point.
+ *
+ * Who it is for: callers that cannot call cudaMalloc where they need events
+ * written - code inside their own CUDA stream capture under an allocation-free
+ * policy, latency-critical loops where cudaMalloc's implicit device-wide
+ * synchronisation would stall other work, and plugins of a host framework that
+ * owns all device memory.  It runs the same kernels as the context's event
+ * writer, with their scratch (about 96 KB) in a fixed array inside the library
+ * that every GPU loading the library keeps until the process exits.
+ *
+ * counts       [height][width] int32, device memory (input, caller-owned).
+ * frame        frame index written into each record.
+ * events       device memory for `capacity` records (output, caller-owned);
+ *              may be NULL when capacity == 0.
+ * total_device one uint64 in device memory (output): the number of events the
+ *              counts call for; records past `capacity` are dropped, so
+ *              *total_device > capacity means the buffer was too small.
+ * cuda_stream  cudaStream_t the work is enqueued on; nothing is synchronised.
+ * Limit: width * height <= 16,777,216 pixels (and each side <= 65535);
+ * larger frames return EINVAL.  EINVAL also for NULL counts/total_device or
+ * NULL events with capacity > 0; ECUDA if a CUDA call fails.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on a device share the one array, so calls whose work
+ * overlaps on the GPU (different streams without ordering) race; the array's
+ * control block is cleared at the start of each call.
+ */
+esim_ad_status esim_ad_write_events_noalloc(const int32_t* counts, int32_t width, int32_t height,
+                                            uint32_t frame, esim_ad_event* events, uint64_t capacity,
+                                            uint64_t* total_device, void* cuda_stream);
+
 /* Restart the sequence at frame 0 and clear events, counters and sticky errors. */
 esim_ad_status esim_ad_reset(esim_ad_ctx* ctx);
 

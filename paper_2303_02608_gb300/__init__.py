@@ -37,6 +37,7 @@ EXPORTS = (
     "esim_ad_init", "esim_ad_push_frame", "esim_ad_events", "esim_ad_denoised",
     "esim_ad_get_state", "esim_ad_set_state", "esim_ad_reset", "esim_ad_stats_get",
     "esim_ad_destroy", "esim_ad_status_string", "esim_ad_profile_enable", "esim_ad_profile_get",
+    "esim_ad_write_events_noalloc",
 )
 
 
@@ -115,6 +116,9 @@ def load_library():
     lib.esim_ad_profile_enable.argtypes = [P, ctypes.c_int]
     lib.esim_ad_profile_get.restype = st
     lib.esim_ad_profile_get.argtypes = [P, ctypes.POINTER(esim_ad_profile)]
+    lib.esim_ad_write_events_noalloc.restype = st
+    lib.esim_ad_write_events_noalloc.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, P,
+                                                 ctypes.c_uint64, P, P]
     lib.esim_ad_status_string.restype = ctypes.c_char_p
     lib.esim_ad_status_string.argtypes = [st]
     _lib = lib
@@ -214,6 +218,14 @@ def esim_ad_profile_get(ctx: int) -> dict:
     return {"launches": {k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
             "ms": {k: float(p.ms[i]) for i, k in enumerate(KERNEL_CLASSES)},
             "neighbours": int(p.neighbours), "regressions": int(p.regressions)}
+
+
+def esim_ad_write_events_noalloc(counts: int, width: int, height: int, frame: int, events: int,
+                                 capacity: int, total_device: int, cuda_stream: int = 0) -> int:
+    """Allocation-free event writer (device pointers in and out); returns the status."""
+    return load_library().esim_ad_write_events_noalloc(
+        ctypes.c_void_p(counts or None), width, height, frame, ctypes.c_void_p(events or None),
+        ctypes.c_uint64(capacity), ctypes.c_void_p(total_device or None), ctypes.c_void_p(cuda_stream or None))
 
 
 def esim_ad_destroy(ctx: int) -> None:
