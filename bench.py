@@ -318,8 +318,7 @@ def run_ours(args):
         "kernel_ms_per_step": {k: round(v / K, 4) for k, v in prof_a["ms"].items()},
         "roofline": roof,
         "hbm_path": hbm_path,
-        "gpu_launches": int(prof_a["launches"]["ingest_test"] + prof_a["launches"]["wlr_emit"]
-                            + 2 * prof_a["launches"]["event_write"]),
+        "gpu_launches": int(prof_a["kernels"]),
         "clocks": clocks,
     }
     if rank == 0 and not args.no_e2e:

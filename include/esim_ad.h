@@ -185,13 +185,16 @@ esim_ad_status esim_ad_set_state(esim_ad_ctx* ctx, const float* l_last, const fl
  * instrumentation).  While enabled, every kernel launch of esim_ad_push_frame
  * is bracketed by CUDA events on the context's stream.  Classes: 0 = ingest +
  * Proposition-1 test, 1 = weighted local regression + emission, 2 = ordered
- * event writer.  `neighbours` counts (pixel, window neighbour) pairs
+ * event writer (class 1 covers both regression launches of an adaptive
+ * frame).  `kernels` counts every kernel launch the library issued while
+ * enabled.  `neighbours` counts (pixel, window neighbour) pairs
  * accumulated by the regression since init/reset, the unit of its arithmetic.
  * esim_ad_profile_enable(ctx, 1) clears the timings; esim_ad_profile_get
  * synchronises and returns totals since then.
  */
 typedef struct esim_ad_profile {
-    uint64_t launches[3];    /* launches per kernel class                        */
+    uint64_t launches[3];    /* timed launch groups per kernel class              */
+    uint64_t kernels;        /* kernel launches issued since enabled             */
     double   ms[3];          /* summed device time per class, milliseconds       */
     uint64_t neighbours;     /* (pixel, neighbour) pairs regressed since init     */
     uint64_t regressions;    /* pixels regressed since init/reset                */

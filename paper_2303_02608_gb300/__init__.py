@@ -65,7 +65,7 @@ class esim_ad_stats(ctypes.Structure):
 
 
 class esim_ad_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64 * 3), ("ms", ctypes.c_double * 3),
+    _fields_ = [("launches", ctypes.c_uint64 * 3), ("kernels", ctypes.c_uint64), ("ms", ctypes.c_double * 3),
                 ("neighbours", ctypes.c_uint64), ("regressions", ctypes.c_uint64)]
 
 
@@ -217,7 +217,7 @@ def esim_ad_profile_get(ctx: int) -> dict:
     _check(load_library().esim_ad_profile_get(ctypes.c_void_p(ctx), ctypes.byref(p)), "esim_ad_profile_get")
     return {"launches": {k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
             "ms": {k: float(p.ms[i]) for i, k in enumerate(KERNEL_CLASSES)},
-            "neighbours": int(p.neighbours), "regressions": int(p.regressions)}
+            "kernels": int(p.kernels), "neighbours": int(p.neighbours), "regressions": int(p.regressions)}
 
 
 def esim_ad_write_events_noalloc(counts: int, width: int, height: int, frame: int, events: int,

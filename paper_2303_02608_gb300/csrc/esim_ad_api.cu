@@ -60,6 +60,10 @@ struct esim_ad_ctx {
     size_t N = 0;
     int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_chunks = 0;
     int smem_bytes = 0;
+    int nbuf = 2;
+    int wlr_grid = 0;
+    int sparse_grid = 0;
+    uint32_t sparse_max = 0;     // adaptive frames with at most this many flagged pixels use the sparse kernel
     float4* ring = nullptr;
     float4* state = nullptr;
     float* alpha = nullptr;
@@ -68,6 +72,7 @@ struct esim_ad_ctx {
     uint32_t* tile_queue = nullptr;
     int32_t* tile_nflag = nullptr;
     uint8_t* tile_pix = nullptr;
+    uint32_t* flag_list = nullptr;
     uint32_t* chunk_cnt = nullptr;
     unsigned long long* chunk_off = nullptr;
     esim_ad_event* events = nullptr;
@@ -82,6 +87,7 @@ struct esim_ad_ctx {
     std::vector<cudaEvent_t> prof_events;      // pool, pairs (start, stop)
     std::vector<int> prof_class;               // class of each recorded pair
     size_t prof_used = 0;                      // pairs recorded
+    uint64_t prof_kernels = 0;                 // kernel launches while profiling
     uint64_t t = 0;
     esim_ad_status sticky = ESIM_AD_OK;
 };
@@ -120,7 +126,7 @@ esim_ad_status check_config(const esim_ad_config* c)
 void release(esim_ad_ctx* c)
 {
     void* ptrs[] = {c->ring, c->state, c->alpha, c->flag, c->nev, c->tile_queue, c->tile_nflag,
-                    c->tile_pix, c->chunk_cnt, c->chunk_off, c->events, c->ctrl,
+                    c->tile_pix, c->flag_list, c->chunk_cnt, c->chunk_off, c->events, c->ctrl,
                     c->staging[0], c->staging[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -232,7 +238,14 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     c->tiles_y = (c->H + kTileY - 1) / kTileY;
     c->n_tiles = c->tiles_x * c->tiles_y;
     c->n_chunks = (int)((c->N + kChunk - 1) / kChunk);
-    c->smem_bytes = (int)wlr_smem_bytes(cfg->radius);
+    int max_smem_sm = 0, num_sms = 0;
+    if (cudaDeviceGetAttribute(&max_smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return ESIM_AD_ECUDA;
+    }
+    c->smem_bytes = (int)wlr_smem_bytes(cfg->radius, max_smem_sm, &c->nbuf);
     const size_t N = c->N, T = (size_t)cfg->frames;
     struct {
         void** p;
@@ -246,6 +259,7 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         {(void**)&c->tile_queue, (size_t)c->n_tiles * sizeof(uint32_t)},
         {(void**)&c->tile_nflag, (size_t)c->n_tiles * sizeof(int32_t)},
         {(void**)&c->tile_pix, (size_t)c->n_tiles * kTilePix},
+        {(void**)&c->flag_list, N * sizeof(uint32_t)},
         {(void**)&c->chunk_cnt, (size_t)c->n_chunks * sizeof(uint32_t)},
         {(void**)&c->chunk_off, (size_t)c->n_chunks * sizeof(unsigned long long)},
         {(void**)&c->events, (size_t)cfg->event_capacity * sizeof(esim_ad_event)},
@@ -272,6 +286,14 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         release(c);
         delete c;
         return ESIM_AD_ECUDA;
+    }
+    c->wlr_grid = wlr_grid(c->smem_bytes, num_sms);
+    c->sparse_grid = wlr_sparse_grid(num_sms);
+    // default: 16 pixels per work item, 8 items per staged CTA; ESIM_AD_SPARSE_MAX
+    // overrides it (0: always the tile-staged kernel; large: always sparse)
+    c->sparse_max = (uint32_t)c->wlr_grid * 128u;
+    if (const char* e = getenv("ESIM_AD_SPARSE_MAX")) {
+        if (*e) c->sparse_max = (uint32_t)strtoul(e, nullptr, 10);
     }
     *out = c;
     return ESIM_AD_OK;
@@ -358,10 +380,14 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
     ip.tile_queue = c->tile_queue;
     ip.tile_nflag = c->tile_nflag;
     ip.tile_pix = c->tile_pix;
+    ip.chunk_cnt = c->chunk_cnt;
+    ip.n_chunks = c->n_chunks;
+    ip.flag_list = c->flag_list;
     ip.ctrl = c->ctrl;
     {
         ProfScope ps(c, 0);
         if (launch_ingest(ip, c->n_tiles, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        c->prof_kernels += 1;
     }
     if (slot >= 0 && cudaEventRecord(c->ev_consumed[slot], c->stream) != cudaSuccess)
         return ESIM_AD_ECUDA;
@@ -374,6 +400,8 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
     wp.t = t;
     wp.n_tau = (int)((c->t + 1) < (uint64_t)c->cfg.frames ? (c->t + 1) : (uint64_t)c->cfg.frames);
     wp.tiles_x = c->tiles_x;
+    wp.n_tiles = c->n_tiles;
+    wp.nbuf = c->nbuf;
     wp.dense = adaptive_test ? 0 : 1;
     wp.init = c->t == 0 ? 1 : 0;
     wp.sw = kTileX + 2 * c->cfg.radius;
@@ -391,11 +419,23 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
     wp.tile_queue = c->tile_queue;
     wp.tile_nflag = c->tile_nflag;
     wp.tile_pix = c->tile_pix;
+    wp.chunk_cnt = c->chunk_cnt;
+    wp.chunk_off = c->chunk_off;
+    wp.n_chunks = c->n_chunks;
+    wp.emit_events = c->t > 0 ? 1 : 0;
+    wp.sparse_max = c->sparse_max;
+    wp.flag_list = c->flag_list;
     wp.ctrl = c->ctrl;
     {
         ProfScope ps(c, 1);
-        if (launch_wlr(c->tmap, wp, c->n_tiles, c->smem_bytes, c->stream) != cudaSuccess)
+        const int grid = wp.dense ? (c->n_tiles < c->wlr_grid ? c->n_tiles : c->wlr_grid) : c->wlr_grid;
+        if (launch_wlr(c->tmap, wp, grid, c->smem_bytes, c->stream) != cudaSuccess)
             return ESIM_AD_ECUDA;
+        // adaptive frames: the sparse kernel takes the frame when few pixels are
+        // flagged; each of the two launches returns at once on the other's frames
+        if (!wp.dense && launch_wlr_sparse(wp, c->sparse_grid, c->stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+        c->prof_kernels += wp.dense ? 1 : 2;
     }
 
     if (c->t > 0) {
@@ -411,7 +451,8 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
         ep.capacity = c->cfg.event_capacity;
         ep.ctrl = c->ctrl;
         ProfScope ps(c, 2);
-        if (launch_events(ep, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        if (launch_event_write(ep, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        c->prof_kernels += 1;
     }
     if (slot >= 0) {
         // the caller may reuse its host buffers once its copies are done
@@ -477,7 +518,7 @@ esim_ad_status esim_ad_get_state(esim_ad_ctx* c, float* l_last, float* beta, flo
     }
     for (size_t i = 0; i < N; ++i) {
         const float4 b0 = h[i], b1 = h[N + i], x0 = h[2 * N + i], x1 = h[3 * N + i];
-        if (l_last) l_last[i] = b1.w;
+        if (l_last) l_last[i] = x1.w;
         if (beta) {
             float* b = beta + 7 * i;
             b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
@@ -507,7 +548,7 @@ esim_ad_status esim_ad_set_state(esim_ad_ctx* c, const float* l_last, const floa
         return ESIM_AD_ECUDA;
     }
     for (size_t i = 0; i < N; ++i) {
-        if (l_last) h[N + i].w = l_last[i];
+        if (l_last) h[3 * N + i].w = l_last[i];
         if (beta) {
             const float* b = beta + 7 * i;
             h[i] = make_float4(b[0], b[1], b[2], b[3]);
@@ -515,9 +556,13 @@ esim_ad_status esim_ad_set_state(esim_ad_ctx* c, const float* l_last, const floa
         }
         if (xc) {
             const float* x = xc + 7 * i;
+            const float lw = h[3 * N + i].w;
             h[2 * N + i] = make_float4(x[0], x[1], x[2], x[3]);
-            h[3 * N + i] = make_float4(x[4], x[5], x[6], 0.0f);
+            h[3 * N + i] = make_float4(x[4], x[5], x[6], lw);
         }
+        // keep sigma = beta . x^c consistent with the stored model
+        const float4 x0 = h[2 * N + i], x1 = h[3 * N + i];
+        h[N + i].w = dot7(h[i], h[N + i], x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z);
     }
     esim_ad_status st = ESIM_AD_OK;
     if (cudaMemcpyAsync(c->state, h, 4 * N * sizeof(float4), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
@@ -560,6 +605,7 @@ esim_ad_status esim_ad_profile_enable(esim_ad_ctx* c, int on)
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
     c->prof_on = on != 0;
     c->prof_used = 0;
+    c->prof_kernels = 0;
     return ESIM_AD_OK;
 }
 
@@ -577,6 +623,7 @@ esim_ad_status esim_ad_profile_get(esim_ad_ctx* c, esim_ad_profile* out)
         out->launches[c->prof_class[k]] += 1;
         out->ms[c->prof_class[k]] += ms;
     }
+    out->kernels = c->prof_kernels;
     out->neighbours = h.neighbours;
     out->regressions = h.regressions;
     return ESIM_AD_OK;

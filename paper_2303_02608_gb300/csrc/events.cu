@@ -1,9 +1,11 @@
 // Ordered event writer (Eq. 1 records at fixed frame times).
 //
-// The regression kernel leaves a signed per-pixel event count p*n in a map.
-// Two launches turn it into event records in canonical order (row, column,
-// repeat) without sorting and without atomics on the output position, so the
-// output is deterministic:
+// The regression kernel leaves a signed per-pixel event count p*n in a map
+// and, in the simulator's own path, already sums |p*n| per 2048-pixel chunk
+// and scans the chunk counts (its last CTA), so only the write launch runs.
+// The stand-alone writer runs both launches below.  Either way the records
+// come out in canonical order (row, column, repeat) without sorting and
+// without atomics on the output position, so the output is deterministic:
 //   1. count: each 2048-pixel chunk sums |p*n|; the last CTA to finish (ticket
 //      from an atomic counter, after a release fence) scans the chunk counts
 //      into global offsets and advances the event total.  No CTA waits on
@@ -12,6 +14,7 @@
 //      offset.  Records past the buffer capacity are dropped and the sticky
 //      overflow bit is set; the total still counts them.
 #include "internal.h"
+#include "block_scan.cuh"
 
 namespace esim {
 
@@ -19,29 +22,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPer = kChunk / kThreads;  // 8 pixels per thread
-
-__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& total)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[wid] = x;
-    __syncthreads();
-    int base = 0;
-    total = 0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-        const int c = s_warp[w];
-        base += (w < wid) ? c : 0;
-        total += c;
-    }
-    __syncthreads();
-    return base + x - v;
-}
 
 __global__ void __launch_bounds__(kThreads) event_count_kernel(EventParams p)
 {
@@ -83,6 +63,7 @@ __global__ void __launch_bounds__(kThreads) event_count_kernel(EventParams p)
 __global__ void __launch_bounds__(kThreads) event_write_kernel(EventParams p)
 {
     __shared__ int s_warp[kThreads / 32];
+    if (p.chunk_cnt[blockIdx.x] == 0u) return;   // no events in this chunk
     const long long p0 = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * kPer;
     int v[kPer];
     int c = 0;
@@ -119,6 +100,12 @@ __global__ void __launch_bounds__(kThreads) event_write_kernel(EventParams p)
 }
 
 }  // namespace
+
+cudaError_t launch_event_write(const EventParams& p, cudaStream_t s)
+{
+    event_write_kernel<<<p.n_chunks, kThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_events(const EventParams& p, cudaStream_t s)
 {

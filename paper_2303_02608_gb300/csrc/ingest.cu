@@ -9,11 +9,13 @@
 // The image-coordinate part of x^c - xhat^c is zero (same pixel), so only the
 // seven feature slopes enter.  Flagged pixels of the CTA's 32x8 tile are
 // compacted in raster order with warp ballots and a block prefix; the tile is
-// appended to the active-tile queue with one atomic per tile.
+// appended to the active-tile queue, and its pixels to a frame-wide flagged
+// list, with one atomic each per tile.
 //
-// Memory traffic per pixel (fp32 RGB input): 44 B in (radiance 12, normal 12,
-// albedo 12, depth 4; variance is not read), 32 B ring write, 64 B state read
-// (adaptive, t >= 1), 1 B flag + 4 B event-count clear.
+// Memory traffic per pixel (fp32 RGB input): 40 B in (radiance 12, normal 12,
+// albedo 12, depth 4; variance is not read), 32 B ring write, 32 B model read
+// (beta and sigma = beta . x^c; adaptive, t >= 1), 1 B flag + 4 B event-count
+// clear.
 #include "internal.h"
 
 namespace esim {
@@ -47,23 +49,20 @@ __global__ void __launch_bounds__(kTilePix) ingest_test_kernel(IngestParams p)
         p.ring[(size_t)(2 * p.slot) * N + i] = make_float4(yv, n0, n1, n2);
         p.ring[(size_t)(2 * p.slot + 1) * N + i] = make_float4(d, a0, a1, a2);
         if (p.test) {
+            // beta^T (x^c - xhat) = sigma - beta . xhat, sigma = beta . x^c kept in the model
             const float4 b0 = p.state[i];
             const float4 b1 = p.state[N + i];
-            const float4 c0 = p.state[2 * N + i];
-            const float4 c1 = p.state[3 * N + i];
-            float s = b0.x * (c0.x - n0);
-            s = fmaf(b0.y, c0.y - n1, s);
-            s = fmaf(b0.z, c0.z - n2, s);
-            s = fmaf(b0.w, c0.w - d, s);
-            s = fmaf(b1.x, c1.x - a0, s);
-            s = fmaf(b1.y, c1.y - a1, s);
-            s = fmaf(b1.z, c1.z - a2, s);
+            const float s = b1.w - dot7(b0, b1, n0, n1, n2, d, a0, a1, a2);
             flag = (s * s >= p.C * p.C) ? 1 : 0;
         } else {
             flag = 1;
         }
         p.flag[i] = (uint8_t)flag;
         p.nev[i] = 0;
+    }
+    {
+        const int g = blockIdx.x * kTilePix + threadIdx.x;
+        if (g < p.n_chunks) p.chunk_cnt[g] = 0u;
     }
     if (!p.test) return;  // the regression walks every tile densely
 
@@ -79,16 +78,20 @@ __global__ void __launch_bounds__(kTilePix) ingest_test_kernel(IngestParams p)
         base += (w < ly) ? c : 0;
         total += c;
     }
-    if (flag) {
-        const int pos = base + __popc(ballot & ((1u << lx) - 1u));
-        p.tile_pix[(size_t)tile * kTilePix + pos] = (uint8_t)threadIdx.x;
-    }
+    __shared__ uint32_t s_list_base;
     if (threadIdx.x == 0) {
         p.tile_nflag[tile] = total;
         if (total > 0) {
             const uint32_t slot = atomicAdd(&p.ctrl->tile_count, 1u);
             p.tile_queue[slot] = (uint32_t)tile;
+            s_list_base = atomicAdd(&p.ctrl->flag_total, (uint32_t)total);
         }
+    }
+    __syncthreads();
+    if (flag) {
+        const int pos = base + __popc(ballot & ((1u << lx) - 1u));
+        p.tile_pix[(size_t)tile * kTilePix + pos] = (uint8_t)threadIdx.x;
+        p.flag_list[s_list_base + pos] = (uint32_t)((size_t)y * p.W + x);
     }
 }
 

@@ -28,7 +28,8 @@ constexpr uint32_t kStatusTimeout = 2u;
 struct Ctrl {
     uint32_t tile_count;            // active tiles queued by the test kernel
     uint32_t chunk_done;            // ticket of the event-count kernel
-    uint32_t pad0, pad1;
+    uint32_t work_next;             // next work item of the persistent regression
+    uint32_t flag_total;            // pixels flagged by the test kernel this frame
     unsigned long long ev_total;    // events produced since the last drain
     unsigned long long ev_cum;      // events since init/reset
     unsigned long long regressions; // pixels regressed since init/reset
@@ -41,8 +42,25 @@ constexpr size_t kCtrlPerFrameBytes = 16;
 // Ring of the last T frames: float4 planes [2T][H][W]; plane 2*slot holds
 // (y, normal xyz), plane 2*slot+1 holds (depth, albedo rgb).
 // Model state: float4 planes [4][H][W]:
-//   0: beta (normal xyz, depth)   1: beta (albedo rgb), L_last
-//   2: x^c (normal xyz, depth)    3: x^c (albedo rgb), 0
+//   0: beta (normal xyz, depth)   1: beta (albedo rgb), sigma = beta . x^c
+//   2: x^c (normal xyz, depth)    3: x^c (albedo rgb), L_last
+// The test kernel reads planes 0-1 only: beta^T (x^c - xhat) = sigma - beta . xhat.
+
+// beta . x over the seven features, in one fixed fma order so that the value
+// stored at an event and the value recomputed by the test agree bit for bit
+// when the features have not moved.
+__host__ __device__ __forceinline__ float dot7(const float4 b0, const float4 b1, float n0, float n1,
+                                               float n2, float d, float a0, float a1, float a2)
+{
+    float s = b0.x * n0;
+    s = fmaf(b0.y, n1, s);
+    s = fmaf(b0.z, n2, s);
+    s = fmaf(b0.w, d, s);
+    s = fmaf(b1.x, a0, s);
+    s = fmaf(b1.y, a1, s);
+    s = fmaf(b1.z, a2, s);
+    return s;
+}
 
 struct IngestParams {
     const float* rad;      // [C][H][W]
@@ -61,11 +79,15 @@ struct IngestParams {
     uint32_t* tile_queue;
     int32_t* tile_nflag;
     uint8_t* tile_pix;
+    uint32_t* chunk_cnt;   // per event chunk, cleared here for the regression's counts
+    int n_chunks;
+    uint32_t* flag_list;   // frame-wide list of flagged pixel indices (tile order)
     Ctrl* ctrl;
 };
 
 struct WlrParams {
-    int W, H, r, T, t, n_tau, tiles_x;
+    int W, H, r, T, t, n_tau, tiles_x, n_tiles;
+    int nbuf;              // staged frames in flight per CTA (2 or 3)
     int dense;             // 1: every tile and pixel; 0: tiles from the queue
     int init;              // 1: frame 0 (initialise models, no events)
     int sw, sh;            // staged tile: (32 + 2r) x (8 + 2r) pixels
@@ -81,6 +103,12 @@ struct WlrParams {
     const uint32_t* tile_queue;
     const int32_t* tile_nflag;
     const uint8_t* tile_pix;
+    uint32_t* chunk_cnt;             // events per 2048-pixel chunk (atomically summed)
+    unsigned long long* chunk_off;   // exclusive offsets, written by the last CTA
+    int n_chunks;
+    int emit_events;                 // 0 on frame 0 (no events)
+    uint32_t sparse_max;             // queue mode: at most this many flagged pixels -> sparse kernel
+    const uint32_t* flag_list;       // flagged pixel indices, flag_total of them
     Ctrl* ctrl;
 };
 
@@ -99,9 +127,13 @@ struct EventParams {
 
 cudaError_t launch_ingest(const IngestParams& p, int n_tiles, cudaStream_t s);
 cudaError_t wlr_prepare(int smem_bytes);
-size_t wlr_smem_bytes(int r);
+size_t wlr_smem_bytes(int r, int max_smem_per_sm, int* nbuf);
+int wlr_grid(int smem_bytes, int num_sms);
+int wlr_sparse_grid(int num_sms);
 cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, int grid, int smem_bytes,
                        cudaStream_t s);
+cudaError_t launch_wlr_sparse(const WlrParams& p, int grid, cudaStream_t s);
 cudaError_t launch_events(const EventParams& p, cudaStream_t s);
+cudaError_t launch_event_write(const EventParams& p, cudaStream_t s);
 
 }  // namespace esim

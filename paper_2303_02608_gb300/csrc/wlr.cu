@@ -1,11 +1,13 @@
 // Weighted local regression (Eqs. 3-5) with fused event emission (Eq. 1).
 //
-// One CTA owns a 32x8 pixel tile.  For each frame tau of the temporal window
-// t-T+1..t it stages the tile plus an r-pixel halo of that frame's ring slot
-// ((32+2r) x (8+2r) pixels x 2 float4 half-planes) in shared memory with one
-// 4-D TMA load, double-buffered over tau on two mbarriers.  Pixels outside the
-// image arrive zero-filled and are never read: each centre's offset range is
-// clipped to the image instead.
+// Work unit: a 32x8 pixel tile.  For each frame tau of the temporal window
+// t-T+1..t the tile plus an r-pixel halo of that frame's ring slot
+// ((32+2r) x (8+2r) pixels x 2 float4 half-planes) is staged in shared memory
+// by one 4-D TMA load.  CTAs are persistent: they pull work items (tiles, or
+// chunks of a tile's flagged pixels) from a counter and keep up to three staged
+// frames in flight, so the copy of the next frame or item overlaps the
+// arithmetic on the current one.  Pixels outside the image arrive zero-filled and are never
+// read: each centre's offset range is clipped to the image instead.
 //
 // Each regressed pixel is owned by g lanes (g = 1 when its tile is densely
 // flagged, up to 32 when it holds few flagged pixels); the lanes split the
@@ -23,6 +25,7 @@
 // writer), L_last moves by p n C and the model (beta, x^c) is replaced by the
 // new fit (Fig. 1: the model is kept until a new event).  Frame 0 only
 // initialises L_last = alpha and the model.
+#include "block_scan.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -42,7 +45,7 @@ struct Acc {
 
 // One neighbour: y and the raw features (h0 = y, normal xyz; h1 = depth, albedo rgb).
 __device__ __forceinline__ void accumulate(Acc& a, const float4 h0, const float4 h1, float u1,
-                                           float u2, float en0, const float (&sf)[7],
+                                           float u2, float en0, const float* __restrict__ sf,
                                            const float (&cf)[7])
 {
     float u[NZ];
@@ -130,8 +133,123 @@ __device__ __forceinline__ void solve(Acc& a, const float (&s2)[NZ], float ridge
     for (int i = 0; i < NZ; ++i) theta[i] *= dsc[i];
 }
 
+// Eq. 1 at a fixed frame time, and the model update of Fig. 1.
+__device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const float (&theta)[NZ],
+                                     const float* __restrict__ sf)
+{
+    const size_t N = (size_t)p.W * p.H;
+    const size_t i = (size_t)cy * p.W + cx;
+    const float alpha = theta[0];
+    float bf[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) bf[j] = theta[3 + j] * sf[j];
+    p.alpha[i] = alpha;
+    float L;
+    if (p.init) {
+        L = alpha;
+    } else {
+        L = p.state[3 * N + i].w;
+        const float dl = alpha - L;
+        const float n = floorf(fabsf(dl) / p.C);
+        if (!(n >= 1.0f)) return;  // no event: keep the model
+        const float pol = dl > 0.0f ? 1.0f : -1.0f;
+        L = fmaf(pol * n, p.C, L);
+        p.nev[i] = (int32_t)(pol * n);
+        atomicAdd(&p.chunk_cnt[i / kChunk], (uint32_t)n);
+    }
+    const int slot = p.t % p.T;
+    const float4 x0 = p.ring[(size_t)(2 * slot) * N + i];
+    const float4 x1 = p.ring[(size_t)(2 * slot + 1) * N + i];
+    const float4 b0 = make_float4(bf[0], bf[1], bf[2], bf[3]);
+    float4 b1 = make_float4(bf[4], bf[5], bf[6], 0.0f);
+    b1.w = dot7(b0, b1, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w);
+    p.state[i] = b0;
+    p.state[N + i] = b1;
+    p.state[2 * N + i] = make_float4(x0.y, x0.z, x0.w, x1.x);
+    p.state[3 * N + i] = make_float4(x1.y, x1.z, x1.w, L);
+}
+
+// End of a regression launch: add this CTA's work counters, record a timeout,
+// and, when events are emitted, take a ticket; the last CTA to finish scans
+// the per-chunk event counts into output offsets (no CTA waits on another).
+__device__ __forceinline__ void finish(const WlrParams& p, unsigned long long pairs,
+                                       unsigned long long pix, bool timed_out)
+{
+    __shared__ int s_timeout, s_last;
+    __shared__ int s_warp[8];
+    if (threadIdx.x == 0) {
+        s_timeout = 0;
+        s_last = 0;
+    }
+    __syncthreads();
+    if (timed_out) s_timeout = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (pairs) atomicAdd(&p.ctrl->neighbours, pairs);
+        if (pix) atomicAdd(&p.ctrl->regressions, pix);
+        if (s_timeout) atomicOr(&p.ctrl->status, kStatusTimeout);
+        if (p.emit_events) {
+            __threadfence();
+            const uint32_t ticket = atomicAdd(&p.ctrl->chunk_done, 1u);
+            s_last = (ticket == gridDim.x - 1u) ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long running = *(volatile unsigned long long*)&p.ctrl->ev_total;
+    const unsigned long long start = running;
+    for (int base = 0; base < p.n_chunks; base += blockDim.x) {
+        const int j = base + (int)threadIdx.x;
+        const int v = (j < p.n_chunks) ? (int)*(volatile uint32_t*)&p.chunk_cnt[j] : 0;
+        int seg;
+        const int off = block_exclusive_scan(v, s_warp, seg);
+        if (j < p.n_chunks) p.chunk_off[j] = running + (unsigned long long)off;
+        running += (unsigned long long)seg;
+    }
+    if (threadIdx.x == 0) {
+        p.ctrl->ev_total = running;
+        p.ctrl->ev_cum += running - start;
+    }
+}
+
 }  // namespace
 
+// Per-stage metadata published by the producer thread with each staged frame.
+struct StageInfo {
+    int tile;   // tile index, or -1: no more work (end of the CTA's stream)
+    int k;      // position in the temporal window: tau = t - k
+    int first;  // first entry of the tile's pixel list in this work item
+    int count;  // pixels in this work item
+};
+
+// Per-CTA shared-memory layout (after 128-byte alignment):
+//   nbuf stage buffers, each 2 half-planes of (32+2r) x (8+2r) float4
+//   full[nbuf] mbarriers, released[nbuf] counters, info[nbuf], window table [(2r+1)^2] float4
+struct SmemLayout {
+    int buf_bytes, nbuf, table_off, bar_off, info_off, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int r, int nbuf)
+{
+    SmemLayout L;
+    const int stage = 2 * (kTileX + 2 * r) * (kTileY + 2 * r) * 16;
+    L.buf_bytes = (stage + 127) & ~127;
+    L.nbuf = nbuf;
+    L.bar_off = nbuf * L.buf_bytes;
+    L.info_off = L.bar_off + 2 * nbuf * 8;
+    L.table_off = (L.info_off + nbuf * (int)sizeof(StageInfo) + 15) & ~15;
+    L.total = L.table_off + (2 * r + 1) * (2 * r + 1) * 16 + 128;  // + alignment slack
+    return L;
+}
+
+// Persistent regression kernel.  Each CTA pulls work items from a counter
+// (every tile in dense mode, chunks of the active-tile queue otherwise) and
+// keeps up to nbuf staged frames in flight, each a (work item, tau) pair
+// published in `info` and landed by TMA on full[b].  Every warp consumes every
+// stage in order and then counts itself out of the buffer; the warp that
+// releases a buffer last issues that buffer's next copy at once, so no warp
+// waits for another and copies start as early as possible.
 template <bool kDense>
 __global__ void __launch_bounds__(kTilePix, 2)
     wlr_kernel(const __grid_constant__ CUtensorMap tmap, const WlrParams p)
@@ -139,94 +257,177 @@ __global__ void __launch_bounds__(kTilePix, 2)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations must be 128-byte aligned; the allocation has 128 bytes of slack
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    const SmemLayout L = smem_layout(p.r, p.nbuf);
     const int plane = p.sw * p.sh;                      // float4 per half-plane
     const uint32_t stage_bytes = (uint32_t)(2 * plane * 16);
-    const int buf_bytes = (int)((stage_bytes + 127u) & ~127u);
-    float4* const buf0 = reinterpret_cast<float4*>(smem);
-    float4* const buf1 = reinterpret_cast<float4*>(smem + buf_bytes);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * buf_bytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+    int* released = reinterpret_cast<int*>(full + L.nbuf);
+    StageInfo* info = reinterpret_cast<StageInfo*>(smem + L.info_off);
+    float4* table = reinterpret_cast<float4*>(smem + L.table_off);
+    const int lane = threadIdx.x & 31;
+    if (!kDense && *(volatile uint32_t*)&p.ctrl->flag_total <= p.sparse_max && p.sparse_max > 0)
+        return;  // the sparse kernel's frame
+    const int n_work = kDense ? p.n_tiles : (int)*(volatile uint32_t*)&p.ctrl->tile_count;
+    const int side = 2 * p.r + 1;
+    const int nq = side * side;
+    const float spx = p.s_coord_px;
 
-    uint32_t tile;
-    int npix;
-    if (kDense) {
-        tile = blockIdx.x;
-        npix = kTilePix;
-    } else {
-        if (blockIdx.x >= *(volatile uint32_t*)&p.ctrl->tile_count) return;
-        tile = p.tile_queue[blockIdx.x];
-        npix = p.tile_nflag[tile];
+    // window walk table for lanes that split one interior pixel's window:
+    // (smem offset, u_dx, u_dy, -(u_dx^2 + u_dy^2)) per offset
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int ox = q % side - p.r, oy = q / side - p.r;
+        const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+        table[q] = make_float4(__int_as_float(oy * p.sw + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
     }
-    const int tx0 = (int)(tile % (uint32_t)p.tiles_x) * kTileX;
-    const int ty0 = (int)(tile / (uint32_t)p.tiles_x) * kTileY;
-
-    // lanes per regressed pixel
-    int lg = 0;  // log2(g)
-    if (!kDense) lg = npix > 128 ? 0 : npix > 64 ? 1 : npix > 32 ? 2 : npix > 16 ? 3 : npix > 8 ? 4 : 5;
-    const int g = 1 << lg;
-    const int item = threadIdx.x >> lg;
-    const int sub = threadIdx.x & (g - 1);
-    bool active = item < npix;
-    const int lidx = kDense ? (int)threadIdx.x
-                            : (active ? (int)p.tile_pix[(size_t)tile * kTilePix + item] : 0);
-    const int lx = lidx & (kTileX - 1), ly = lidx / kTileX;
-    const int cx = tx0 + lx, cy = ty0 + ly;
-    if (cx >= p.W || cy >= p.H) active = false;
-
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < L.nbuf; ++b) {
+            mbar_init(&full[b], 1);
+            released[b] = 0;
+        }
         mbar_fence_init();
     }
     __syncthreads();
+
+    // ---- work items.  Dense: one per tile.  Queue: each active tile's pixel
+    // list is cut into chunks of `chunk` pixels (chosen from this frame's flagged
+    // total so that every CTA gets several items), item w -> (queue slot w / per,
+    // chunk w % per); chunks past a tile's count are empty and skipped.
+    int chunk = kTilePix, per = 1, n_items = n_work;
+    if (!kDense) {
+        const uint32_t total = *(volatile uint32_t*)&p.ctrl->flag_total;
+        const uint32_t target = total / (uint32_t)(gridDim.x * 8u);
+        chunk = 16;
+        while (chunk < kTilePix && (uint32_t)chunk < target) chunk <<= 1;
+        per = kTilePix / chunk;
+        n_items = n_work * per;
+    }
+
+    // ---- producer state, shared by whichever thread issues the next stage;
+    // kept in shared memory so the consumers' accumulators keep the registers.
+    // Stages are issued strictly in order: issuing stage S waits (bounded) until
+    // stage S-1 has been issued.
+    struct Producer {
+        int tile, k, first, count, issued, done, ok;
+    };
+    __shared__ Producer pr_store;
+    volatile Producer* pr = &pr_store;
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar[0], stage_bytes);
-        tma_load_4d(buf0, &tmap, &bar[0], 0, tx0 - p.r, ty0 - p.r, 2 * (p.t % p.T));
+        pr->tile = -1;
+        pr->k = pr->first = pr->count = pr->issued = pr->done = 0;
+        pr->ok = 1;
     }
-
-    const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
-    const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
-    const int nx = dxhi - dxlo + 1;
-    const int nvalid = nx * (dyhi - dylo + 1);
-    const int sx = lx + p.r, sy = ly + p.r;
-    const float spx = p.s_coord_px;
-
-    Acc acc;
-#pragma unroll
-    for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
-    float sf[7], cf[7];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-        sf[j] = p.s_feat[j];
-        cf[j] = 0.0f;
-    }
-
-    for (int k = 0; k < p.n_tau; ++k) {
-        const int b = k & 1;
-        if (k + 1 < p.n_tau && threadIdx.x == 0) {
-            // the other buffer was released by the barrier that ended step k-1
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[b ^ 1], stage_bytes);
-            const int slot = (p.t - k - 1) % p.T;
-            tma_load_4d(b ? buf0 : buf1, &tmap, &bar[b ^ 1], 0, tx0 - p.r, ty0 - p.r, 2 * slot);
-        }
-        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            // A staged copy never landed: record it, let the copies in flight
-            // finish (bounded), and give up on this tile.
-            if (threadIdx.x == 0) {
-                atomicOr(&p.ctrl->status, kStatusTimeout);
-                mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1));
-                if (k + 1 < p.n_tau) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+    auto produce = [&](int S) {
+        for (uint32_t spin = 0; pr->issued != S && !pr->done; ++spin) {
+            if (spin > (1u << 26)) {
+                pr->ok = 0;
+                return;
             }
-            __syncthreads();
-            return;
         }
-        const float4* P0 = b ? buf1 : buf0;
+        if (pr->done) return;
+        const int b = S % L.nbuf;
+        if (pr->tile < 0 || pr->k == p.n_tau) {
+            int tile = -1, first = 0, count = 0;
+            while (pr->ok) {
+                const int w = (int)atomicAdd(&p.ctrl->work_next, 1u);
+                if (w >= n_items) break;
+                if (kDense) {
+                    tile = w;
+                    count = kTilePix;
+                    break;
+                }
+                const int t = (int)p.tile_queue[w / per];
+                const int np = p.tile_nflag[t];
+                const int f = (w % per) * chunk;
+                if (f >= np) continue;               // empty chunk
+                tile = t;
+                first = f;
+                count = min(chunk, np - f);
+                break;
+            }
+            if (tile < 0) {
+                pr->done = 1;
+                pr->tile = -1;
+                info[b].tile = -1;
+                __threadfence_block();
+                mbar_arrive(&full[b]);               // end of stream, no copy
+                pr->issued = S + 1;
+                return;
+            }
+            pr->tile = tile;
+            pr->first = first;
+            pr->count = count;
+            pr->k = 0;
+        }
+        const int tile = pr->tile, k = pr->k;
+        info[b].tile = tile;
+        info[b].k = k;
+        info[b].first = pr->first;
+        info[b].count = pr->count;
+        const int tx0 = (tile % p.tiles_x) * kTileX, ty0 = (tile / p.tiles_x) * kTileY;
+        const int slot = (p.t - k) % p.T;
+        pr->k = k + 1;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&full[b], stage_bytes);
+        tma_load_4d(smem + b * L.buf_bytes, &tmap, &full[b], 0, tx0 - p.r, ty0 - p.r, 2 * slot);
+        __threadfence_block();
+        pr->issued = S + 1;
+    };
+    // ---- consumer state
+    Acc acc;
+    const float* sf = p.s_feat;
+    float cf[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) cf[j] = 0.0f;
+    int g = 1, lg = 0, sub = 0, npix = 0, cx = 0, cy = 0, sx = 0, sy = 0;
+    int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0;
+    bool active = false;
+    bool timed_out = false;
+    __shared__ unsigned long long s_pairs, s_pix;
+    if (threadIdx.x == 0) {
+        s_pairs = 0ull;
+        s_pix = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < L.nbuf; ++i) produce(i);
+
+    for (int s = 0;; ++s) {
+        const int b = s % L.nbuf;
+        if (!mbar_wait_bounded(&full[b], (uint32_t)((s / L.nbuf) & 1))) {
+            timed_out = true;
+            break;
+        }
+        const StageInfo in = info[b];
+        if (in.tile < 0) break;
+        const float4* P0 = reinterpret_cast<const float4*>(smem + b * L.buf_bytes);
         const float4* P1 = P0 + plane;
-        if (active) {
-            if (k == 0) {
+        if (in.k == 0) {
+            // new tile: assign lanes to its regressed pixels
+            const int tx0 = (in.tile % p.tiles_x) * kTileX, ty0 = (in.tile / p.tiles_x) * kTileY;
+            npix = in.count;
+            lg = 0;
+            if (!kDense) lg = npix > 128 ? 0 : npix > 64 ? 1 : npix > 32 ? 2 : npix > 16 ? 3 : npix > 8 ? 4 : 5;
+            g = 1 << lg;
+            const int item = (int)threadIdx.x >> lg;
+            sub = (int)threadIdx.x & (g - 1);
+            active = item < npix;
+            const int lidx = kDense ? (int)threadIdx.x
+                                    : (active ? (int)p.tile_pix[(size_t)in.tile * kTilePix + in.first + item] : 0);
+            const int lx = lidx & (kTileX - 1), ly = lidx / kTileX;
+            cx = tx0 + lx;
+            cy = ty0 + ly;
+            if (cx >= p.W || cy >= p.H) active = false;
+            dxlo = max(-p.r, -cx);
+            dxhi = min(p.r, p.W - 1 - cx);
+            dylo = max(-p.r, -cy);
+            dyhi = min(p.r, p.H - 1 - cy);
+            sx = lx + p.r;
+            sy = ly + p.r;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
+            if (active) {
                 const float4 c0 = P0[sy * p.sw + sx];
                 const float4 c1 = P1[sy * p.sw + sx];
                 cf[0] = c0.y * sf[0];
@@ -237,6 +438,9 @@ __global__ void __launch_bounds__(kTilePix, 2)
                 cf[5] = c1.z * sf[5];
                 cf[6] = c1.w * sf[6];
             }
+        }
+        if (active) {
+            const int nx = dxhi - dxlo + 1;
             if (g == 1) {
                 for (int oy = dylo; oy <= dyhi; ++oy) {
                     const float u2 = (float)oy * spx;
@@ -245,22 +449,28 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     float u1 = (float)dxlo * spx;
 #pragma unroll 3
                     for (int ox = dxlo; ox <= dxhi; ++ox) {
-                        const float4 h0 = P0[row + ox];
-                        const float4 h1 = P1[row + ox];
-                        accumulate(acc, h0, h1, u1, u2, fmaf(-u1, u1, en_row), sf, cf);
+                        accumulate(acc, P0[row + ox], P1[row + ox], u1, u2, fmaf(-u1, u1, en_row), sf, cf);
                         u1 += spx;
                     }
                 }
+            } else if (nx == side && dyhi - dylo + 1 == side) {
+                // interior pixel: walk the full window through the table
+                const int cbase = sy * p.sw + sx;
+                for (int q = sub; q < nq; q += g) {
+                    const float4 e = table[q];
+                    const int si = cbase + __float_as_int(e.x);
+                    accumulate(acc, P0[si], P1[si], e.y, e.z, e.w, sf, cf);
+                }
             } else {
+                // window clipped by the image border
+                const int nvalid = nx * (dyhi - dylo + 1);
                 int ox = dxlo + sub % nx;
                 int oy = dylo + sub / nx;
                 for (int q = sub; q < nvalid; q += g) {
                     const int si = (sy + oy) * p.sw + sx + ox;
-                    const float4 h0 = P0[si];
-                    const float4 h1 = P1[si];
                     const float u1 = (float)ox * spx;
                     const float u2 = (float)oy * spx;
-                    accumulate(acc, h0, h1, u1, u2, -fmaf(u1, u1, u2 * u2), sf, cf);
+                    accumulate(acc, P0[si], P1[si], u1, u2, -fmaf(u1, u1, u2 * u2), sf, cf);
                     ox += g;
                     while (ox > dxhi) {
                         ox -= nx;
@@ -269,79 +479,191 @@ __global__ void __launch_bounds__(kTilePix, 2)
                 }
             }
         }
-        __syncthreads();
+        // count this warp out of the buffer; the last warp refills it
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&released[b], 1) == kTilePix / 32 - 1) {
+                released[b] = 0;
+                __threadfence_block();
+                produce(s + L.nbuf);
+            }
+        }
+
+        if (in.k == p.n_tau - 1) {
+            // last frame of the window for this tile: reduce, solve, emit
+            if (!kDense && g > 1) {
+                for (int off = g >> 1; off >= 1; off >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) acc.B[i] += __shfl_xor_sync(0xffffffffu, acc.B[i], off);
+                }
+            }
+            if (active && sub == 0) {
+                atomicAdd(&s_pairs, (unsigned long long)((dxhi - dxlo + 1) * (dyhi - dylo + 1) * p.n_tau));
+                atomicAdd(&s_pix, 1ull);
+                float s2[NZ];
+                s2[0] = 0.0f;
+                s2[1] = p.s_coord * p.s_coord;
+                s2[2] = s2[1];
+#pragma unroll
+                for (int j = 0; j < 7; ++j) s2[3 + j] = sf[j] * sf[j];
+                float theta[NZ];
+                solve(acc, s2, p.ridge, theta);
+                emit(p, cx, cy, theta, sf);
+            }
+        }
     }
 
-    {
-        // work accounting: (pixel, neighbour) pairs of this tile
-        __shared__ unsigned long long s_pairs;
-        if (threadIdx.x == 0) s_pairs = 0ull;
-        __syncthreads();
-        if (active && sub == 0) atomicAdd(&s_pairs, (unsigned long long)nvalid * (unsigned long long)p.n_tau);
-        __syncthreads();
-        if (threadIdx.x == 0 && s_pairs) atomicAdd(&p.ctrl->neighbours, s_pairs);
-    }
+    __syncthreads();   // every thread's counter updates are in before thread 0 reads them
+    finish(p, s_pairs, s_pix, timed_out || (threadIdx.x == 0 && !pr->ok));
+}
 
-    if (!kDense && g > 1) {
-        // lanes of one pixel are adjacent in the warp: butterfly-reduce
-        for (int off = g >> 1; off >= 1; off >>= 1) {
+// Sparse-frame regression.  When few pixels are flagged they lie on thin
+// feature edges, a handful per tile, and staging a whole tile window per work
+// item would move far more data than it feeds.  This kernel instead reads each
+// neighbour's two float4 half-planes straight from the ring through L1 (it
+// reserves almost no shared memory, so L1 keeps the overlapping windows of
+// nearby pixels).  Warps work independently: each takes the next two entries
+// of the frame's flagged-pixel list, 16 lanes per pixel split its window, and
+// the lanes are shuffle-reduced; no block-wide barrier after set-up.
+__global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams p)
+{
+    if (p.sparse_max == 0 || *(volatile uint32_t*)&p.ctrl->flag_total > p.sparse_max)
+        return;  // the tile-staged kernel's frame
+    constexpr int kLanes = 16;
+    __shared__ float4 table[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];
+    __shared__ unsigned long long s_pairs, s_pix;
+    const int side = 2 * p.r + 1, nq = side * side;
+    const float spx = p.s_coord_px;
+    const size_t N = (size_t)p.W * p.H;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int ox = q % side - p.r, oy = q / side - p.r;
+        const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+        table[q] = make_float4(__int_as_float(oy * p.W + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
+    }
+    if (threadIdx.x == 0) {
+        s_pairs = 0ull;
+        s_pix = 0ull;
+    }
+    __syncthreads();
+    const uint32_t n_flag = *(volatile uint32_t*)&p.ctrl->flag_total;
+    const float* sf = p.s_feat;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (kLanes - 1);
+    const int half = lane >> 4;
+    const int slot_t = p.t % p.T;
+    Acc acc;
+    float cf[7];
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctrl->work_next, 2u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_flag) break;
+        const uint32_t my = base + (uint32_t)half;
+        const bool active = my < n_flag;
+        const uint32_t pix = active ? p.flag_list[my] : 0u;
+        const int cx = (int)(pix % (uint32_t)p.W), cy = (int)(pix / (uint32_t)p.W);
+#pragma unroll
+        for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
+        const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
+        const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
+        const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
+        if (active) {
+            const float4 c0 = __ldg(p.ring + (size_t)(2 * slot_t) * N + pix);
+            const float4 c1 = __ldg(p.ring + (size_t)(2 * slot_t + 1) * N + pix);
+            cf[0] = c0.y * sf[0];
+            cf[1] = c0.z * sf[1];
+            cf[2] = c0.w * sf[2];
+            cf[3] = c1.x * sf[3];
+            cf[4] = c1.y * sf[4];
+            cf[5] = c1.z * sf[5];
+            cf[6] = c1.w * sf[6];
+            for (int k = 0; k < p.n_tau; ++k) {
+                const int slot = (p.t - k) % p.T;
+                const float4* __restrict__ R0 = p.ring + (size_t)(2 * slot) * N + pix;
+                const float4* __restrict__ R1 = p.ring + (size_t)(2 * slot + 1) * N + pix;
+                if (nx == side && ny == side) {
+#pragma unroll 2
+                    for (int q = sub; q < nq; q += kLanes) {
+                        const float4 e = table[q];
+                        const int d = __float_as_int(e.x);
+                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), e.y, e.z, e.w, sf, cf);
+                    }
+                } else {
+                    const int nvalid = nx * ny;
+                    int ox = dxlo + sub % nx;
+                    int oy = dylo + sub / nx;
+                    for (int q = sub; q < nvalid; q += kLanes) {
+                        const int d = oy * p.W + ox;
+                        const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, -fmaf(u1, u1, u2 * u2), sf, cf);
+                        ox += kLanes;
+                        while (ox > dxhi) {
+                            ox -= nx;
+                            ++oy;
+                        }
+                    }
+                }
+            }
+        }
+        for (int off = kLanes >> 1; off >= 1; off >>= 1) {
 #pragma unroll
             for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
 #pragma unroll
             for (int i = 0; i < NZ; ++i) acc.B[i] += __shfl_xor_sync(0xffffffffu, acc.B[i], off);
         }
-    }
-
-    if (threadIdx.x == 0) {
-        int cnt = npix;
-        if (kDense) cnt = min(kTileX, p.W - tx0) * min(kTileY, p.H - ty0);
-        atomicAdd(&p.ctrl->regressions, (unsigned long long)cnt);
-    }
-    if (!active || sub != 0) return;
-
-    float s2[NZ];
-    s2[0] = 0.0f;
-    s2[1] = p.s_coord * p.s_coord;
-    s2[2] = s2[1];
+        if (active && sub == 0) {
+            atomicAdd(&s_pairs, (unsigned long long)(nx * ny * p.n_tau));
+            atomicAdd(&s_pix, 1ull);
+            float s2[NZ];
+            s2[0] = 0.0f;
+            s2[1] = p.s_coord * p.s_coord;
+            s2[2] = s2[1];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) s2[3 + j] = sf[j] * sf[j];
-    float theta[NZ];
-    solve(acc, s2, p.ridge, theta);
-
-    const size_t N = (size_t)p.W * p.H;
-    const size_t i = (size_t)cy * p.W + cx;
-    const float alpha = theta[0];
-    float bf[7];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) bf[j] = theta[3 + j] * sf[j];
-    p.alpha[i] = alpha;
-
-    float L;
-    if (p.init) {
-        L = alpha;
-    } else {
-        L = p.state[N + i].w;
-        const float dl = alpha - L;
-        const float n = floorf(fabsf(dl) / p.C);
-        if (!(n >= 1.0f)) return;  // no event: keep the model (Fig. 1)
-        const float pol = dl > 0.0f ? 1.0f : -1.0f;
-        L = fmaf(pol * n, p.C, L);
-        p.nev[i] = (int32_t)(pol * n);
+            for (int j = 0; j < 7; ++j) s2[3 + j] = sf[j] * sf[j];
+            float theta[NZ];
+            solve(acc, s2, p.ridge, theta);
+            emit(p, cx, cy, theta, sf);
+        }
     }
-    const int slot = p.t % p.T;
-    const float4 x0 = p.ring[(size_t)(2 * slot) * N + i];
-    const float4 x1 = p.ring[(size_t)(2 * slot + 1) * N + i];
-    p.state[i] = make_float4(bf[0], bf[1], bf[2], bf[3]);
-    p.state[N + i] = make_float4(bf[4], bf[5], bf[6], L);
-    p.state[2 * N + i] = make_float4(x0.y, x0.z, x0.w, x1.x);
-    p.state[3 * N + i] = make_float4(x1.y, x1.z, x1.w, 0.0f);
+    __syncthreads();
+    finish(p, s_pairs, s_pix, false);
 }
 
-size_t wlr_smem_bytes(int r)
+int wlr_sparse_grid(int num_sms)
 {
-    const size_t stage = (size_t)2 * (kTileX + 2 * r) * (kTileY + 2 * r) * 16;
-    const size_t buf = (stage + 127) & ~(size_t)127;
-    return 2 * buf + 2 * sizeof(uint64_t) + 128;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel, kTilePix, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * num_sms;
+}
+
+cudaError_t launch_wlr_sparse(const WlrParams& p, int grid, cudaStream_t s)
+{
+    wlr_sparse_kernel<<<grid, kTilePix, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+SmemLayout host_layout(int r, int max_smem_per_sm)
+{
+    // three stages in flight when two CTAs still fit on an SM, else two
+    SmemLayout L3 = smem_layout(r, 3);
+    if (2 * (L3.total + 1024) <= max_smem_per_sm) return L3;
+    return smem_layout(r, 2);
+}
+
+size_t wlr_smem_bytes(int r, int max_smem_per_sm, int* nbuf)
+{
+    const SmemLayout L = host_layout(r, max_smem_per_sm);
+    *nbuf = L.nbuf;
+    return (size_t)L.total;
 }
 
 cudaError_t wlr_prepare(int smem_bytes)
@@ -351,6 +673,18 @@ cudaError_t wlr_prepare(int smem_bytes)
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(wlr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_bytes);
+}
+
+int wlr_grid(int smem_bytes, int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_kernel<false>, kTilePix, smem_bytes) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * num_sms;
 }
 
 cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, int grid, int smem_bytes,

@@ -16,43 +16,57 @@ from scenes import Scene, SceneConfig, preset
 pytestmark = pytest.mark.gpu
 
 
-def _sim(W, H, r, T, C, mode, rgb, capacity=1 << 22):
+# which regression kernel serves adaptive frames: the library's choice, the
+# tile-staged kernel always, or the sparse (L1 window) kernel always
+PATHS = {"auto": None, "staged": "0", "sparse": "4294967295"}
+
+
+def _sim(W, H, r, T, C, mode, rgb, capacity=1 << 22, path="auto"):
+    import os
     from paper_2303_02608_gb300 import SimConfig, Simulator
-    return Simulator(SimConfig(width=W, height=H, radius=r, frames=T, contrast=C, mode=mode, rgb=rgb,
-                               event_capacity=capacity))
+    old = os.environ.pop("ESIM_AD_SPARSE_MAX", None)
+    if PATHS[path] is not None:
+        os.environ["ESIM_AD_SPARSE_MAX"] = PATHS[path]
+    try:
+        return Simulator(SimConfig(width=W, height=H, radius=r, frames=T, contrast=C, mode=mode, rgb=rgb,
+                                   event_capacity=capacity))
+    finally:
+        os.environ.pop("ESIM_AD_SPARSE_MAX", None)
+        if old is not None:
+            os.environ["ESIM_AD_SPARSE_MAX"] = old
 
 
 def _orc(W, H, r, T, C, mode, rgb):
     return Oracle(OracleConfig(W, H, radius=r, frames=T, channels=3 if rgb else 1, mode=mode, contrast=C))
 
 
-def _case(scene_cfg, r, T, C, mode, n_frames, rows=None, strict=True):
+def _case(scene_cfg, r, T, C, mode, n_frames, rows=None, strict=True, path="auto"):
     sc = Scene(scene_cfg)
     frames = sc.sequence(n_frames)
     W, H, rgb = scene_cfg.width, scene_cfg.height, scene_cfg.rgb
-    sim = _sim(W, H, r, T, C, mode, rgb)
+    sim = _sim(W, H, r, T, C, mode, rgb, path=path)
     orc = _orc(W, H, r, T, C, mode, rgb)
     rep = run(frames, sim, orc, C, rows=rows, strict=strict, adaptive=(mode == ADAPTIVE))
     sim.close()
     return rep
 
 
-@pytest.mark.parametrize("mode", [ADAPTIVE, EXHAUSTIVE])
+@pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse"), (EXHAUSTIVE, "auto")])
 @pytest.mark.parametrize("strict", [True, False])
-def test_disc_64(mode, strict):
+def test_disc_64(mode, path, strict):
     """64x64 disc, 8 frames, 7x7x3 window, C = 0.2, luminance (the tiny workload)."""
-    rep = _case(preset("disc64"), 3, 3, 0.2, mode, 8, strict=strict)
+    rep = _case(preset("disc64"), 3, 3, 0.2, mode, 8, strict=strict, path=path)
     assert rep["events"] > 0 and rep["regressed"] > 0
     total = 64 * 64 * 8
     assert rep["flag_ambiguous"] + rep["event_ambiguous"] < 0.001 * total + 2
 
 
-@pytest.mark.parametrize("mode", [ADAPTIVE, EXHAUSTIVE])
-def test_ragged_rects(mode):
+@pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse"), (EXHAUSTIVE, "auto")])
+def test_ragged_rects(mode, path):
     """77x45 RGB rectangles (ragged tiles both ways), 5x5x2 window."""
     cfg = SceneConfig(kind="rects", width=77, height=45, frames=6, spp=4, seed=3, rgb=True,
                       n_rects=8, bg_depth=10.0)
-    rep = _case(cfg, 2, 2, 0.15, mode, 6)
+    rep = _case(cfg, 2, 2, 0.15, mode, 6, path=path)
     assert rep["regressed"] > 0
 
 
@@ -60,10 +74,11 @@ def test_ragged_rects(mode):
                                      (70, 40, 15, 16)])
 def test_edge_shapes(W, H, r, T):
     """Single pixel, smaller than a tile, radius 1, the maximum radius (15) and
-    temporal window (16)."""
+    temporal window (16), through both adaptive regression kernels."""
     cfg = SceneConfig(kind="rects", width=W, height=H, frames=max(3, min(T + 2, 18)), spp=2, seed=5,
                       rgb=True, n_rects=6, bg_depth=10.0)
-    _case(cfg, r, T, 0.15, ADAPTIVE, cfg.frames)
+    _case(cfg, r, T, 0.15, ADAPTIVE, cfg.frames, path="staged")
+    _case(cfg, r, T, 0.15, ADAPTIVE, cfg.frames, path="sparse")
     _case(cfg, r, T, 0.15, EXHAUSTIVE, 3)
 
 
@@ -84,12 +99,13 @@ def test_static_scene_no_events():
         sim.close()
 
 
-@pytest.mark.parametrize("mode,rows", [(ADAPTIVE, (352, 368)), (EXHAUSTIVE, (352, 360)),
-                                       (ADAPTIVE, (0, 8)), (ADAPTIVE, (712, 720))])
-def test_720p_band(mode, rows):
+@pytest.mark.parametrize("mode,rows,path", [(ADAPTIVE, (352, 368), "auto"), (ADAPTIVE, (352, 368), "staged"),
+                                            (EXHAUSTIVE, (352, 360), "auto"), (ADAPTIVE, (0, 8), "auto"),
+                                            (ADAPTIVE, (712, 720), "staged")])
+def test_720p_band(mode, rows, path):
     """The paper-scale workload at full size (1280x720 RGB, 15x15x5, C = 0.15),
     7 frames so the temporal window fills; oracle on a band of rows."""
-    rep = _case(preset("rects720p"), 7, 5, 0.15, mode, 7, rows=rows)
+    rep = _case(preset("rects720p"), 7, 5, 0.15, mode, 7, rows=rows, path=path)
     assert rep["regressed"] > 0
 
 
