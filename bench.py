@@ -195,7 +195,8 @@ def _cpu_baseline(frames_cpu, wl, budget_s=15.0, rows=None):
     from oracle import ADAPTIVE, Oracle, OracleConfig
     H, Wd = frames_cpu[0]["depth"].shape
     r0, r1 = rows or (H // 2 - 128, H // 2 + 128)
-    orc = Oracle(OracleConfig(Wd, H, radius=wl["r"], frames=wl["T"], channels=3 if wl["rgb"] else 1,
+    channels = 0 if wl["rgb"] is None else (3 if wl["rgb"] else 1)
+    orc = Oracle(OracleConfig(Wd, H, radius=wl["r"], frames=wl["T"], channels=channels,
                               mode=ADAPTIVE, contrast=wl["C"]))
     t0 = time.perf_counter()
     n = 0
@@ -211,8 +212,28 @@ def _cpu_baseline(frames_cpu, wl, budget_s=15.0, rows=None):
                       f"adaptive, FP64 C oracle with OpenMP", "seconds": round(dt, 2)}
 
 
+FSCALE = [1.0, 1.0, 1.0, 8.0, 1.0, 1.0, 1.0]   # BF16 feature scales: depth stored as depth / 8
+REC709 = (0.2126, 0.7152, 0.0722)
+
+
+def _storage_frames(frames, log_eps=1e-3):
+    """The precision workload's input: the renderer's log brightness as FP16 and
+    its features as BF16 (depth / 8), prepared on the device before timing."""
+    import torch
+    out = []
+    for f in frames:
+        rad = f["radiance"]
+        Y = REC709[0] * rad[0] + REC709[1] * rad[1] + REC709[2] * rad[2]
+        fs = torch.tensor(FSCALE, device=rad.device).view(7, 1, 1)
+        feat = torch.cat([f["normal"], f["depth"][None], f["albedo"]], 0) / fs
+        out.append({"radiance": torch.log(Y + log_eps).half().contiguous(),
+                    "features": feat.to(torch.bfloat16).contiguous()})
+    return out
+
+
 def run_ours(args):
     import torch
+    import paper_2303_02608_gb300 as lib
     from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, ESIM_AD_EXHAUSTIVE, SimConfig, Simulator
     from scenes import Scene, preset
 
@@ -228,93 +249,101 @@ def run_ours(args):
     F = scfg.frames
     n_gen = min(F, args.warmup + args.steps)
     frames = _gen_frames(scene, n_gen, dev)
+    sframes = _storage_frames(frames)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-
     cap = args.event_capacity
     sink = torch.empty(cap * 12, dtype=torch.uint8, device=dev)
 
-    def make(mode):
+    def make(mode, mixed):
+        extra = dict(radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
+                     precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE) if mixed else {}
         return Simulator(SimConfig(width=Wd, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
-                                   mode=mode, rgb=wl["rgb"], event_capacity=cap), stream)
+                                   mode=mode, rgb=wl["rgb"], event_capacity=cap, **extra), stream)
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     gpu_index = vis.split(",")[local] if vis else str(local)
+    runs = {}
     with ClockSampler(gpu_index) as clk:
-        sim_a = make(ESIM_AD_ADAPTIVE)
-        if dist:
-            dist.barrier()
-        ms_a, prof_a, ev_a = _timed_run(sim_a, frames, args.warmup, args.steps, stream, sink=sink)
-        stats_a = sim_a.stats()
-        sim_a.close()
-        sim_e = make(ESIM_AD_EXHAUSTIVE)
-        if dist:
-            dist.barrier()
-        ms_e, prof_e, ev_e = _timed_run(sim_e, frames, args.warmup, args.steps, stream, sink=sink)
-        sim_e.close()
+        for name, mode, mixed, fr in (("mixed_adaptive", ESIM_AD_ADAPTIVE, True, sframes),
+                                      ("mixed_exhaustive", ESIM_AD_EXHAUSTIVE, True, sframes),
+                                      ("fp32_adaptive", ESIM_AD_ADAPTIVE, False, frames),
+                                      ("fp32_exhaustive", ESIM_AD_EXHAUSTIVE, False, frames)):
+            sim = make(mode, mixed)
+            if dist:
+                dist.barrier()
+            ms, prof, ev = _timed_run(sim, fr, args.warmup, args.steps, stream, sink=sink)
+            prof["fp64_solves"] = sim.stats()["fp64_solves"]
+            sim.close()
+            runs[name] = (ms, prof, ev)
     clocks = clk.summary()
 
     if dist:
-        t = torch.tensor([ms_a, ms_e], device=dev)
+        t = torch.tensor([runs[k][0] for k in runs], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_a, ms_e = float(t[0]), float(t[1])
+        for i, k in enumerate(list(runs)):
+            runs[k] = (float(t[i]),) + runs[k][1:]
     K = args.steps
-    value = ws * N * K / (ms_a * 1e-3)
-    value_e = ws * N * K / (ms_e * 1e-3)
+
+    def rate(name):
+        return ws * N * K / (runs[name][0] * 1e-3)
+
+    ms_a, prof_a, ev_a = runs["mixed_adaptive"]
+    value = rate("mixed_adaptive")
 
     peaks, peak_src = _peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
 
-    def wlr_roof(prof):
+    def roofline(prof):
         n_launch = prof["launches"]["wlr_emit"]
         wlr_ms = prof["ms"]["wlr_emit"]
-        return n_launch, wlr_ms
+        flops = prof["neighbours_timed"] * FLOP_PER_NEIGHBOUR + prof["regressions_timed"] * FLOP_PER_SOLVE
+        ach = flops / n_launch / (wlr_ms * 1e-3 / n_launch) / 1e12
+        return {"achieved": round(ach, 3), "frac": round(ach / fp32_peak, 4),
+                "flops_per_launch": flops / n_launch, "launch_ms": round(wlr_ms / n_launch, 4)}
 
-    # neighbour and regression counts of the timed region only
-    n_launch, wlr_ms = wlr_roof(prof_a)
-    flops = prof_a["neighbours_timed"] * FLOP_PER_NEIGHBOUR + prof_a["regressions_timed"] * FLOP_PER_SOLVE \
-        if "neighbours_timed" in prof_a else None
+    phi = prof_a["regressions_timed"] / (N * K)
     src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2303_02608_gb300", "csrc", "wlr.cu"),
                                    "rb").read()).hexdigest()[:16]
-    roof = {"kernel": "wlr_kernel (regression + emission, adaptive queue)", "bound": "alu",
-            "unit": "TFLOP/s", "peak": round(fp32_peak, 2),
+    roof = {"kernel": "regression + emission launches of an adaptive frame (wlr_sparse_kernel at this "
+                      "flag density; the tile-staged wlr_kernel returns at once)",
+            "bound": "alu", "unit": "TFLOP/s", "peak": round(fp32_peak, 2),
             "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
                            f"(max SM clock, {peak_src} peaks file)",
             "traffic": NCU_TRAFFIC.get(src_hash)}
-    if flops is not None and wlr_ms > 0:
-        per_launch_flops = flops / n_launch
-        per_launch_s = wlr_ms * 1e-3 / n_launch
-        roof["achieved"] = round(per_launch_flops / per_launch_s / 1e12, 3)
-        roof["frac"] = round(roof["achieved"] / fp32_peak, 4)
-        roof["flops_per_launch"] = per_launch_flops
-        roof["launch_ms"] = round(wlr_ms / n_launch, 4)
-        if roof["traffic"] is not None:
-            roof["traffic_per_launch_bytes"] = roof["traffic"]
+    roof.update(roofline(prof_a))
 
-    # path-level HBM accounting (adaptive): fused minimum bytes per pixel-frame
-    phi = prof_a["regressions_timed"] / (N * K) if "regressions_timed" in prof_a else None
-    bytes_pf = 40 + 32 + 64 + 1 + 4 + 4 + 4          # inputs, ring write, model read, flag, count, 2 reads
+    # path-level HBM accounting (precision form, adaptive): minimum bytes per pixel-frame
+    bytes_pf = 16 + 16 + 32 + 1 + 4 + 4 + 4    # FP16+BF16 input, ring write, model read, flag, counts
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
-    path_bytes = bytes_pf * N * K + (phi or 0) * N * K * (4 + 64) + ev_a * 12
+    path_bytes = bytes_pf * N * K + phi * N * K * (4 + 64) + ev_a * 12
     hbm_path = {"bytes_per_pixel_frame_min": bytes_pf, "achieved_gbs": round(path_bytes / (ms_a * 1e-3) / 1e9, 1),
                 "peak_gbs": hbm_gbs, "frac": round(path_bytes / (ms_a * 1e-3) / 1e9 / hbm_gbs, 4)}
+
+    def form(name):
+        ms, prof, ev = runs[name]
+        return {"value": round(rate(name), 1), "unit": UNIT, "ms_per_step": round(ms / K, 4),
+                "events_per_step": round(ev / K, 1),
+                "kernel_ms_per_step": {k: round(v / K, 4) for k, v in prof["ms"].items()},
+                "regression_roofline": roofline(prof), "fp64_solves": prof["fp64_solves"]}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_a / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {wl['desc']}", "mode": "adaptive",
+                   "form": "precision (FP16 log brightness + BF16 features in storage, FP32 accumulation, "
+                           "refined FP32 Cholesky, FP64 re-solve above cond 1e6)",
                    "width": Wd, "height": H, "radius": wl["r"], "T": wl["T"], "C": wl["C"],
                    "spp": scfg.spp, "sequence_frames": F,
-                   "l2": "inputs larger than L2: each step reads a distinct 83 MB frame; ring 330 MB"},
-        "exhaustive": {"value": round(value_e, 1), "unit": UNIT, "ms_per_step": round(ms_e / K, 4),
-                       "speedup_adaptive": round(value / value_e, 3),
-                       "wlr_launch_ms": round(prof_e["ms"]["wlr_emit"] / max(1, prof_e["launches"]["wlr_emit"]), 4)},
-        "flagged_fraction": round(phi, 4) if phi is not None else None,
+                   "l2": "inputs larger than L2: each step reads a distinct frame; 240-frame sequence"},
+        "exhaustive": form("mixed_exhaustive"),
+        "fp32_form": {"adaptive": form("fp32_adaptive"), "exhaustive": form("fp32_exhaustive")},
+        "speedup_adaptive_vs_exhaustive": round(value / rate("mixed_exhaustive"), 3),
+        "flagged_fraction": round(phi, 4),
         "events_per_step": round(ev_a / K, 1),
-        "events_per_step_exhaustive": round(ev_e / K, 1),
         "kernel_ms_per_step": {k: round(v / K, 4) for k, v in prof_a["ms"].items()},
         "roofline": roof,
         "hbm_path": hbm_path,
@@ -325,19 +354,29 @@ def run_ours(args):
         line["e2e"] = _e2e(args, scene, wl, N, stream)
     if rank == 0 and not args.no_cpu_baseline:
         nb = min(len(frames), 48)
-        frames_cpu = [{k: v.cpu() for k, v in f.items()} for f in frames[:nb]]
-        line["cpu_baseline"] = _cpu_baseline(frames_cpu, wl)
+        frames_cpu = [_dequantised_cpu(f) for f in sframes[:nb]]
+        line["cpu_baseline"] = _cpu_baseline(frames_cpu, dict(wl, rgb=None))
     if dist:
         dist.barrier()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def _e2e(args, scene, wl, N, stream):
-    """Same metric through the public API with pinned host buffers: every step
-    copies its frame in (inside esim_ad_push_frame) and drains its events to
-    the host (esim_ad_events)."""
+def _dequantised_cpu(sf):
+    """Storage-format frame widened to float32 on the host (what the oracle reads)."""
     import torch
+    fs = torch.tensor(FSCALE).view(7, 1, 1)
+    q = sf["features"].float().cpu() * fs
+    return {"radiance": sf["radiance"].float().cpu()[None], "normal": q[0:3].contiguous(),
+            "depth": q[3].contiguous(), "albedo": q[4:7].contiguous()}
+
+
+def _e2e(args, scene, wl, N, stream):
+    """Same metric through the public API with pinned host buffers (precision
+    form): every step copies its frame in (inside esim_ad_push_frame) and
+    drains its events to the host (esim_ad_events)."""
+    import torch
+    import paper_2303_02608_gb300 as lib
     from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, SimConfig, Simulator
     W = args.warmup
     K = min(args.steps, args.e2e_steps)
@@ -345,10 +384,13 @@ def _e2e(args, scene, wl, N, stream):
     host = []
     for t in range(n):
         f = scene.frame(t, "cuda")
-        host.append({k: f[k].cpu().pin_memory() for k in ("radiance", "normal", "albedo", "depth")})
+        sf = _storage_frames([{k: f[k] for k in ("radiance", "normal", "albedo", "depth")}])[0]
+        host.append({k: v.cpu().pin_memory() for k, v in sf.items()})
     Wd, H = scene.cfg.width, scene.cfg.height
     sim = Simulator(SimConfig(width=Wd, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
-                              mode=ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=1 << 24), stream)
+                              mode=ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=1 << 24,
+                              radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
+                              precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE), stream)
     for s in range(W):
         sim.push(host[s % n])
         sim.events()
@@ -364,9 +406,10 @@ def _e2e(args, scene, wl, N, stream):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()
-    h2d = sum(v.numel() * 4 for v in host[0].values())
+    h2d = sum(v.numel() * v.element_size() for v in host[0].values())
     return {"value": round(N * K / dt, 1), "unit": UNIT, "steps": K, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": int(d2h / K), "ms_per_step": round(dt * 1e3 / K, 3)}
+            "d2h_bytes_per_step": int(d2h / K), "ms_per_step": round(dt * 1e3 / K, 3),
+            "form": "precision, pinned host FP16/BF16 frames"}
 
 
 def run_reference(args):
@@ -385,7 +428,8 @@ def run_reference(args):
     Wd, H = scfg.width, scfg.height
     r0, r1 = H // 2 - 4, H // 2 + 4
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    orc = Oracle(OracleConfig(Wd, H, radius=wl["r"], frames=wl["T"], channels=3 if wl["rgb"] else 1,
+    # the same precision-form input as the timed arm, widened to FP64 by the oracle
+    orc = Oracle(OracleConfig(Wd, H, radius=wl["r"], frames=wl["T"], channels=0,
                               mode=ADAPTIVE, contrast=wl["C"]))
     F = scfg.frames
     total = 0.0
@@ -395,7 +439,7 @@ def run_reference(args):
         if idx == 0 and s > 0:
             orc = Oracle(orc.cfg)
         f = scene.frame(idx, dev)
-        fr = {k: f[k].cpu() for k in ("radiance", "normal", "albedo", "depth")}
+        fr = _dequantised_cpu(_storage_frames([{k: f[k] for k in ("radiance", "normal", "albedo", "depth")}])[0])
         t0 = time.perf_counter()
         orc.push(fr, (r0, r1))
         dt = time.perf_counter() - t0

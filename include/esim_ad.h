@@ -57,7 +57,17 @@ typedef enum esim_ad_status {
 } esim_ad_status;
 
 enum { ESIM_AD_ADAPTIVE = 0, ESIM_AD_EXHAUSTIVE = 1 };
-enum { ESIM_AD_LUMA_F32 = 0, ESIM_AD_RGB_F32 = 1 };
+/* radiance input: linear luminance, linear RGB (Rec.709 luminance is taken), or
+ * log brightness y = ln(Y + eps) already computed by the renderer, as FP16 */
+enum { ESIM_AD_LUMA_F32 = 0, ESIM_AD_RGB_F32 = 1, ESIM_AD_LOGLUMA_F16 = 2 };
+/* feature input: separate float32 planes, or one [7][H][W] BF16 stack
+ * (normal xyz, depth, albedo rgb) whose values are multiplied by feature_scale */
+enum { ESIM_AD_FEAT_F32 = 0, ESIM_AD_FEAT_BF16 = 1 };
+/* arithmetic form: FP32 storage and solve, or the mixed form (FP16 log
+ * brightness and BF16 features in the frame ring, FP32 accumulation, FP32
+ * Cholesky with one refinement step, FP64 re-solve when the estimated
+ * condition number exceeds 1e6) */
+enum { ESIM_AD_FP32 = 0, ESIM_AD_MIXED = 1 };
 
 /*
  * Simulation parameters.  Paper symbols: C (Eq. 1), h and b_j (Eq. 5), the
@@ -79,13 +89,19 @@ typedef struct esim_ad_config {
     int32_t  radius;         /* r in [1, 15]: (2r+1)^2 spatial window           */
     int32_t  frames;         /* T in [1, 16]: temporal window                   */
     int32_t  mode;           /* ESIM_AD_ADAPTIVE | ESIM_AD_EXHAUSTIVE           */
-    int32_t  radiance_fmt;   /* ESIM_AD_LUMA_F32 (1 plane) | ESIM_AD_RGB_F32 (3) */
+    int32_t  radiance_fmt;   /* ESIM_AD_LUMA_F32 (1 plane) | RGB_F32 (3) | LOGLUMA_F16 */
+    int32_t  feature_fmt;    /* ESIM_AD_FEAT_F32 | ESIM_AD_FEAT_BF16             */
+    int32_t  precision;      /* ESIM_AD_FP32 | ESIM_AD_MIXED                     */
     int32_t  reserved0;
     float    contrast;       /* C > 0                                           */
     float    h;              /* global bandwidth h > 0                          */
     float    bandwidth[7];   /* b_j > 0: normal x,y,z, depth, albedo r,g,b      */
     float    log_eps;        /* eps >= 0 in y = ln(Y + eps)                     */
     float    ridge;          /* lambda > 0                                      */
+    float    feature_scale[7]; /* > 0; BF16 feature j stores x_j / scale_j (inputs
+                                  in FEAT_BF16 and the MIXED ring); powers of two
+                                  keep the round trip exact. Ignored otherwise. */
+    float    reserved1;
     uint64_t event_capacity; /* device event buffer size in events, >= 1        */
 } esim_ad_config;
 
@@ -98,12 +114,14 @@ typedef struct esim_ad_config {
  * enqueued and completed.
  */
 typedef struct esim_ad_frame {
-    const float* radiance;   /* [1 or 3][H][W] float32 (radiance_fmt)           */
+    const void*  radiance;   /* [1 or 3][H][W] float32, or [H][W] FP16 log (radiance_fmt) */
     const float* variance;   /* [H][W] sample variance, may be NULL (unused by
                                 the method; carried for callers' bookkeeping)  */
-    const float* normal;     /* [3][H][W]                                       */
-    const float* albedo;     /* [3][H][W]                                       */
-    const float* depth;      /* [H][W]                                          */
+    const float* normal;     /* [3][H][W] float32 (FEAT_F32)                    */
+    const float* albedo;     /* [3][H][W] float32 (FEAT_F32)                    */
+    const float* depth;      /* [H][W] float32 (FEAT_F32)                       */
+    const void*  features;   /* [7][H][W] BF16 (FEAT_BF16): normal xyz, depth,
+                                albedo rgb, each stored as x_j / feature_scale_j */
     int32_t      on_host;    /* 0: device pointers, 1: host pointers            */
     int32_t      reserved0;
 } esim_ad_frame;
@@ -121,6 +139,7 @@ typedef struct esim_ad_stats {
     uint64_t regressions;    /* pixels regressed (all frames); exhaustive: W*H*frames */
     uint64_t events;         /* events emitted since init/reset                 */
     uint64_t pixels;         /* W*H                                             */
+    uint64_t fp64_solves;    /* MIXED: regressions re-solved in FP64 (cond > 1e6) */
 } esim_ad_stats;
 
 /*
@@ -141,8 +160,9 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
  * t = 0 and in exhaustive mode), and event emission with the last-event update
  * (Eq. 1).  Frame 0 only initialises L_last and the models and emits no events.
  * Does not synchronise unless frame->on_host (then it waits for its own
- * host-to-device copies only).  EINVAL on NULL/missing planes, ESTATE after a
- * sticky error, ECUDA if a launch fails.
+ * host-to-device copies only).  EINVAL on NULL/missing planes (normal, albedo
+ * and depth for FEAT_F32, features for FEAT_BF16), ESTATE after a sticky
+ * error, ECUDA if a launch fails.
  */
 esim_ad_status esim_ad_push_frame(esim_ad_ctx* ctx, const esim_ad_frame* frame);
 

@@ -31,6 +31,11 @@ ESIM_AD_ADAPTIVE = 0
 ESIM_AD_EXHAUSTIVE = 1
 ESIM_AD_LUMA_F32 = 0
 ESIM_AD_RGB_F32 = 1
+ESIM_AD_LOGLUMA_F16 = 2
+ESIM_AD_FEAT_F32 = 0
+ESIM_AD_FEAT_BF16 = 1
+ESIM_AD_FP32 = 0
+ESIM_AD_MIXED = 1
 
 # Every exported symbol of the library, as declared in include/esim_ad.h.
 EXPORTS = (
@@ -45,23 +50,25 @@ class esim_ad_config(ctypes.Structure):
     _fields_ = [
         ("struct_size", ctypes.c_uint32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
         ("radius", ctypes.c_int32), ("frames", ctypes.c_int32), ("mode", ctypes.c_int32),
-        ("radiance_fmt", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("radiance_fmt", ctypes.c_int32), ("feature_fmt", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
         ("contrast", ctypes.c_float), ("h", ctypes.c_float), ("bandwidth", ctypes.c_float * 7),
-        ("log_eps", ctypes.c_float), ("ridge", ctypes.c_float), ("event_capacity", ctypes.c_uint64),
+        ("log_eps", ctypes.c_float), ("ridge", ctypes.c_float), ("feature_scale", ctypes.c_float * 7),
+        ("reserved1", ctypes.c_float), ("event_capacity", ctypes.c_uint64),
     ]
 
 
 class esim_ad_frame(ctypes.Structure):
     _fields_ = [
         ("radiance", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("normal", ctypes.c_void_p),
-        ("albedo", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("on_host", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("albedo", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("features", ctypes.c_void_p),
+        ("on_host", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 
 class esim_ad_stats(ctypes.Structure):
     _fields_ = [("frames", ctypes.c_uint64), ("regressions", ctypes.c_uint64),
-                ("events", ctypes.c_uint64), ("pixels", ctypes.c_uint64)]
+                ("events", ctypes.c_uint64), ("pixels", ctypes.c_uint64), ("fp64_solves", ctypes.c_uint64)]
 
 
 class esim_ad_profile(ctypes.Structure):
@@ -141,12 +148,19 @@ def _check(status: int, what: str) -> None:
 
 def make_config(width: int, height: int, radius: int = 7, frames: int = 5, contrast: float = 0.15,
                 mode: int = ESIM_AD_ADAPTIVE, rgb: bool = True, h: float = 1.0, bandwidth=None,
-                log_eps: float = 1e-3, ridge: float = 1e-4, event_capacity: int = 1 << 22) -> esim_ad_config:
+                log_eps: float = 1e-3, ridge: float = 1e-4, event_capacity: int = 1 << 22,
+                radiance_fmt: int | None = None, feature_fmt: int = ESIM_AD_FEAT_F32,
+                precision: int = ESIM_AD_FP32, feature_scale=None) -> esim_ad_config:
     c = esim_ad_config()
     c.struct_size = ctypes.sizeof(esim_ad_config)
     c.width, c.height, c.radius, c.frames = width, height, radius, frames
     c.mode = mode
-    c.radiance_fmt = ESIM_AD_RGB_F32 if rgb else ESIM_AD_LUMA_F32
+    if radiance_fmt is None:
+        radiance_fmt = ESIM_AD_RGB_F32 if rgb else ESIM_AD_LUMA_F32
+    c.radiance_fmt, c.feature_fmt, c.precision = radiance_fmt, feature_fmt, precision
+    fs = [1.0] * 7 if feature_scale is None else list(feature_scale)
+    for j in range(7):
+        c.feature_scale[j] = float(fs[j])
     c.contrast, c.h, c.log_eps, c.ridge = contrast, h, log_eps, ridge
     bw = [1.0] * 7 if bandwidth is None else list(bandwidth)
     for j in range(7):
@@ -162,9 +176,10 @@ def esim_ad_init(cfg: esim_ad_config, cuda_stream: int = 0) -> int:
     return h.value
 
 
-def esim_ad_push_frame(ctx: int, radiance: int, normal: int, albedo: int, depth: int,
-                       variance: int = 0, on_host: bool = False) -> None:
-    f = esim_ad_frame(radiance, variance or None, normal, albedo, depth, int(on_host), 0)
+def esim_ad_push_frame(ctx: int, radiance: int, normal: int = 0, albedo: int = 0, depth: int = 0,
+                       variance: int = 0, on_host: bool = False, features: int = 0) -> None:
+    f = esim_ad_frame(radiance, variance or None, normal or None, albedo or None, depth or None,
+                      features or None, int(on_host), 0)
     _check(load_library().esim_ad_push_frame(ctypes.c_void_p(ctx), ctypes.byref(f)), "esim_ad_push_frame")
 
 
@@ -202,7 +217,8 @@ def esim_ad_reset(ctx: int) -> None:
 def esim_ad_stats_get(ctx: int) -> dict:
     s = esim_ad_stats()
     _check(load_library().esim_ad_stats_get(ctypes.c_void_p(ctx), ctypes.byref(s)), "esim_ad_stats_get")
-    return {"frames": s.frames, "regressions": s.regressions, "events": s.events, "pixels": s.pixels}
+    return {"frames": s.frames, "regressions": s.regressions, "events": s.events, "pixels": s.pixels,
+            "fp64_solves": s.fp64_solves}
 
 
 def esim_ad_profile_enable(ctx: int, on: bool = True) -> None:
@@ -249,18 +265,25 @@ class SimConfig:
     log_eps: float = 1e-3
     ridge: float = 1e-4
     event_capacity: int = 1 << 22
+    radiance_fmt: int | None = None      # default: RGB_F32 if rgb else LUMA_F32
+    feature_fmt: int = ESIM_AD_FEAT_F32
+    precision: int = ESIM_AD_FP32
+    feature_scale: list = field(default_factory=lambda: [1.0] * 7)
 
     def c_config(self) -> esim_ad_config:
         return make_config(self.width, self.height, self.radius, self.frames, self.contrast, self.mode,
-                           self.rgb, self.h, self.bandwidth, self.log_eps, self.ridge, self.event_capacity)
+                           self.rgb, self.h, self.bandwidth, self.log_eps, self.ridge, self.event_capacity,
+                           self.radiance_fmt, self.feature_fmt, self.precision, self.feature_scale)
 
 
 class Simulator:
     """One event-simulation context on the current CUDA device and stream.
 
-    ``push`` accepts a dict with ``radiance`` [C][H][W], ``normal`` [3][H][W],
-    ``albedo`` [3][H][W], ``depth`` [H][W] as contiguous float32 torch tensors,
-    all on the GPU, or all on the host (pinned for asynchronous copies).
+    ``push`` accepts a dict with ``radiance`` ([C][H][W] float32, or [H][W]
+    float16 log brightness) and either ``normal`` [3][H][W], ``albedo``
+    [3][H][W], ``depth`` [H][W] float32 or ``features`` [7][H][W] bfloat16, as
+    contiguous torch tensors, all on the GPU or all on the host (pinned for
+    asynchronous copies).
     """
 
     def __init__(self, cfg: SimConfig, stream=None):
@@ -281,13 +304,15 @@ class Simulator:
 
     def push(self, frame: dict) -> None:
         t = self._torch
-        planes = [frame[k] for k in ("radiance", "normal", "albedo", "depth")]
+        keys = ["radiance"] + (["features"] if "features" in frame else ["normal", "albedo", "depth"])
+        planes = [frame[k] for k in keys]
         on_host = not planes[0].is_cuda
         for p in planes:
-            if p.dtype != t.float32 or not p.is_contiguous() or p.is_cuda == on_host:
-                raise ValueError("frame planes must be contiguous float32, all on the GPU or all on the host")
-        rad, nor, alb, dep = (p.data_ptr() for p in planes)
-        esim_ad_push_frame(self.ctx, rad, nor, alb, dep, on_host=on_host)
+            if p.dtype not in (t.float32, t.float16, t.bfloat16) or not p.is_contiguous() or p.is_cuda == on_host:
+                raise ValueError("frame planes must be contiguous, all on the GPU or all on the host")
+        ptr = {k: v.data_ptr() for k, v in zip(keys, planes)}
+        esim_ad_push_frame(self.ctx, ptr["radiance"], ptr.get("normal", 0), ptr.get("albedo", 0),
+                           ptr.get("depth", 0), on_host=on_host, features=ptr.get("features", 0))
         if not on_host:
             # inputs are read in stream order; keep them alive until the next sync point
             self._keep.append(planes)

@@ -63,6 +63,7 @@ struct esim_ad_ctx {
     int nbuf = 2;
     int wlr_grid = 0;
     int sparse_grid = 0;
+    bool mixed = false;
     uint32_t sparse_max = 0;     // adaptive frames with at most this many flagged pixels use the sparse kernel
     float4* ring = nullptr;
     float4* state = nullptr;
@@ -114,7 +115,14 @@ esim_ad_status check_config(const esim_ad_config* c)
     if (c->radius < 1 || c->radius > kMaxRadius) return ESIM_AD_EINVAL;
     if (c->frames < 1 || c->frames > kMaxFrames) return ESIM_AD_EINVAL;
     if (c->mode != ESIM_AD_ADAPTIVE && c->mode != ESIM_AD_EXHAUSTIVE) return ESIM_AD_EINVAL;
-    if (c->radiance_fmt != ESIM_AD_LUMA_F32 && c->radiance_fmt != ESIM_AD_RGB_F32) return ESIM_AD_EINVAL;
+    if (c->radiance_fmt != ESIM_AD_LUMA_F32 && c->radiance_fmt != ESIM_AD_RGB_F32 &&
+        c->radiance_fmt != ESIM_AD_LOGLUMA_F16)
+        return ESIM_AD_EINVAL;
+    if (c->feature_fmt != ESIM_AD_FEAT_F32 && c->feature_fmt != ESIM_AD_FEAT_BF16) return ESIM_AD_EINVAL;
+    if (c->precision != ESIM_AD_FP32 && c->precision != ESIM_AD_MIXED) return ESIM_AD_EINVAL;
+    if (c->feature_fmt == ESIM_AD_FEAT_BF16 || c->precision == ESIM_AD_MIXED)
+        for (int j = 0; j < 7; ++j)
+            if (!finite_pos(c->feature_scale[j])) return ESIM_AD_EINVAL;
     if (!finite_pos(c->contrast) || !finite_pos(c->h) || !finite_pos(c->ridge)) return ESIM_AD_EINVAL;
     for (int j = 0; j < 7; ++j)
         if (!finite_pos(c->bandwidth[j])) return ESIM_AD_EINVAL;
@@ -172,14 +180,18 @@ esim_ad_status encode_ring_map(esim_ad_ctx* c)
                                          &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn)
         return ESIM_AD_ECUDA;
-    // ring viewed as a 4-D tensor: {4 floats, W, H, 2T planes}
-    const cuuint64_t dims[4] = {4, (cuuint64_t)c->W, (cuuint64_t)c->H, (cuuint64_t)(2 * c->cfg.frames)};
+    // ring viewed as a 4-D tensor of 16-byte records: FP32 form {4 floats, W, H,
+    // 2T half-planes}, box of both half-planes; mixed form {8 halves, W, H, T}
+    const bool mixed = c->cfg.precision == ESIM_AD_MIXED;
+    const cuuint64_t dims[4] = {mixed ? 8u : 4u, (cuuint64_t)c->W, (cuuint64_t)c->H,
+                                (cuuint64_t)((mixed ? 1 : 2) * c->cfg.frames)};
     const cuuint64_t strides[3] = {16, (cuuint64_t)16 * c->W, (cuuint64_t)16 * c->W * c->H};
-    const cuuint32_t box[4] = {4, (cuuint32_t)(kTileX + 2 * c->cfg.radius),
-                               (cuuint32_t)(kTileY + 2 * c->cfg.radius), 2};
+    const cuuint32_t box[4] = {mixed ? 8u : 4u, (cuuint32_t)(kTileX + 2 * c->cfg.radius),
+                               (cuuint32_t)(kTileY + 2 * c->cfg.radius), mixed ? 1u : 2u};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = reinterpret_cast<EncodeTiledFn>(fn)(
-        &c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->ring, dims, strides, box, estr,
+        &c->tmap, mixed ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->ring, dims,
+        strides, box, estr,
         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? ESIM_AD_OK : ESIM_AD_ECUDA;
@@ -245,7 +257,8 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         delete c;
         return ESIM_AD_ECUDA;
     }
-    c->smem_bytes = (int)wlr_smem_bytes(cfg->radius, max_smem_sm, &c->nbuf);
+    c->mixed = cfg->precision == ESIM_AD_MIXED;
+    c->smem_bytes = (int)wlr_smem_bytes(cfg->radius, c->mixed, max_smem_sm, &c->nbuf);
     const size_t N = c->N, T = (size_t)cfg->frames;
     struct {
         void** p;
@@ -281,17 +294,19 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         delete c;
         return ESIM_AD_ECUDA;
     }
-    if (encode_ring_map(c) != ESIM_AD_OK || wlr_prepare(c->smem_bytes) != cudaSuccess) {
+    if (encode_ring_map(c) != ESIM_AD_OK || wlr_prepare(c->smem_bytes, c->mixed) != cudaSuccess) {
         cudaGetLastError();
         release(c);
         delete c;
         return ESIM_AD_ECUDA;
     }
-    c->wlr_grid = wlr_grid(c->smem_bytes, num_sms);
-    c->sparse_grid = wlr_sparse_grid(num_sms);
-    // default: 16 pixels per work item, 8 items per staged CTA; ESIM_AD_SPARSE_MAX
-    // overrides it (0: always the tile-staged kernel; large: always sparse)
-    c->sparse_max = (uint32_t)c->wlr_grid * 128u;
+    c->wlr_grid = wlr_grid(c->smem_bytes, num_sms, c->mixed);
+    c->sparse_grid = wlr_sparse_grid(num_sms, c->mixed);
+    // default: frames with up to 1/8 of the pixels flagged take the sparse kernel
+    // (measured faster than tile staging at the 1-2% densities of edge-like
+    // flag patterns); ESIM_AD_SPARSE_MAX overrides it (0: always the tile-staged
+    // kernel; large: always sparse)
+    c->sparse_max = (uint32_t)(c->N / 8);
     if (const char* e = getenv("ESIM_AD_SPARSE_MAX")) {
         if (*e) c->sparse_max = (uint32_t)strtoul(e, nullptr, 10);
     }
@@ -302,8 +317,7 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
 // Copy a host frame into one of two device landing buffers on the copy
 // stream, ordered after the kernels that last read that buffer; the compute
 // stream then waits for the copy.  Returns the device-side plane pointers.
-static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, const float** rad,
-                                       const float** nor, const float** alb, const float** dep,
+static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, esim_ad_frame* dev,
                                        int* slot_out)
 {
     const size_t N = c->N;
@@ -322,50 +336,77 @@ static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, c
         esim_ad_status st = dev_alloc((void**)&c->staging[s], 10 * N * sizeof(float));
         if (st != ESIM_AD_OK) return st;
     }
-    float* base = c->staging[s];
-    const int ch = c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1;
+    unsigned char* base = reinterpret_cast<unsigned char*>(c->staging[s]);
     if (cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[s], 0) != cudaSuccess) return ESIM_AD_ECUDA;
-    struct {
-        const float* src;
-        size_t off, n;
-    } cp[] = {{f->radiance, 0, ch * N}, {f->normal, 3 * N, 3 * N}, {f->albedo, 6 * N, 3 * N},
-              {f->depth, 9 * N, N}};
-    for (auto& k : cp)
-        if (cudaMemcpyAsync(base + k.off, k.src, k.n * sizeof(float), cudaMemcpyHostToDevice,
+    // landing layout: radiance at 0 (up to 3N floats), features after it
+    const size_t rad_bytes = c->cfg.radiance_fmt == ESIM_AD_LOGLUMA_F16 ? N * 2
+                           : (c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1) * N * 4;
+    struct Copy {
+        const void* src;
+        size_t off, bytes;
+    };
+    Copy cp[4];
+    int n = 0;
+    cp[n++] = {f->radiance, 0, rad_bytes};
+    *dev = *f;
+    dev->on_host = 0;
+    dev->radiance = base;
+    if (c->cfg.feature_fmt == ESIM_AD_FEAT_BF16) {
+        cp[n++] = {f->features, 12 * N, 7 * N * 2};
+        dev->features = base + 12 * N;
+    } else {
+        cp[n++] = {f->normal, 12 * N, 3 * N * 4};
+        cp[n++] = {f->albedo, 24 * N, 3 * N * 4};
+        cp[n++] = {f->depth, 36 * N, N * 4};
+        dev->normal = reinterpret_cast<const float*>(base + 12 * N);
+        dev->albedo = reinterpret_cast<const float*>(base + 24 * N);
+        dev->depth = reinterpret_cast<const float*>(base + 36 * N);
+    }
+    for (int k = 0; k < n; ++k)
+        if (cudaMemcpyAsync(base + cp[k].off, cp[k].src, cp[k].bytes, cudaMemcpyHostToDevice,
                             c->copy_stream) != cudaSuccess)
             return ESIM_AD_ECUDA;
     if (cudaEventRecord(c->ev_copied[s], c->copy_stream) != cudaSuccess) return ESIM_AD_ECUDA;
     if (cudaStreamWaitEvent(c->stream, c->ev_copied[s], 0) != cudaSuccess) return ESIM_AD_ECUDA;
-    *rad = base;
-    *nor = base + 3 * N;
-    *alb = base + 6 * N;
-    *dep = base + 9 * N;
     *slot_out = s;
     c->staging_next ^= 1;
     return ESIM_AD_OK;
 }
 
-esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
+esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
 {
-    if (!c || !f || !f->radiance || !f->normal || !f->albedo || !f->depth) return ESIM_AD_EINVAL;
+    if (!c || !fin || !fin->radiance) return ESIM_AD_EINVAL;
+    if (c->cfg.feature_fmt == ESIM_AD_FEAT_BF16 ? !fin->features
+                                                : (!fin->normal || !fin->albedo || !fin->depth))
+        return ESIM_AD_EINVAL;
     if (c->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
     DeviceGuard guard(c->device);
-    const float *rad = f->radiance, *nor = f->normal, *alb = f->albedo, *dep = f->depth;
+    esim_ad_frame staged;
+    const esim_ad_frame* f = fin;
     int slot = -1;
-    if (f->on_host) {
-        esim_ad_status st = stage_host_frame(c, f, &rad, &nor, &alb, &dep, &slot);
+    if (fin->on_host) {
+        esim_ad_status st = stage_host_frame(c, fin, &staged, &slot);
         if (st != ESIM_AD_OK) return st;
+        f = &staged;
     }
     const int t = (int)(c->t % 0x7fffffff);
     const bool adaptive_test = c->cfg.mode == ESIM_AD_ADAPTIVE && c->t > 0;
     if (cudaMemsetAsync(c->ctrl, 0, kCtrlPerFrameBytes, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
 
     IngestParams ip;
-    ip.rad = rad;
-    ip.normal = nor;
-    ip.albedo = alb;
-    ip.depth = dep;
-    ip.rad_ch = c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1;
+    ip.rad = f->radiance;
+    ip.normal = f->normal;
+    ip.albedo = f->albedo;
+    ip.depth = f->depth;
+    ip.feat_bf16 = reinterpret_cast<const unsigned short*>(f->features);
+    ip.rad_fmt = c->cfg.radiance_fmt;
+    ip.feat_fmt = c->cfg.feature_fmt;
+    ip.mixed = c->mixed ? 1 : 0;
+    for (int j = 0; j < 7; ++j) {
+        const float fs = (c->cfg.feature_fmt == ESIM_AD_FEAT_BF16 || c->mixed) ? c->cfg.feature_scale[j] : 1.0f;
+        ip.fscale[j] = fs;
+        ip.inv_fscale[j] = 1.0f / fs;
+    }
     ip.W = c->W;
     ip.H = c->H;
     ip.tiles_x = c->tiles_x;
@@ -409,8 +450,12 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
     wp.C = c->cfg.contrast;
     wp.s_coord = (float)(kExp2Scale / c->cfg.h);
     wp.s_coord_px = (float)(kExp2Scale / ((double)c->cfg.h * c->cfg.radius));
-    for (int j = 0; j < 7; ++j)
+    wp.mixed = c->mixed ? 1 : 0;
+    for (int j = 0; j < 7; ++j) {
         wp.s_feat[j] = (float)(kExp2Scale / ((double)c->cfg.h * c->cfg.bandwidth[j]));
+        wp.fscale[j] = c->mixed ? c->cfg.feature_scale[j] : 1.0f;
+        wp.q_scale[j] = (float)((double)wp.s_feat[j] * wp.fscale[j]);
+    }
     wp.ridge = c->cfg.ridge;
     wp.ring = c->ring;
     wp.state = c->state;
@@ -429,11 +474,11 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* f)
     {
         ProfScope ps(c, 1);
         const int grid = wp.dense ? (c->n_tiles < c->wlr_grid ? c->n_tiles : c->wlr_grid) : c->wlr_grid;
-        if (launch_wlr(c->tmap, wp, grid, c->smem_bytes, c->stream) != cudaSuccess)
+        if (launch_wlr(c->tmap, wp, c->mixed, grid, c->smem_bytes, c->stream) != cudaSuccess)
             return ESIM_AD_ECUDA;
         // adaptive frames: the sparse kernel takes the frame when few pixels are
         // flagged; each of the two launches returns at once on the other's frames
-        if (!wp.dense && launch_wlr_sparse(wp, c->sparse_grid, c->stream) != cudaSuccess)
+        if (!wp.dense && launch_wlr_sparse(wp, c->mixed, c->sparse_grid, c->stream) != cudaSuccess)
             return ESIM_AD_ECUDA;
         c->prof_kernels += wp.dense ? 1 : 2;
     }
@@ -595,6 +640,7 @@ esim_ad_status esim_ad_stats_get(esim_ad_ctx* c, esim_ad_stats* out)
     out->regressions = h.regressions;
     out->events = h.ev_cum;
     out->pixels = c->N;
+    out->fp64_solves = h.fp64_solves;
     return ESIM_AD_OK;
 }
 

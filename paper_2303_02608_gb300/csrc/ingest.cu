@@ -2,8 +2,9 @@
 // the frame).
 //
 // Per pixel: luminance -> log brightness y = ln(Y + eps) (Section 1.1,
-// Section 2.1: y := L = log E), write (y, features) into the ring slot of
-// this frame, then, in adaptive mode, evaluate the test of Proposition 1
+// Section 2.1: y := L = log E; or y as given in FP16 by the renderer), write
+// (y, features) into the ring slot of this frame (FP32, or FP16 + BF16 in the
+// mixed form), then, in adaptive mode, evaluate the test of Proposition 1
 // (Eqs. 6-9) with the model kept since the pixel's last event:
 //     Delta R = (beta^T (x^c - xhat^c))^2 >= C^2   ->   flag the pixel.
 // The image-coordinate part of x^c - xhat^c is zero (same pixel), so only the
@@ -32,22 +33,51 @@ __global__ void __launch_bounds__(kTilePix) ingest_test_kernel(IngestParams p)
     int flag = 0;
     if (inside) {
         const size_t i = (size_t)y * p.W + x;
-        float Y;
-        if (p.rad_ch == 3) {
-            // Rec.709 luminance of the RGB radiance
-            Y = 0.2126f * __ldg(p.rad + i) + 0.7152f * __ldg(p.rad + N + i) +
-                0.0722f * __ldg(p.rad + 2 * N + i);
+        float yv;
+        if (p.rad_fmt == ESIM_AD_LOGLUMA_F16) {
+            yv = __half2float(reinterpret_cast<const __half*>(p.rad)[i]);
         } else {
-            Y = __ldg(p.rad + i);
+            const float* rad = reinterpret_cast<const float*>(p.rad);
+            float Y;
+            if (p.rad_fmt == ESIM_AD_RGB_F32) {
+                // Rec.709 luminance of the RGB radiance
+                Y = 0.2126f * __ldg(rad + i) + 0.7152f * __ldg(rad + N + i) + 0.0722f * __ldg(rad + 2 * N + i);
+            } else {
+                Y = __ldg(rad + i);
+            }
+            yv = logf(Y + p.log_eps);
         }
-        const float yv = logf(Y + p.log_eps);
-        const float n0 = __ldg(p.normal + i), n1 = __ldg(p.normal + N + i),
-                    n2 = __ldg(p.normal + 2 * N + i);
-        const float d = __ldg(p.depth + i);
-        const float a0 = __ldg(p.albedo + i), a1 = __ldg(p.albedo + N + i),
-                    a2 = __ldg(p.albedo + 2 * N + i);
-        p.ring[(size_t)(2 * p.slot) * N + i] = make_float4(yv, n0, n1, n2);
-        p.ring[(size_t)(2 * p.slot + 1) * N + i] = make_float4(d, a0, a1, a2);
+        float f[7];   // normal xyz, depth, albedo rgb
+        if (p.feat_fmt == ESIM_AD_FEAT_BF16) {
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+                f[j] = __uint_as_float((uint32_t)__ldg(p.feat_bf16 + j * N + i) << 16) * p.fscale[j];
+        } else {
+            f[0] = __ldg(p.normal + i);
+            f[1] = __ldg(p.normal + N + i);
+            f[2] = __ldg(p.normal + 2 * N + i);
+            f[3] = __ldg(p.depth + i);
+            f[4] = __ldg(p.albedo + i);
+            f[5] = __ldg(p.albedo + N + i);
+            f[6] = __ldg(p.albedo + 2 * N + i);
+        }
+        if (p.mixed) {
+            // FP16 log brightness and BF16 features; the test below sees the
+            // stored (dequantised) values, as the regression will
+            unsigned short q[7];
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                q[j] = __bfloat16_as_ushort(__float2bfloat16_rn(f[j] * p.inv_fscale[j]));
+                f[j] = __uint_as_float((uint32_t)q[j] << 16) * p.fscale[j];
+            }
+            reinterpret_cast<uint4*>(p.ring)[(size_t)p.slot * N + i] =
+                pack_mixed(__half_as_ushort(__float2half_rn(yv)), q);
+        } else {
+            float4* ring = reinterpret_cast<float4*>(p.ring);
+            ring[(size_t)(2 * p.slot) * N + i] = make_float4(yv, f[0], f[1], f[2]);
+            ring[(size_t)(2 * p.slot + 1) * N + i] = make_float4(f[3], f[4], f[5], f[6]);
+        }
+        const float n0 = f[0], n1 = f[1], n2 = f[2], d = f[3], a0 = f[4], a1 = f[5], a2 = f[6];
         if (p.test) {
             // beta^T (x^c - xhat) = sigma - beta . xhat, sigma = beta . x^c kept in the model
             const float4 b0 = p.state[i];

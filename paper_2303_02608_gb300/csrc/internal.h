@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,13 +36,38 @@ struct Ctrl {
     unsigned long long ev_cum;      // events since init/reset
     unsigned long long regressions; // pixels regressed since init/reset
     unsigned long long neighbours;  // (pixel, neighbour) pairs regressed
+    unsigned long long fp64_solves; // mixed form: systems re-solved in FP64
     uint32_t status;                // sticky kStatus* bits
     uint32_t pad2;
 };
 constexpr size_t kCtrlPerFrameBytes = 16;
 
-// Ring of the last T frames: float4 planes [2T][H][W]; plane 2*slot holds
-// (y, normal xyz), plane 2*slot+1 holds (depth, albedo rgb).
+// Ring of the last T frames.  FP32 form: float4 planes [2T][H][W]; plane
+// 2*slot holds (y, normal xyz), plane 2*slot+1 holds (depth, albedo rgb).
+// Mixed form: one 16-byte record per pixel, planes [T][H][W] of uint4
+//   x = y (FP16) | n_x (BF16) << 16,  y = n_y | n_z << 16,
+//   z = depth | a_r << 16,            w = a_g | a_b << 16
+// where each BF16 feature q_j stores x_j / feature_scale_j.
+
+__host__ __device__ __forceinline__ uint4 pack_mixed(unsigned short yh, const unsigned short (&q)[7])
+{
+    return make_uint4((uint32_t)yh | ((uint32_t)q[0] << 16), (uint32_t)q[1] | ((uint32_t)q[2] << 16),
+                      (uint32_t)q[3] | ((uint32_t)q[4] << 16), (uint32_t)q[5] | ((uint32_t)q[6] << 16));
+}
+
+// Unpack a mixed record: y, then the seven stored feature values (still divided
+// by their scales).  BF16 -> FP32 is exact (a 16-bit shift).
+__device__ __forceinline__ void unpack_mixed(const uint4 v, float& y, float (&q)[7])
+{
+    y = __half2float(__ushort_as_half((unsigned short)(v.x & 0xffffu)));
+    q[0] = __uint_as_float(v.x & 0xffff0000u);
+    q[1] = __uint_as_float(v.y << 16);
+    q[2] = __uint_as_float(v.y & 0xffff0000u);
+    q[3] = __uint_as_float(v.z << 16);
+    q[4] = __uint_as_float(v.z & 0xffff0000u);
+    q[5] = __uint_as_float(v.w << 16);
+    q[6] = __uint_as_float(v.w & 0xffff0000u);
+}
 // Model state: float4 planes [4][H][W]:
 //   0: beta (normal xyz, depth)   1: beta (albedo rgb), sigma = beta . x^c
 //   2: x^c (normal xyz, depth)    3: x^c (albedo rgb), L_last
@@ -63,16 +90,21 @@ __host__ __device__ __forceinline__ float dot7(const float4 b0, const float4 b1,
 }
 
 struct IngestParams {
-    const float* rad;      // [C][H][W]
-    const float* normal;   // [3][H][W]
-    const float* albedo;   // [3][H][W]
-    const float* depth;    // [H][W]
-    int rad_ch;            // 1 or 3
+    const void* rad;       // [C][H][W] float32, or [H][W] FP16 log brightness
+    const float* normal;   // [3][H][W] (FEAT_F32)
+    const float* albedo;   // [3][H][W] (FEAT_F32)
+    const float* depth;    // [H][W]    (FEAT_F32)
+    const unsigned short* feat_bf16;  // [7][H][W] BF16 bits (FEAT_BF16)
+    int rad_fmt;           // ESIM_AD_LUMA_F32 | RGB_F32 | LOGLUMA_F16
+    int feat_fmt;          // ESIM_AD_FEAT_F32 | FEAT_BF16
+    int mixed;             // ring in the mixed form
+    float fscale[7];       // feature_scale
+    float inv_fscale[7];
     int W, H, tiles_x;
     int slot;              // ring slot of this frame
     int test;              // 1: Proposition-1 test; 0: flag every pixel
     float log_eps, C;
-    float4* ring;
+    void* ring;
     const float4* state;
     uint8_t* flag;
     int32_t* nev;
@@ -87,6 +119,7 @@ struct IngestParams {
 
 struct WlrParams {
     int W, H, r, T, t, n_tau, tiles_x, n_tiles;
+    int mixed;             // ring in the mixed form (FP16/BF16), refined + FP64-fallback solve
     int nbuf;              // staged frames in flight per CTA (2 or 3)
     int dense;             // 1: every tile and pixel; 0: tiles from the queue
     int init;              // 1: frame 0 (initialise models, no events)
@@ -95,8 +128,10 @@ struct WlrParams {
     float s_coord_px;      // regressor scale of a one-pixel coordinate offset
     float s_coord;         // regressor scale of the coordinate unit (offset / r)
     float s_feat[7];       // regressor scale per feature: k / (h b_j)
+    float q_scale[7];      // mixed form: regressor scale per stored value, s_feat * feature_scale
+    float fscale[7];       // mixed form: feature_scale
     float ridge;
-    const float4* ring;
+    const void* ring;
     float4* state;
     float* alpha;
     int32_t* nev;
@@ -126,13 +161,13 @@ struct EventParams {
 };
 
 cudaError_t launch_ingest(const IngestParams& p, int n_tiles, cudaStream_t s);
-cudaError_t wlr_prepare(int smem_bytes);
-size_t wlr_smem_bytes(int r, int max_smem_per_sm, int* nbuf);
-int wlr_grid(int smem_bytes, int num_sms);
-int wlr_sparse_grid(int num_sms);
-cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, int grid, int smem_bytes,
-                       cudaStream_t s);
-cudaError_t launch_wlr_sparse(const WlrParams& p, int grid, cudaStream_t s);
+cudaError_t wlr_prepare(int smem_bytes, bool mixed);
+size_t wlr_smem_bytes(int r, bool mixed, int max_smem_per_sm, int* nbuf);
+int wlr_grid(int smem_bytes, int num_sms, bool mixed);
+int wlr_sparse_grid(int num_sms, bool mixed);
+cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, bool mixed, int grid,
+                       int smem_bytes, cudaStream_t s);
+cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s);
 cudaError_t launch_events(const EventParams& p, cudaStream_t s);
 cudaError_t launch_event_write(const EventParams& p, cudaStream_t s);
 

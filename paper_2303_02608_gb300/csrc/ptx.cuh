@@ -79,6 +79,12 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Hint the next use of a global line into L1 (never faults; no effect on values).
+__device__ __forceinline__ void prefetch_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // 2^x on the MUFU unit (ex2.approx, flush-to-zero).
 __device__ __forceinline__ float ex2_approx(float x)
 {

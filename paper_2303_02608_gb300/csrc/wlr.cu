@@ -43,27 +43,30 @@ struct Acc {
     float B[NZ];
 };
 
-// One neighbour: y and the raw features (h0 = y, normal xyz; h1 = depth, albedo rgb).
-__device__ __forceinline__ void accumulate(Acc& a, const float4 h0, const float4 h1, float u1,
-                                           float u2, float en0, const float* __restrict__ sf,
+// One neighbour with log brightness y and seven feature values f (raw
+// features, or the stored values of the mixed form); sc[j] turns a feature
+// difference into its regressor, cf[j] = sc[j] * f_centre[j].
+__device__ __forceinline__ void accum_core(Acc& a, float y, float f0, float f1, float f2, float f3,
+                                           float f4, float f5, float f6, float u1, float u2,
+                                           float en0, const float* __restrict__ sc,
                                            const float (&cf)[7])
 {
     float u[NZ];
     u[0] = 1.0f;
     u[1] = u1;
     u[2] = u2;
-    u[3] = fmaf(h0.y, sf[0], -cf[0]);
-    u[4] = fmaf(h0.z, sf[1], -cf[1]);
-    u[5] = fmaf(h0.w, sf[2], -cf[2]);
-    u[6] = fmaf(h1.x, sf[3], -cf[3]);
-    u[7] = fmaf(h1.y, sf[4], -cf[4]);
-    u[8] = fmaf(h1.z, sf[5], -cf[5]);
-    u[9] = fmaf(h1.w, sf[6], -cf[6]);
+    u[3] = fmaf(f0, sc[0], -cf[0]);
+    u[4] = fmaf(f1, sc[1], -cf[1]);
+    u[5] = fmaf(f2, sc[2], -cf[2]);
+    u[6] = fmaf(f3, sc[3], -cf[3]);
+    u[7] = fmaf(f4, sc[4], -cf[4]);
+    u[8] = fmaf(f5, sc[5], -cf[5]);
+    u[9] = fmaf(f6, sc[6], -cf[6]);
     float en = en0;  // -(u1^2 + u2^2)
 #pragma unroll
     for (int j = 3; j < NZ; ++j) en = fmaf(-u[j], u[j], en);
     const float w = ex2_approx(en);
-    const float wy = w * h0.x;
+    const float wy = w * y;
     float wu[NZ];
     wu[0] = w;
 #pragma unroll
@@ -78,6 +81,23 @@ __device__ __forceinline__ void accumulate(Acc& a, const float4 h0, const float4
     a.B[0] += wy;
 #pragma unroll
     for (int i = 1; i < NZ; ++i) a.B[i] = fmaf(wy, u[i], a.B[i]);
+}
+
+// FP32 ring: h0 = (y, normal xyz), h1 = (depth, albedo rgb).
+__device__ __forceinline__ void accumulate(Acc& a, const float4 h0, const float4 h1, float u1,
+                                           float u2, float en0, const float* __restrict__ sf,
+                                           const float (&cf)[7])
+{
+    accum_core(a, h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w, u1, u2, en0, sf, cf);
+}
+
+// Mixed ring: one 16-byte record (FP16 y, BF16 stored features).
+__device__ __forceinline__ void accumulate(Acc& a, const uint4 v, float u1, float u2, float en0,
+                                           const float* __restrict__ qs, const float (&cf)[7])
+{
+    float y, q[7];
+    unpack_mixed(v, y, q);
+    accum_core(a, y, q[0], q[1], q[2], q[3], q[4], q[5], q[6], u1, u2, en0, qs, cf);
 }
 
 // Ridge, Jacobi equilibration and Cholesky solve of the packed 10x10 system.
@@ -133,16 +153,129 @@ __device__ __forceinline__ void solve(Acc& a, const float (&s2)[NZ], float ridge
     for (int i = 0; i < NZ; ++i) theta[i] *= dsc[i];
 }
 
+// Mixed-form solve: FP32 Cholesky of the equilibrated system plus one step of
+// iterative refinement (the residual taken against the unfactored matrix),
+// and an FP64 Cholesky re-solve when the condition number estimated from the
+// factor's diagonal, (max L_ii / min L_ii)^2, exceeds 1e6.  Returns 1 if the
+// FP64 path ran.
+__device__ __noinline__ int solve_mixed(Acc& a, const float (&s2)[NZ], float ridge,
+                                        float (&theta)[NZ])
+{
+    const float W = a.G[0];
+#pragma unroll
+    for (int j = 1; j < NZ; ++j) a.G[tri(j, j)] = fmaf(ridge * W, s2[j], a.G[tri(j, j)]);
+    float dsc[NZ];
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) dsc[i] = rsqrtf(a.G[tri(i, i)]);
+    float A[NG], b[NZ];
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) A[tri(i, j)] = a.G[tri(i, j)] * (dsc[i] * dsc[j]);
+        b[i] = a.B[i] * dsc[i];
+    }
+    // factor into a.G
+    float inv[NZ];
+    float lmin = 3.4e38f, lmax = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+        float sj = A[tri(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) sj = fmaf(-a.G[tri(j, k)], a.G[tri(j, k)], sj);
+        sj = fmaxf(sj, 1e-20f);
+        const float l = sqrtf(sj);
+        lmin = fminf(lmin, l);
+        lmax = fmaxf(lmax, l);
+        a.G[tri(j, j)] = l;
+        inv[j] = 1.0f / l;
+#pragma unroll
+        for (int i = j + 1; i < NZ; ++i) {
+            float v = A[tri(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v = fmaf(-a.G[tri(i, k)], a.G[tri(j, k)], v);
+            a.G[tri(i, j)] = v * inv[j];
+        }
+    }
+    auto llt_solve = [&](const float (&rhs)[NZ], float (&x)[NZ]) {
+        float z[NZ];
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            float v = rhs[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) v = fmaf(-a.G[tri(i, k)], z[k], v);
+            z[i] = v * inv[i];
+        }
+#pragma unroll
+        for (int i = NZ - 1; i >= 0; --i) {
+            float v = z[i];
+#pragma unroll
+            for (int k = i + 1; k < NZ; ++k) v = fmaf(-a.G[tri(k, i)], x[k], v);
+            x[i] = v * inv[i];
+        }
+    };
+    float th[NZ];
+    llt_solve(b, th);
+    // one refinement step: r = b - A th, th += (L L^T)^-1 r
+    float r[NZ];
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) {
+        float v = b[i];
+#pragma unroll
+        for (int j = 0; j < NZ; ++j) v = fmaf(-A[i >= j ? tri(i, j) : tri(j, i)], th[j], v);
+        r[i] = v;
+    }
+    float dth[NZ];
+    llt_solve(r, dth);
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) th[i] += dth[i];
+    int used64 = 0;
+    const float ratio = lmax / lmin;
+    if (ratio * ratio > 1e6f) {
+        // FP64 Cholesky of the same equilibrated FP32 system
+        double L[NG];
+        double dinv[NZ];
+        for (int j = 0; j < NZ; ++j) {
+            double sj = (double)A[tri(j, j)];
+            for (int k = 0; k < j; ++k) sj -= L[tri(j, k)] * L[tri(j, k)];
+            sj = sj > 1e-300 ? sj : 1e-300;
+            const double l = sqrt(sj);
+            L[tri(j, j)] = l;
+            dinv[j] = 1.0 / l;
+            for (int i = j + 1; i < NZ; ++i) {
+                double v = (double)A[tri(i, j)];
+                for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
+                L[tri(i, j)] = v * dinv[j];
+            }
+        }
+        double z[NZ], x[NZ];
+        for (int i = 0; i < NZ; ++i) {
+            double v = (double)b[i];
+            for (int k = 0; k < i; ++k) v -= L[tri(i, k)] * z[k];
+            z[i] = v * dinv[i];
+        }
+        for (int i = NZ - 1; i >= 0; --i) {
+            double v = z[i];
+            for (int k = i + 1; k < NZ; ++k) v -= L[tri(k, i)] * x[k];
+            x[i] = v * dinv[i];
+        }
+        for (int i = 0; i < NZ; ++i) th[i] = (float)x[i];
+        used64 = 1;
+    }
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) theta[i] = th[i] * dsc[i];
+    return used64;
+}
+
 // Eq. 1 at a fixed frame time, and the model update of Fig. 1.
-__device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const float (&theta)[NZ],
-                                     const float* __restrict__ sf)
+template <bool kMixed>
+__device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const float (&theta)[NZ])
 {
     const size_t N = (size_t)p.W * p.H;
     const size_t i = (size_t)cy * p.W + cx;
     const float alpha = theta[0];
     float bf[7];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) bf[j] = theta[3 + j] * sf[j];
+    for (int j = 0; j < 7; ++j) bf[j] = theta[3 + j] * p.s_feat[j];
     p.alpha[i] = alpha;
     float L;
     if (p.init) {
@@ -158,22 +291,52 @@ __device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const f
         atomicAdd(&p.chunk_cnt[i / kChunk], (uint32_t)n);
     }
     const int slot = p.t % p.T;
-    const float4 x0 = p.ring[(size_t)(2 * slot) * N + i];
-    const float4 x1 = p.ring[(size_t)(2 * slot + 1) * N + i];
+    float x[7];
+    if (kMixed) {
+        float y, q[7];
+        unpack_mixed(reinterpret_cast<const uint4*>(p.ring)[(size_t)slot * N + i], y, q);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) x[j] = q[j] * p.fscale[j];
+    } else {
+        const float4* ring = reinterpret_cast<const float4*>(p.ring);
+        const float4 x0 = ring[(size_t)(2 * slot) * N + i];
+        const float4 x1 = ring[(size_t)(2 * slot + 1) * N + i];
+        x[0] = x0.y; x[1] = x0.z; x[2] = x0.w; x[3] = x1.x; x[4] = x1.y; x[5] = x1.z; x[6] = x1.w;
+    }
     const float4 b0 = make_float4(bf[0], bf[1], bf[2], bf[3]);
     float4 b1 = make_float4(bf[4], bf[5], bf[6], 0.0f);
-    b1.w = dot7(b0, b1, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w);
+    b1.w = dot7(b0, b1, x[0], x[1], x[2], x[3], x[4], x[5], x[6]);
     p.state[i] = b0;
     p.state[N + i] = b1;
-    p.state[2 * N + i] = make_float4(x0.y, x0.z, x0.w, x1.x);
-    p.state[3 * N + i] = make_float4(x1.y, x1.z, x1.w, L);
+    p.state[2 * N + i] = make_float4(x[0], x[1], x[2], x[3]);
+    p.state[3 * N + i] = make_float4(x[4], x[5], x[6], L);
+}
+
+// Regress one pixel from its reduced sums, then emit (both forms).
+template <bool kMixed>
+__device__ __forceinline__ void solve_and_emit(const WlrParams& p, Acc& acc, int cx, int cy,
+                                               unsigned long long* fp64_count)
+{
+    float s2[NZ];
+    s2[0] = 0.0f;
+    s2[1] = p.s_coord * p.s_coord;
+    s2[2] = s2[1];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) s2[3 + j] = p.s_feat[j] * p.s_feat[j];
+    float theta[NZ];
+    if (kMixed) {
+        if (solve_mixed(acc, s2, p.ridge, theta)) atomicAdd(fp64_count, 1ull);
+    } else {
+        solve(acc, s2, p.ridge, theta);
+    }
+    emit<kMixed>(p, cx, cy, theta);
 }
 
 // End of a regression launch: add this CTA's work counters, record a timeout,
 // and, when events are emitted, take a ticket; the last CTA to finish scans
 // the per-chunk event counts into output offsets (no CTA waits on another).
 __device__ __forceinline__ void finish(const WlrParams& p, unsigned long long pairs,
-                                       unsigned long long pix, bool timed_out)
+                                       unsigned long long pix, unsigned long long fp64, bool timed_out)
 {
     __shared__ int s_timeout, s_last;
     __shared__ int s_warp[8];
@@ -187,6 +350,7 @@ __device__ __forceinline__ void finish(const WlrParams& p, unsigned long long pa
     if (threadIdx.x == 0) {
         if (pairs) atomicAdd(&p.ctrl->neighbours, pairs);
         if (pix) atomicAdd(&p.ctrl->regressions, pix);
+        if (fp64) atomicAdd(&p.ctrl->fp64_solves, fp64);
         if (s_timeout) atomicOr(&p.ctrl->status, kStatusTimeout);
         if (p.emit_events) {
             __threadfence();
@@ -230,10 +394,10 @@ struct SmemLayout {
     int buf_bytes, nbuf, table_off, bar_off, info_off, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int r, int nbuf)
+__host__ __device__ inline SmemLayout smem_layout(int r, int nbuf, bool mixed)
 {
     SmemLayout L;
-    const int stage = 2 * (kTileX + 2 * r) * (kTileY + 2 * r) * 16;
+    const int stage = (mixed ? 1 : 2) * (kTileX + 2 * r) * (kTileY + 2 * r) * 16;
     L.buf_bytes = (stage + 127) & ~127;
     L.nbuf = nbuf;
     L.bar_off = nbuf * L.buf_bytes;
@@ -250,16 +414,16 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int nbuf)
 // stage in order and then counts itself out of the buffer; the warp that
 // releases a buffer last issues that buffer's next copy at once, so no warp
 // waits for another and copies start as early as possible.
-template <bool kDense>
+template <bool kDense, bool kMixed>
 __global__ void __launch_bounds__(kTilePix, 2)
     wlr_kernel(const __grid_constant__ CUtensorMap tmap, const WlrParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations must be 128-byte aligned; the allocation has 128 bytes of slack
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    const SmemLayout L = smem_layout(p.r, p.nbuf);
-    const int plane = p.sw * p.sh;                      // float4 per half-plane
-    const uint32_t stage_bytes = (uint32_t)(2 * plane * 16);
+    const SmemLayout L = smem_layout(p.r, p.nbuf, kMixed);
+    const int plane = p.sw * p.sh;                      // 16-byte records per half-plane
+    const uint32_t stage_bytes = (uint32_t)((kMixed ? 1 : 2) * plane * 16);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     int* released = reinterpret_cast<int*>(full + L.nbuf);
     StageInfo* info = reinterpret_cast<StageInfo*>(smem + L.info_off);
@@ -368,13 +532,14 @@ __global__ void __launch_bounds__(kTilePix, 2)
         pr->k = k + 1;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&full[b], stage_bytes);
-        tma_load_4d(smem + b * L.buf_bytes, &tmap, &full[b], 0, tx0 - p.r, ty0 - p.r, 2 * slot);
+        tma_load_4d(smem + b * L.buf_bytes, &tmap, &full[b], 0, tx0 - p.r, ty0 - p.r,
+                    kMixed ? slot : 2 * slot);
         __threadfence_block();
         pr->issued = S + 1;
     };
     // ---- consumer state
     Acc acc;
-    const float* sf = p.s_feat;
+    const float* sf = kMixed ? p.q_scale : p.s_feat;   // regressor scale of a stored value
     float cf[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) cf[j] = 0.0f;
@@ -382,10 +547,11 @@ __global__ void __launch_bounds__(kTilePix, 2)
     int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0;
     bool active = false;
     bool timed_out = false;
-    __shared__ unsigned long long s_pairs, s_pix;
+    __shared__ unsigned long long s_pairs, s_pix, s_fp64;
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
         s_pix = 0ull;
+        s_fp64 = 0ull;
     }
     __syncthreads();
     if (threadIdx.x == 0)
@@ -401,6 +567,14 @@ __global__ void __launch_bounds__(kTilePix, 2)
         if (in.tile < 0) break;
         const float4* P0 = reinterpret_cast<const float4*>(smem + b * L.buf_bytes);
         const float4* P1 = P0 + plane;
+        const uint4* PM = reinterpret_cast<const uint4*>(smem + b * L.buf_bytes);
+        // accumulate the neighbour at staged index si (either ring form)
+        auto at = [&](int si, float u1, float u2, float en0) {
+            if (kMixed)
+                accumulate(acc, PM[si], u1, u2, en0, sf, cf);
+            else
+                accumulate(acc, P0[si], P1[si], u1, u2, en0, sf, cf);
+        };
         if (in.k == 0) {
             // new tile: assign lanes to its regressed pixels
             const int tx0 = (in.tile % p.tiles_x) * kTileX, ty0 = (in.tile / p.tiles_x) * kTileY;
@@ -428,15 +602,17 @@ __global__ void __launch_bounds__(kTilePix, 2)
 #pragma unroll
             for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
             if (active) {
-                const float4 c0 = P0[sy * p.sw + sx];
-                const float4 c1 = P1[sy * p.sw + sx];
-                cf[0] = c0.y * sf[0];
-                cf[1] = c0.z * sf[1];
-                cf[2] = c0.w * sf[2];
-                cf[3] = c1.x * sf[3];
-                cf[4] = c1.y * sf[4];
-                cf[5] = c1.z * sf[5];
-                cf[6] = c1.w * sf[6];
+                float c[7];
+                if (kMixed) {
+                    float yc;
+                    unpack_mixed(PM[sy * p.sw + sx], yc, c);
+                } else {
+                    const float4 c0 = P0[sy * p.sw + sx];
+                    const float4 c1 = P1[sy * p.sw + sx];
+                    c[0] = c0.y; c[1] = c0.z; c[2] = c0.w; c[3] = c1.x; c[4] = c1.y; c[5] = c1.z; c[6] = c1.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
             }
         }
         if (active) {
@@ -449,7 +625,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     float u1 = (float)dxlo * spx;
 #pragma unroll 3
                     for (int ox = dxlo; ox <= dxhi; ++ox) {
-                        accumulate(acc, P0[row + ox], P1[row + ox], u1, u2, fmaf(-u1, u1, en_row), sf, cf);
+                        at(row + ox, u1, u2, fmaf(-u1, u1, en_row));
                         u1 += spx;
                     }
                 }
@@ -458,8 +634,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
                 const int cbase = sy * p.sw + sx;
                 for (int q = sub; q < nq; q += g) {
                     const float4 e = table[q];
-                    const int si = cbase + __float_as_int(e.x);
-                    accumulate(acc, P0[si], P1[si], e.y, e.z, e.w, sf, cf);
+                    at(cbase + __float_as_int(e.x), e.y, e.z, e.w);
                 }
             } else {
                 // window clipped by the image border
@@ -470,7 +645,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     const int si = (sy + oy) * p.sw + sx + ox;
                     const float u1 = (float)ox * spx;
                     const float u2 = (float)oy * spx;
-                    accumulate(acc, P0[si], P1[si], u1, u2, -fmaf(u1, u1, u2 * u2), sf, cf);
+                    at(si, u1, u2, -fmaf(u1, u1, u2 * u2));
                     ox += g;
                     while (ox > dxhi) {
                         ox -= nx;
@@ -503,21 +678,13 @@ __global__ void __launch_bounds__(kTilePix, 2)
             if (active && sub == 0) {
                 atomicAdd(&s_pairs, (unsigned long long)((dxhi - dxlo + 1) * (dyhi - dylo + 1) * p.n_tau));
                 atomicAdd(&s_pix, 1ull);
-                float s2[NZ];
-                s2[0] = 0.0f;
-                s2[1] = p.s_coord * p.s_coord;
-                s2[2] = s2[1];
-#pragma unroll
-                for (int j = 0; j < 7; ++j) s2[3 + j] = sf[j] * sf[j];
-                float theta[NZ];
-                solve(acc, s2, p.ridge, theta);
-                emit(p, cx, cy, theta, sf);
+                solve_and_emit<kMixed>(p, acc, cx, cy, &s_fp64);
             }
         }
     }
 
     __syncthreads();   // every thread's counter updates are in before thread 0 reads them
-    finish(p, s_pairs, s_pix, timed_out || (threadIdx.x == 0 && !pr->ok));
+    finish(p, s_pairs, s_pix, s_fp64, timed_out || (threadIdx.x == 0 && !pr->ok));
 }
 
 // Sparse-frame regression.  When few pixels are flagged they lie on thin
@@ -525,16 +692,19 @@ __global__ void __launch_bounds__(kTilePix, 2)
 // item would move far more data than it feeds.  This kernel instead reads each
 // neighbour's two float4 half-planes straight from the ring through L1 (it
 // reserves almost no shared memory, so L1 keeps the overlapping windows of
-// nearby pixels).  Warps work independently: each takes the next two entries
-// of the frame's flagged-pixel list, 16 lanes per pixel split its window, and
-// the lanes are shuffle-reduced; no block-wide barrier after set-up.
+// nearby pixels).  A CTA takes the next 16 entries of the frame's flagged-pixel
+// list (neighbours within one tile, so its warps' windows overlap in L1); each
+// warp owns two of them, 16 lanes per pixel split its window, and the lanes
+// are shuffle-reduced.  Interior pixels all cost the same, so the per-block
+// barrier waits little.
+template <bool kMixed>
 __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams p)
 {
     if (p.sparse_max == 0 || *(volatile uint32_t*)&p.ctrl->flag_total > p.sparse_max)
         return;  // the tile-staged kernel's frame
     constexpr int kLanes = 16;
     __shared__ float4 table[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];
-    __shared__ unsigned long long s_pairs, s_pix;
+    __shared__ unsigned long long s_pairs, s_pix, s_fp64;
     const int side = 2 * p.r + 1, nq = side * side;
     const float spx = p.s_coord_px;
     const size_t N = (size_t)p.W * p.H;
@@ -546,21 +716,29 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
         s_pix = 0ull;
+        s_fp64 = 0ull;
     }
     __syncthreads();
     const uint32_t n_flag = *(volatile uint32_t*)&p.ctrl->flag_total;
-    const float* sf = p.s_feat;
+    const float* sf = kMixed ? p.q_scale : p.s_feat;
+    const float4* ringf = reinterpret_cast<const float4*>(p.ring);
+    const uint4* ringm = reinterpret_cast<const uint4*>(p.ring);
     const int lane = threadIdx.x & 31;
     const int sub = lane & (kLanes - 1);
     const int half = lane >> 4;
     const int slot_t = p.t % p.T;
     Acc acc;
     float cf[7];
+    __shared__ uint32_t s_base;
     for (;;) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&p.ctrl->work_next, 2u);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n_flag) break;
+        // the CTA takes 16 consecutive list entries (neighbours in one tile, so
+        // the warps' windows overlap in L1); warp w owns entries 2w and 2w+1
+        if (threadIdx.x == 0) s_base = atomicAdd(&p.ctrl->work_next, 16u);
+        __syncthreads();
+        const uint32_t blk = s_base;
+        __syncthreads();   // all have read the block before thread 0 takes the next
+        if (blk >= n_flag) break;
+        const uint32_t base = blk + 2u * (threadIdx.x >> 5);
         const uint32_t my = base + (uint32_t)half;
         const bool active = my < n_flag;
         const uint32_t pix = active ? p.flag_list[my] : 0u;
@@ -573,34 +751,59 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
         const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
         if (active) {
-            const float4 c0 = __ldg(p.ring + (size_t)(2 * slot_t) * N + pix);
-            const float4 c1 = __ldg(p.ring + (size_t)(2 * slot_t + 1) * N + pix);
-            cf[0] = c0.y * sf[0];
-            cf[1] = c0.z * sf[1];
-            cf[2] = c0.w * sf[2];
-            cf[3] = c1.x * sf[3];
-            cf[4] = c1.y * sf[4];
-            cf[5] = c1.z * sf[5];
-            cf[6] = c1.w * sf[6];
+            float c[7];
+            if (kMixed) {
+                float yc;
+                unpack_mixed(__ldg(ringm + (size_t)slot_t * N + pix), yc, c);
+            } else {
+                const float4 c0 = __ldg(ringf + (size_t)(2 * slot_t) * N + pix);
+                const float4 c1 = __ldg(ringf + (size_t)(2 * slot_t + 1) * N + pix);
+                c[0] = c0.y; c[1] = c0.z; c[2] = c0.w; c[3] = c1.x; c[4] = c1.y; c[5] = c1.z; c[6] = c1.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
             for (int k = 0; k < p.n_tau; ++k) {
                 const int slot = (p.t - k) % p.T;
-                const float4* __restrict__ R0 = p.ring + (size_t)(2 * slot) * N + pix;
-                const float4* __restrict__ R1 = p.ring + (size_t)(2 * slot + 1) * N + pix;
+                const float4* __restrict__ R0 = ringf + (size_t)(2 * slot) * N + pix;
+                const float4* __restrict__ R1 = ringf + (size_t)(2 * slot + 1) * N + pix;
+                const uint4* __restrict__ RM = ringm + (size_t)slot * N + pix;
+                auto at = [&](int d, float u1, float u2, float en0) {
+                    if (kMixed)
+                        accumulate(acc, __ldg(RM + d), u1, u2, en0, sf, cf);
+                    else
+                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, en0, sf, cf);
+                };
                 if (nx == side && ny == side) {
+                    if (k + 1 < p.n_tau && sub < side) {
+                        // pull the next frame's window rows towards L1 while this one is summed
+                        const int nslot = (p.t - k - 1) % p.T;
+                        const size_t off = (size_t)pix + (size_t)((sub - p.r) * p.W - p.r);
+                        if (kMixed) {
+                            const uint4* row = ringm + (size_t)nslot * N + off;
+                            for (int c2 = 0; c2 < side; c2 += 8) prefetch_l1(row + c2);
+                            prefetch_l1(row + side - 1);
+                        } else {
+                            const float4* row = ringf + (size_t)(2 * nslot) * N + off;
+                            for (int c2 = 0; c2 < side; c2 += 8) {
+                                prefetch_l1(row + c2);
+                                prefetch_l1(row + N + c2);
+                            }
+                            prefetch_l1(row + side - 1);
+                            prefetch_l1(row + N + side - 1);
+                        }
+                    }
 #pragma unroll 2
                     for (int q = sub; q < nq; q += kLanes) {
                         const float4 e = table[q];
-                        const int d = __float_as_int(e.x);
-                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), e.y, e.z, e.w, sf, cf);
+                        at(__float_as_int(e.x), e.y, e.z, e.w);
                     }
                 } else {
                     const int nvalid = nx * ny;
                     int ox = dxlo + sub % nx;
                     int oy = dylo + sub / nx;
                     for (int q = sub; q < nvalid; q += kLanes) {
-                        const int d = oy * p.W + ox;
                         const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, -fmaf(u1, u1, u2 * u2), sf, cf);
+                        at(oy * p.W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
                         ox += kLanes;
                         while (ox > dxhi) {
                             ox -= nx;
@@ -619,81 +822,92 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         if (active && sub == 0) {
             atomicAdd(&s_pairs, (unsigned long long)(nx * ny * p.n_tau));
             atomicAdd(&s_pix, 1ull);
-            float s2[NZ];
-            s2[0] = 0.0f;
-            s2[1] = p.s_coord * p.s_coord;
-            s2[2] = s2[1];
-#pragma unroll
-            for (int j = 0; j < 7; ++j) s2[3 + j] = sf[j] * sf[j];
-            float theta[NZ];
-            solve(acc, s2, p.ridge, theta);
-            emit(p, cx, cy, theta, sf);
+            solve_and_emit<kMixed>(p, acc, cx, cy, &s_fp64);
         }
     }
     __syncthreads();
-    finish(p, s_pairs, s_pix, false);
+    finish(p, s_pairs, s_pix, s_fp64, false);
 }
 
-int wlr_sparse_grid(int num_sms)
+int wlr_sparse_grid(int num_sms, bool mixed)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel, kTilePix, 0) != cudaSuccess ||
-        per_sm < 1) {
+    const cudaError_t e = mixed
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel<true>, kTilePix, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel<false>, kTilePix, 0);
+    if (e != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
     return per_sm * num_sms;
 }
 
-cudaError_t launch_wlr_sparse(const WlrParams& p, int grid, cudaStream_t s)
+cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s)
 {
-    wlr_sparse_kernel<<<grid, kTilePix, 0, s>>>(p);
+    if (mixed)
+        wlr_sparse_kernel<true><<<grid, kTilePix, 0, s>>>(p);
+    else
+        wlr_sparse_kernel<false><<<grid, kTilePix, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-SmemLayout host_layout(int r, int max_smem_per_sm)
+SmemLayout host_layout(int r, bool mixed, int max_smem_per_sm)
 {
     // three stages in flight when two CTAs still fit on an SM, else two
-    SmemLayout L3 = smem_layout(r, 3);
+    SmemLayout L3 = smem_layout(r, 3, mixed);
     if (2 * (L3.total + 1024) <= max_smem_per_sm) return L3;
-    return smem_layout(r, 2);
+    return smem_layout(r, 2, mixed);
 }
 
-size_t wlr_smem_bytes(int r, int max_smem_per_sm, int* nbuf)
+size_t wlr_smem_bytes(int r, bool mixed, int max_smem_per_sm, int* nbuf)
 {
-    const SmemLayout L = host_layout(r, max_smem_per_sm);
+    const SmemLayout L = host_layout(r, mixed, max_smem_per_sm);
     *nbuf = L.nbuf;
     return (size_t)L.total;
 }
 
-cudaError_t wlr_prepare(int smem_bytes)
+template <bool kMixed>
+static cudaError_t prepare_one(int smem_bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(wlr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(wlr_kernel<true, kMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(wlr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(wlr_kernel<false, kMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_bytes);
 }
 
-int wlr_grid(int smem_bytes, int num_sms)
+cudaError_t wlr_prepare(int smem_bytes, bool mixed)
+{
+    return mixed ? prepare_one<true>(smem_bytes) : prepare_one<false>(smem_bytes);
+}
+
+int wlr_grid(int smem_bytes, int num_sms, bool mixed)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_kernel<false>, kTilePix, smem_bytes) !=
-            cudaSuccess ||
-        per_sm < 1) {
+    const cudaError_t e = mixed
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_kernel<false, true>, kTilePix, smem_bytes)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_kernel<false, false>, kTilePix, smem_bytes);
+    if (e != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
     return per_sm * num_sms;
 }
 
-cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, int grid, int smem_bytes,
-                       cudaStream_t s)
+cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, bool mixed, int grid,
+                       int smem_bytes, cudaStream_t s)
 {
-    if (p.dense)
-        wlr_kernel<true><<<grid, kTilePix, smem_bytes, s>>>(tmap, p);
-    else
-        wlr_kernel<false><<<grid, kTilePix, smem_bytes, s>>>(tmap, p);
+    if (mixed) {
+        if (p.dense)
+            wlr_kernel<true, true><<<grid, kTilePix, smem_bytes, s>>>(tmap, p);
+        else
+            wlr_kernel<false, true><<<grid, kTilePix, smem_bytes, s>>>(tmap, p);
+    } else {
+        if (p.dense)
+            wlr_kernel<true, false><<<grid, kTilePix, smem_bytes, s>>>(tmap, p);
+        else
+            wlr_kernel<false, false><<<grid, kTilePix, smem_bytes, s>>>(tmap, p);
+    }
     return cudaGetLastError();
 }
 

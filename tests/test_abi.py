@@ -45,8 +45,9 @@ def test_struct_layout_matches_header(lib):
 #include <stddef.h>
 #include "esim_ad.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(esim_ad_config), offsetof(esim_ad_config, contrast),
-         offsetof(esim_ad_config, event_capacity), sizeof(esim_ad_frame), offsetof(esim_ad_frame, on_host),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(esim_ad_config), offsetof(esim_ad_config, contrast),
+         offsetof(esim_ad_config, event_capacity), offsetof(esim_ad_config, feature_scale),
+         sizeof(esim_ad_frame), offsetof(esim_ad_frame, on_host), offsetof(esim_ad_frame, features),
          sizeof(esim_ad_event), sizeof(esim_ad_stats));
   return 0;
 }
@@ -58,8 +59,9 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(lib.esim_ad_config), lib.esim_ad_config.contrast.offset,
-            lib.esim_ad_config.event_capacity.offset, ctypes.sizeof(lib.esim_ad_frame),
-            lib.esim_ad_frame.on_host.offset, lib.EVENT_DTYPE.itemsize, ctypes.sizeof(lib.esim_ad_stats)]
+            lib.esim_ad_config.event_capacity.offset, lib.esim_ad_config.feature_scale.offset,
+            ctypes.sizeof(lib.esim_ad_frame), lib.esim_ad_frame.on_host.offset, lib.esim_ad_frame.features.offset,
+            lib.EVENT_DTYPE.itemsize, ctypes.sizeof(lib.esim_ad_stats)]
     assert got == want
 
 
@@ -69,7 +71,7 @@ def _bad_configs(lib):
     for k, v in [("width", 0), ("height", -1), ("width", 70000), ("radius", 0), ("radius", 16),
                  ("frames", 0), ("frames", 17), ("mode", 2), ("radiance_fmt", 5), ("contrast", 0.0),
                  ("contrast", float("nan")), ("h", -1.0), ("ridge", 0.0), ("log_eps", -1.0),
-                 ("event_capacity", 0)]:
+                 ("event_capacity", 0), ("feature_fmt", 2), ("precision", 3), ("radiance_fmt", 3)]:
         yield k, {k: v}
     yield "bandwidth", {"bandwidth": 0.0}
     del ok
