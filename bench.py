@@ -350,6 +350,8 @@ def run_ours(args):
         "gpu_launches": int(prof_a["kernels"]),
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_diff:
+        line["differentiation_form"] = _differentiation(dev)
     if rank == 0 and not args.no_e2e:
         line["e2e"] = _e2e(args, scene, wl, N, stream)
     if rank == 0 and not args.no_cpu_baseline:
@@ -360,6 +362,45 @@ def run_ours(args):
         dist.barrier()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _differentiation(dev, reps=5):
+    """The differentiation workload (512x512, 16 frames, 2 spp, 7x7x3 window):
+    dense regression forward + hand-written adjoint for dL/dE and dL/db."""
+    import torch
+    from paper_2303_02608_gb300 import wlr
+    from scenes import Scene, preset
+    sc = Scene(preset("rects512"))
+    fr = [sc.frame(t, dev) for t in range(sc.cfg.frames)]
+    rad = torch.stack([f["radiance"] for f in fr]).contiguous()
+    feat = torch.stack([torch.cat([f["normal"], f["depth"][None], f["albedo"]]) for f in fr]).contiguous()
+    Yc = sum(w * torch.stack([f["clean"][i] for f in fr]) for i, w in enumerate(REC709))
+    target = torch.log(Yc + 1e-3)
+    b = torch.ones(7, device=dev, requires_grad=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd, bwd = [], []
+    for it in range(reps + 2):
+        r = rad.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        ev[0].record()
+        alpha = wlr(r, feat, b, radius=3, frames=3)
+        ev[1].record()
+        g = 2.0 * (alpha - target) / alpha.numel()      # dL/dalpha of the mean squared error
+        ev[1].synchronize()
+        e_b0 = torch.cuda.Event(enable_timing=True)
+        e_b0.record()
+        alpha.backward(g)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if it >= 2:
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(e_b0.elapsed_time(ev[2]))
+    n_pf = rad.shape[0] * rad.shape[2] * rad.shape[3]
+    f_ms, b_ms = statistics.median(fwd), statistics.median(bwd)
+    return {"workload": "rects512: 512x512 RGB, 16 frames, 2 spp, 7x7x3 window, 7 bandwidths",
+            "forward_ms": round(f_ms, 3), "backward_ms": round(b_ms, 3),
+            "value": round(n_pf / ((f_ms + b_ms) * 1e-3), 1), "unit": "pixel-frames/s (forward + backward)",
+            "grad_bandwidth_finite": bool(torch.isfinite(b.grad).all())}
 
 
 def _dequantised_cpu(sf):
@@ -469,6 +510,7 @@ def main():
     ap.add_argument("--event-capacity", type=int, default=1 << 27)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

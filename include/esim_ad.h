@@ -224,6 +224,62 @@ esim_ad_status esim_ad_profile_enable(esim_ad_ctx* ctx, int on);
 esim_ad_status esim_ad_profile_get(esim_ad_ctx* ctx, esim_ad_profile* out);
 
 /*
+ * Differentiation form: the dense weighted local regression of Eqs. 3-5 over a
+ * whole sequence, as a differentiable function of the noisy radiance E and of
+ * the seven feature bandwidths b_j of Eq. 5 (the paper fixes h = 1, b_j = 1
+ * and names bandwidth selection, Section 3, as the costly alternative; fitting
+ * b by gradient descent is this library's extension).  Stateless: the caller
+ * owns every buffer, including a workspace of esim_ad_wlr_workspace_size bytes.
+ *
+ * Per frame t and pixel c, alpha_t(c) solves Eq. 4 over frames t-T+1..t with
+ * the ridge of esim_ad_config.  The adjoint uses v = A^-1 e_0 and the residuals
+ * r_i = y_i - z_i^T theta:  d alpha/d y_i = w_i v^T z_i,
+ * d alpha/d w_i = v^T z_i r_i - lambda v^T P theta (P = diag(0,1,..,1), from the
+ * ridge lambda W |beta|^2 with dW/dw_i = 1),  d w_i/d b_j = w_i d_ij^2 / (h^2 b_j^3),
+ * d y/d E = (luminance weight) / (Y + eps).  Weights are recomputed, not stored.
+ */
+typedef struct esim_ad_wlr_desc {
+    uint32_t struct_size;    /* = sizeof(esim_ad_wlr_desc)                      */
+    int32_t  width, height;  /* W, H >= 1                                       */
+    int32_t  sequence;       /* F >= 1 frames in the sequence                   */
+    int32_t  radius;         /* r in [1, 15]                                    */
+    int32_t  frames;         /* T in [1, 16]                                    */
+    int32_t  radiance_fmt;   /* ESIM_AD_LUMA_F32 | ESIM_AD_RGB_F32              */
+    float    h;              /* > 0                                             */
+    float    log_eps;        /* >= 0                                            */
+    float    ridge;          /* > 0                                             */
+} esim_ad_wlr_desc;
+
+/* Bytes of device workspace the forward and backward calls need (0 on a bad desc). */
+size_t esim_ad_wlr_workspace_size(const esim_ad_wlr_desc* d);
+
+/*
+ * radiance  [F][C][H][W] float32, C = 1 or 3 (device, input)
+ * features  [F][7][H][W] float32: normal xyz, depth, albedo rgb (device, input)
+ * bandwidth [7] float32 b_j > 0 (device, input; read by the kernels, no host copy)
+ * alpha     [F][H][W] float32 (device, output)
+ * saved     [F][20][H][W] float32 (device, output; theta and v for the backward)
+ * workspace esim_ad_wlr_workspace_size bytes (device, caller-owned scratch)
+ * Asynchronous on cuda_stream.  EINVAL on a bad desc or NULL pointer.
+ */
+esim_ad_status esim_ad_wlr_forward(const esim_ad_wlr_desc* d, const float* radiance,
+                                   const float* features, const float* bandwidth, float* alpha,
+                                   float* saved, void* workspace, void* cuda_stream);
+
+/*
+ * g_alpha     [F][H][W] dL/d alpha (device, input)
+ * g_radiance  [F][C][H][W] dL/dE (device, output, overwritten)
+ * g_bandwidth [7] dL/db (device, output, overwritten)
+ * Other arguments as for the forward, with `saved` and `workspace` from it
+ * (the workspace must not have been reused in between).  The sums are taken in
+ * a fixed order: results are deterministic.  Asynchronous on cuda_stream.
+ */
+esim_ad_status esim_ad_wlr_backward(const esim_ad_wlr_desc* d, const float* radiance,
+                                    const float* features, const float* bandwidth,
+                                    const float* saved, const float* g_alpha, float* g_radiance,
+                                    float* g_bandwidth, void* workspace, void* cuda_stream);
+
+/*
  * Write the events of one frame from a map of signed per-pixel event counts
  * (p*n, as Eq. 1 emission produces), in canonical order (row, column, repeat),
  * without allocating anything.  The paper has no counterpart: this is a

@@ -42,7 +42,8 @@ EXPORTS = (
     "esim_ad_init", "esim_ad_push_frame", "esim_ad_events", "esim_ad_denoised",
     "esim_ad_get_state", "esim_ad_set_state", "esim_ad_reset", "esim_ad_stats_get",
     "esim_ad_destroy", "esim_ad_status_string", "esim_ad_profile_enable", "esim_ad_profile_get",
-    "esim_ad_write_events_noalloc",
+    "esim_ad_write_events_noalloc", "esim_ad_wlr_workspace_size", "esim_ad_wlr_forward",
+    "esim_ad_wlr_backward",
 )
 
 
@@ -74,6 +75,13 @@ class esim_ad_stats(ctypes.Structure):
 class esim_ad_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64 * 3), ("kernels", ctypes.c_uint64), ("ms", ctypes.c_double * 3),
                 ("neighbours", ctypes.c_uint64), ("regressions", ctypes.c_uint64)]
+
+
+class esim_ad_wlr_desc(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("sequence", ctypes.c_int32), ("radius", ctypes.c_int32), ("frames", ctypes.c_int32),
+                ("radiance_fmt", ctypes.c_int32), ("h", ctypes.c_float), ("log_eps", ctypes.c_float),
+                ("ridge", ctypes.c_float)]
 
 
 EVENT_DTYPE = np.dtype({"names": ["frame", "x", "y", "polarity"],
@@ -126,6 +134,12 @@ def load_library():
     lib.esim_ad_write_events_noalloc.restype = st
     lib.esim_ad_write_events_noalloc.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, P,
                                                  ctypes.c_uint64, P, P]
+    lib.esim_ad_wlr_workspace_size.restype = ctypes.c_size_t
+    lib.esim_ad_wlr_workspace_size.argtypes = [ctypes.POINTER(esim_ad_wlr_desc)]
+    lib.esim_ad_wlr_forward.restype = st
+    lib.esim_ad_wlr_forward.argtypes = [ctypes.POINTER(esim_ad_wlr_desc), P, P, P, P, P, P, P]
+    lib.esim_ad_wlr_backward.restype = st
+    lib.esim_ad_wlr_backward.argtypes = [ctypes.POINTER(esim_ad_wlr_desc), P, P, P, P, P, P, P, P, P]
     lib.esim_ad_status_string.restype = ctypes.c_char_p
     lib.esim_ad_status_string.argtypes = [st]
     _lib = lib
@@ -242,6 +256,85 @@ def esim_ad_write_events_noalloc(counts: int, width: int, height: int, frame: in
     return load_library().esim_ad_write_events_noalloc(
         ctypes.c_void_p(counts or None), width, height, frame, ctypes.c_void_p(events or None),
         ctypes.c_uint64(capacity), ctypes.c_void_p(total_device or None), ctypes.c_void_p(cuda_stream or None))
+
+
+def make_wlr_desc(width: int, height: int, sequence: int, radius: int = 3, frames: int = 3, rgb: bool = True,
+                  h: float = 1.0, log_eps: float = 1e-3, ridge: float = 1e-4) -> esim_ad_wlr_desc:
+    d = esim_ad_wlr_desc()
+    d.struct_size = ctypes.sizeof(esim_ad_wlr_desc)
+    d.width, d.height, d.sequence, d.radius, d.frames = width, height, sequence, radius, frames
+    d.radiance_fmt = ESIM_AD_RGB_F32 if rgb else ESIM_AD_LUMA_F32
+    d.h, d.log_eps, d.ridge = h, log_eps, ridge
+    return d
+
+
+def esim_ad_wlr_workspace_size(desc: esim_ad_wlr_desc) -> int:
+    return int(load_library().esim_ad_wlr_workspace_size(ctypes.byref(desc)))
+
+
+def esim_ad_wlr_forward(desc, radiance: int, features: int, bandwidth: int, alpha: int, saved: int,
+                        workspace: int, cuda_stream: int = 0) -> None:
+    _check(load_library().esim_ad_wlr_forward(ctypes.byref(desc), *(ctypes.c_void_p(x) for x in (
+        radiance, features, bandwidth, alpha, saved, workspace, cuda_stream or None))), "esim_ad_wlr_forward")
+
+
+def esim_ad_wlr_backward(desc, radiance: int, features: int, bandwidth: int, saved: int, g_alpha: int,
+                         g_radiance: int, g_bandwidth: int, workspace: int, cuda_stream: int = 0) -> None:
+    _check(load_library().esim_ad_wlr_backward(ctypes.byref(desc), *(ctypes.c_void_p(x) for x in (
+        radiance, features, bandwidth, saved, g_alpha, g_radiance, g_bandwidth, workspace,
+        cuda_stream or None))), "esim_ad_wlr_backward")
+
+
+def _wlr_function():
+    import torch
+
+    class WLRFunction(torch.autograd.Function):
+        """alpha = WLR(radiance, features; bandwidth): the dense regression of every
+        pixel of every frame, differentiable in the radiance and the 7 feature
+        bandwidths.  Forward and backward run in the library's kernels."""
+
+        @staticmethod
+        def forward(ctx, radiance, features, bandwidth, radius, frames, h, log_eps, ridge):
+            F_, C, H, W = radiance.shape
+            desc = make_wlr_desc(W, H, F_, radius, frames, C == 3, h, log_eps, ridge)
+            dev = radiance.device
+            ws = torch.empty(esim_ad_wlr_workspace_size(desc), dtype=torch.uint8, device=dev)
+            alpha = torch.empty(F_, H, W, dtype=torch.float32, device=dev)
+            saved = torch.empty(F_, 20, H, W, dtype=torch.float32, device=dev)
+            radiance, features, bandwidth = (t.contiguous().float() for t in (radiance, features, bandwidth))
+            stream = torch.cuda.current_stream(dev).cuda_stream
+            esim_ad_wlr_forward(desc, radiance.data_ptr(), features.data_ptr(), bandwidth.data_ptr(),
+                                alpha.data_ptr(), saved.data_ptr(), ws.data_ptr(), stream)
+            ctx.desc = desc
+            ctx.save_for_backward(radiance, features, bandwidth, saved, ws)
+            return alpha
+
+        @staticmethod
+        def backward(ctx, g_alpha):
+            radiance, features, bandwidth, saved, ws = ctx.saved_tensors
+            g_alpha = g_alpha.contiguous().float()
+            g_rad = torch.empty_like(radiance)
+            g_b = torch.empty(7, dtype=torch.float32, device=radiance.device)
+            stream = torch.cuda.current_stream(radiance.device).cuda_stream
+            esim_ad_wlr_backward(ctx.desc, radiance.data_ptr(), features.data_ptr(), bandwidth.data_ptr(),
+                                 saved.data_ptr(), g_alpha.data_ptr(), g_rad.data_ptr(), g_b.data_ptr(),
+                                 ws.data_ptr(), stream)
+            return g_rad, None, g_b, None, None, None, None, None
+
+    return WLRFunction
+
+
+_WLR = None
+
+
+def wlr(radiance, features, bandwidth, radius: int = 3, frames: int = 3, h: float = 1.0, log_eps: float = 1e-3,
+        ridge: float = 1e-4):
+    """Differentiable dense regression: radiance [F][C][H][W], features [F][7][H][W]
+    (normal xyz, depth, albedo rgb), bandwidth [7] -> alpha [F][H][W]."""
+    global _WLR
+    if _WLR is None:
+        _WLR = _wlr_function()
+    return _WLR.apply(radiance, features, bandwidth, radius, frames, h, log_eps, ridge)
 
 
 def esim_ad_destroy(ctx: int) -> None:
