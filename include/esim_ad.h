@@ -224,6 +224,74 @@ esim_ad_status esim_ad_profile_enable(esim_ad_ctx* ctx, int on);
 esim_ad_status esim_ad_profile_get(esim_ad_ctx* ctx, esim_ad_profile* out);
 
 /*
+ * Batching form: many independent sequences of uneven resolution advanced one
+ * frame each per step.  The paper has no batched mode; this is the serving
+ * shape of the same per-sequence method (every sequence behaves exactly as a
+ * context of esim_ad_init would, up to floating-point summation order).
+ *
+ * Per step: one ingest/test launch over the tiles of all sequences, one
+ * persistent regression launch over a single compacted queue of flagged
+ * (sequence, pixel) entries of all sequences, one event-writer launch; the
+ * whole step is a CUDA graph instantiated at init and replayed per step (the
+ * per-step frame pointers travel in a small table copied by the graph).  The
+ * regression's lanes per pixel are chosen by an autotuner that times the
+ * candidates on the first adaptive steps and caches the choice per (radius,
+ * frames, precision, SM count) in $ESIM_AD_CACHE (default
+ * ~/.cache/esim_ad_autotune.txt); ESIM_AD_BATCH_LANES=8|16|32 forces one.
+ */
+typedef struct esim_ad_batch esim_ad_batch;
+
+/* One batched event: as esim_ad_event plus the sequence index. 12 bytes. */
+typedef struct esim_ad_batch_event {
+    uint32_t frame;          /* the sequence's own frame index                   */
+    uint16_t x, y;
+    int8_t   polarity;
+    uint8_t  pad;
+    uint16_t seq;            /* index into the configs given at init            */
+} esim_ad_batch_event;
+
+/*
+ * cfgs[n_seq] (1 <= n_seq <= 255): width, height and contrast may differ per
+ * sequence; every other field must equal cfgs[0]'s, and event_capacity is
+ * taken from cfgs[0] for the whole batch; each sequence has at most 16,777,216
+ * pixels.  EINVAL otherwise; ENOMEM / ECUDA as esim_ad_init.  Synchronises.
+ */
+esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, void* cuda_stream,
+                                  esim_ad_batch** out);
+
+/*
+ * Advance every sequence whose frames[i].radiance is non-NULL by one frame
+ * (device pointers; the others are idle this step and keep their state).
+ * frames[n_seq].  Asynchronous: the frames must stay valid until the step has
+ * run on the stream.  ESTATE after a sticky error, ECUDA on a launch failure.
+ */
+esim_ad_status esim_ad_batch_step(esim_ad_batch* b, const esim_ad_frame* frames);
+
+/* Drain all sequences' events (order: step, sequence, row, column, repeat);
+ * semantics as esim_ad_events.  Synchronises. */
+esim_ad_status esim_ad_batch_events(esim_ad_batch* b, esim_ad_batch_event* dst, uint64_t cap,
+                                    uint64_t* n_out, int dst_is_device);
+
+/* Restart sequence `seq` at frame 0 (its next step initialises it again). */
+esim_ad_status esim_ad_batch_reset_sequence(esim_ad_batch* b, int32_t seq);
+
+/* Per-sequence read-back, as esim_ad_denoised / esim_ad_get_state for sequence
+ * `seq` (its last step; host pointers for the state).  Synchronise. */
+esim_ad_status esim_ad_batch_denoised(esim_ad_batch* b, int32_t seq, float* alpha, uint8_t* flags,
+                                      int dst_is_device);
+esim_ad_status esim_ad_batch_get_state(esim_ad_batch* b, int32_t seq, float* l_last, float* beta,
+                                       float* xc);
+
+/* Counters and kernel timing as for a context: stats over all sequences, and
+ * the profile of the steps run while enabled (class 1 = the one persistent
+ * regression launch per step).  lanes_out receives the autotuned lanes per pixel. */
+esim_ad_status esim_ad_batch_stats(esim_ad_batch* b, esim_ad_stats* out, int32_t* lanes_out);
+esim_ad_status esim_ad_batch_profile_enable(esim_ad_batch* b, int on);
+esim_ad_status esim_ad_batch_profile_get(esim_ad_batch* b, esim_ad_profile* out);
+
+void esim_ad_batch_destroy(esim_ad_batch* b);
+
+/*
  * Differentiation form: the dense weighted local regression of Eqs. 3-5 over a
  * whole sequence, as a differentiable function of the noisy radiance E and of
  * the seven feature bandwidths b_j of Eq. 5 (the paper fixes h = 1, b_j = 1

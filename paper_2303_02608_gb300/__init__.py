@@ -43,7 +43,10 @@ EXPORTS = (
     "esim_ad_get_state", "esim_ad_set_state", "esim_ad_reset", "esim_ad_stats_get",
     "esim_ad_destroy", "esim_ad_status_string", "esim_ad_profile_enable", "esim_ad_profile_get",
     "esim_ad_write_events_noalloc", "esim_ad_wlr_workspace_size", "esim_ad_wlr_forward",
-    "esim_ad_wlr_backward",
+    "esim_ad_wlr_backward", "esim_ad_batch_init", "esim_ad_batch_step", "esim_ad_batch_events",
+    "esim_ad_batch_reset_sequence", "esim_ad_batch_denoised", "esim_ad_batch_get_state",
+    "esim_ad_batch_stats", "esim_ad_batch_profile_enable", "esim_ad_batch_profile_get",
+    "esim_ad_batch_destroy",
 )
 
 
@@ -83,6 +86,10 @@ class esim_ad_wlr_desc(ctypes.Structure):
                 ("radiance_fmt", ctypes.c_int32), ("h", ctypes.c_float), ("log_eps", ctypes.c_float),
                 ("ridge", ctypes.c_float)]
 
+
+BATCH_EVENT_DTYPE = np.dtype({"names": ["frame", "x", "y", "polarity", "seq"],
+                              "formats": ["<u4", "<u2", "<u2", "i1", "<u2"],
+                              "offsets": [0, 4, 6, 8, 10], "itemsize": 12})
 
 EVENT_DTYPE = np.dtype({"names": ["frame", "x", "y", "polarity"],
                         "formats": ["<u4", "<u2", "<u2", "i1"],
@@ -140,6 +147,26 @@ def load_library():
     lib.esim_ad_wlr_forward.argtypes = [ctypes.POINTER(esim_ad_wlr_desc), P, P, P, P, P, P, P]
     lib.esim_ad_wlr_backward.restype = st
     lib.esim_ad_wlr_backward.argtypes = [ctypes.POINTER(esim_ad_wlr_desc), P, P, P, P, P, P, P, P, P]
+    lib.esim_ad_batch_init.restype = st
+    lib.esim_ad_batch_init.argtypes = [ctypes.POINTER(esim_ad_config), ctypes.c_int32, P, ctypes.POINTER(P)]
+    lib.esim_ad_batch_step.restype = st
+    lib.esim_ad_batch_step.argtypes = [P, ctypes.POINTER(esim_ad_frame)]
+    lib.esim_ad_batch_events.restype = st
+    lib.esim_ad_batch_events.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+    lib.esim_ad_batch_reset_sequence.restype = st
+    lib.esim_ad_batch_reset_sequence.argtypes = [P, ctypes.c_int32]
+    lib.esim_ad_batch_denoised.restype = st
+    lib.esim_ad_batch_denoised.argtypes = [P, ctypes.c_int32, P, P, ctypes.c_int]
+    lib.esim_ad_batch_get_state.restype = st
+    lib.esim_ad_batch_get_state.argtypes = [P, ctypes.c_int32, P, P, P]
+    lib.esim_ad_batch_stats.restype = st
+    lib.esim_ad_batch_stats.argtypes = [P, ctypes.POINTER(esim_ad_stats), ctypes.POINTER(ctypes.c_int32)]
+    lib.esim_ad_batch_profile_enable.restype = st
+    lib.esim_ad_batch_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.esim_ad_batch_profile_get.restype = st
+    lib.esim_ad_batch_profile_get.argtypes = [P, ctypes.POINTER(esim_ad_profile)]
+    lib.esim_ad_batch_destroy.restype = None
+    lib.esim_ad_batch_destroy.argtypes = [P]
     lib.esim_ad_status_string.restype = ctypes.c_char_p
     lib.esim_ad_status_string.argtypes = [st]
     _lib = lib
@@ -461,3 +488,124 @@ class Simulator:
             esim_ad_profile_enable(self.ctx, on)
             return None
         return esim_ad_profile_get(self.ctx)
+
+
+# ------------------------------------------------------------- batching form
+
+def esim_ad_batch_init(cfgs: list, cuda_stream: int = 0) -> int:
+    arr = (esim_ad_config * len(cfgs))(*cfgs)
+    h = ctypes.c_void_p()
+    _check(load_library().esim_ad_batch_init(arr, len(cfgs), ctypes.c_void_p(cuda_stream or None), ctypes.byref(h)),
+           "esim_ad_batch_init")
+    return h.value
+
+
+def esim_ad_batch_step(b: int, frames: list) -> None:
+    arr = (esim_ad_frame * len(frames))(*frames)
+    _check(load_library().esim_ad_batch_step(ctypes.c_void_p(b), arr), "esim_ad_batch_step")
+
+
+def esim_ad_batch_events(b: int, dst: int, cap: int, dst_is_device: bool = False) -> tuple[int, int]:
+    n = ctypes.c_uint64(0)
+    st = load_library().esim_ad_batch_events(ctypes.c_void_p(b), ctypes.c_void_p(dst or None), ctypes.c_uint64(cap),
+                                             ctypes.byref(n), int(dst_is_device))
+    return st, n.value
+
+
+def esim_ad_batch_destroy(b: int) -> None:
+    if b:
+        load_library().esim_ad_batch_destroy(ctypes.c_void_p(b))
+
+
+class Batch:
+    """Many sequences stepped together (one config per sequence; width, height
+    and contrast may differ).  ``step`` takes one frame dict per sequence (device
+    tensors, as for Simulator.push) or None for a sequence idle this step."""
+
+    def __init__(self, cfgs: list, stream=None):
+        import torch
+        self._torch = torch
+        self.cfgs = cfgs
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.b = esim_ad_batch_init([c.c_config() for c in cfgs], self.stream.cuda_stream)
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "b", None):
+            esim_ad_batch_destroy(self.b)
+            self.b = None
+
+    __del__ = close
+
+    def step(self, frames: list) -> None:
+        t = self._torch
+        out = []
+        for f in frames:
+            if f is None:
+                out.append(esim_ad_frame(None, None, None, None, None, None, 0, 0))
+                continue
+            for v in f.values():
+                if not v.is_cuda or not v.is_contiguous():
+                    raise ValueError("batched frames must be contiguous device tensors")
+            g = lambda k: f[k].data_ptr() if k in f else None
+            out.append(esim_ad_frame(g("radiance"), None, g("normal"), g("albedo"), g("depth"), g("features"), 0, 0))
+            self._keep.append(f)
+        esim_ad_batch_step(self.b, out)
+        del t
+
+    def events(self) -> np.ndarray:
+        st, n = esim_ad_batch_events(self.b, 0, 0)
+        if st not in (ESIM_AD_OK, ESIM_AD_ENOSPACE):
+            raise EsimError(st, "esim_ad_batch_events")
+        out = np.empty(n, BATCH_EVENT_DTYPE)
+        if n:
+            st, _ = esim_ad_batch_events(self.b, out.ctypes.data, n)
+            _check(st, "esim_ad_batch_events")
+        self._keep.clear()
+        return out
+
+    def events_device(self, dst, cap: int) -> int:
+        st, n = esim_ad_batch_events(self.b, dst.data_ptr(), cap, dst_is_device=True)
+        _check(st, "esim_ad_batch_events")
+        self._keep.clear()
+        return n
+
+    def denoised(self, seq: int):
+        t = self._torch
+        c = self.cfgs[seq]
+        a = t.empty(c.height, c.width, dtype=t.float32, device="cuda")
+        f = t.empty(c.height, c.width, dtype=t.uint8, device="cuda")
+        _check(load_library().esim_ad_batch_denoised(ctypes.c_void_p(self.b), seq, ctypes.c_void_p(a.data_ptr()),
+                                                     ctypes.c_void_p(f.data_ptr()), 1), "esim_ad_batch_denoised")
+        return a, f
+
+    def get_state(self, seq: int) -> dict:
+        c = self.cfgs[seq]
+        n = c.width * c.height
+        l_last, beta, xc = np.empty(n, np.float32), np.empty((n, 7), np.float32), np.empty((n, 7), np.float32)
+        _check(load_library().esim_ad_batch_get_state(ctypes.c_void_p(self.b), seq, ctypes.c_void_p(l_last.ctypes.data),
+                                                      ctypes.c_void_p(beta.ctypes.data), ctypes.c_void_p(xc.ctypes.data)),
+               "esim_ad_batch_get_state")
+        return {"l_last": l_last, "beta": beta, "xc": xc}
+
+    def reset_sequence(self, seq: int) -> None:
+        _check(load_library().esim_ad_batch_reset_sequence(ctypes.c_void_p(self.b), seq), "esim_ad_batch_reset_sequence")
+
+    def stats(self) -> dict:
+        s = esim_ad_stats()
+        lanes = ctypes.c_int32(0)
+        _check(load_library().esim_ad_batch_stats(ctypes.c_void_p(self.b), ctypes.byref(s), ctypes.byref(lanes)),
+               "esim_ad_batch_stats")
+        return {"steps": s.frames, "regressions": s.regressions, "events": s.events, "pixels": s.pixels,
+                "fp64_solves": s.fp64_solves, "lanes": lanes.value}
+
+    def profile(self, on: bool | None = None):
+        lib = load_library()
+        if on is not None:
+            _check(lib.esim_ad_batch_profile_enable(ctypes.c_void_p(self.b), int(on)), "esim_ad_batch_profile_enable")
+            return None
+        p = esim_ad_profile()
+        _check(lib.esim_ad_batch_profile_get(ctypes.c_void_p(self.b), ctypes.byref(p)), "esim_ad_batch_profile_get")
+        return {"launches": {k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
+                "ms": {k: float(p.ms[i]) for i, k in enumerate(KERNEL_CLASSES)},
+                "kernels": int(p.kernels), "neighbours": int(p.neighbours), "regressions": int(p.regressions)}

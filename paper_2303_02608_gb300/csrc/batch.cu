@@ -1,0 +1,920 @@
+// Batching form: many independent sequences of uneven resolution advanced one
+// frame each per step, as one CUDA graph per step:
+//   1. copy of the step table (per-sequence frame pointers and frame index),
+//   2. clear of the per-step counters and the per-chunk event counts,
+//   3. one ingest/test launch over the tiles of every sequence; flagged pixels
+//      of all sequences are compacted into one queue of (sequence, pixel)
+//      entries (sequence in the top 8 bits),
+//   4. one persistent regression launch over that queue (windows read through
+//      L1; lanes per pixel chosen by the autotuner),
+//   5. one event-writer launch over the chunks of every sequence.
+// Each sequence keeps its own ring, model state and maps, exactly as a
+// single-sequence context does; the per-pixel arithmetic is shared with it.
+#include <errno.h>
+#include <stdio.h>
+#include <sys/stat.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "block_scan.cuh"
+#include "ingest_pixel.cuh"
+#include "internal.h"
+#include "wlr_math.cuh"
+
+namespace esim {
+namespace {
+
+constexpr int kMaxSeq = 255;
+constexpr uint32_t kPixBits = 24;
+constexpr uint32_t kPixMask = (1u << kPixBits) - 1u;
+
+// Per-sequence, per-step description (device table, rewritten every step).
+struct SeqStep {
+    IngestParams ip;       // frame inputs, ring slot, test on/off
+    WlrParams wp;          // frame index, window, maps; chunk_cnt points at the sequence's chunks
+    int active;            // the sequence advances this step
+    int tile_base;         // first global tile of the sequence
+    int chunk_base;        // first global event chunk of the sequence
+    uint32_t frame;        // frame index written into its events
+};
+
+struct BatchGlobal {
+    const SeqStep* steps;
+    const uint16_t* tile_seq;    // global tile -> sequence
+    const uint16_t* chunk_seq;   // global chunk -> sequence
+    uint32_t* flag_list;         // (seq << 24) | pixel
+    uint32_t* chunk_cnt;         // [total chunks]
+    unsigned long long* chunk_off;
+    esim_ad_batch_event* events;
+    unsigned long long capacity;
+    int total_tiles, total_chunks, r;
+    float s_px;
+    Ctrl* ctrl;
+};
+
+__global__ void __launch_bounds__(kTilePix) batch_ingest_kernel(BatchGlobal g)
+{
+    const int gt = blockIdx.x;
+    const int seq = g.tile_seq[gt];
+    const SeqStep& st = g.steps[seq];
+    if (!st.active) return;
+    const IngestParams& p = st.ip;
+    const int tile = gt - st.tile_base;
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int x = (tile % p.tiles_x) * kTileX + lx;
+    const int y = (tile / p.tiles_x) * kTileY + ly;
+    const int flag = ingest_pixel(p, x, y);
+    // compact this tile's regressed pixels into the global queue
+    __shared__ int warp_cnt[kTilePix / 32];
+    __shared__ uint32_t s_base;
+    const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+    if (lx == 0) warp_cnt[ly] = __popc(ballot);
+    __syncthreads();
+    int base = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kTilePix / 32; ++w) {
+        const int c = warp_cnt[w];
+        base += (w < ly) ? c : 0;
+        total += c;
+    }
+    if (threadIdx.x == 0 && total > 0) s_base = atomicAdd(&g.ctrl->flag_total, (uint32_t)total);
+    __syncthreads();
+    if (flag) {
+        const int pos = base + __popc(ballot & ((1u << lx) - 1u));
+        g.flag_list[s_base + pos] = ((uint32_t)seq << kPixBits) | (uint32_t)((size_t)y * p.W + x);
+    }
+}
+
+// One persistent launch over the queue of every sequence.  A CTA takes
+// 8 * (32 / kLanes) consecutive entries (neighbours in one tile of one
+// sequence); kLanes lanes split each pixel's window and are shuffle-reduced.
+template <int kLanes, bool kMixed>
+__global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, const WlrParams gp)
+{
+    constexpr int kPerWarp = 32 / kLanes;
+    constexpr int kBlock = (kTilePix / 32) * kPerWarp;
+    __shared__ float4 table[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];
+    __shared__ unsigned long long s_pairs, s_pix, s_fp64;
+    __shared__ uint32_t s_blk;
+    const int r = g.r, side = 2 * r + 1, nq = side * side;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int ox = q % side - r, oy = q / side - r;
+        const float u1 = (float)ox * g.s_px, u2 = (float)oy * g.s_px;
+        table[q] = make_float4(__int_as_float((oy << 16) | (ox & 0xffff)), u1, u2, -fmaf(u1, u1, u2 * u2));
+    }
+    if (threadIdx.x == 0) {
+        s_pairs = 0ull;
+        s_pix = 0ull;
+        s_fp64 = 0ull;
+    }
+    __syncthreads();
+    const uint32_t n_flag = *(volatile uint32_t*)&g.ctrl->flag_total;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (kLanes - 1);
+    const int grp = lane / kLanes;
+    Acc acc;
+    float cf[7];
+    for (;;) {
+        if (threadIdx.x == 0) s_blk = atomicAdd(&g.ctrl->work_next, (uint32_t)kBlock);
+        __syncthreads();
+        const uint32_t blk = s_blk;
+        __syncthreads();
+        if (blk >= n_flag) break;
+        const uint32_t my = blk + (uint32_t)((threadIdx.x >> 5) * kPerWarp + grp);
+        const bool active = my < n_flag;
+        const uint32_t e = active ? g.flag_list[my] : 0u;
+        const int seq = (int)(e >> kPixBits);
+        const uint32_t pix = e & kPixMask;
+        const WlrParams& sp = g.steps[seq].wp;
+        const int W = sp.W, H = sp.H;
+        const size_t N = (size_t)W * H;
+        const int cx = (int)(pix % (uint32_t)W), cy = (int)(pix / (uint32_t)W);
+        const float* sf = kMixed ? sp.q_scale : sp.s_feat;
+#pragma unroll
+        for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
+        const int dxlo = max(-r, -cx), dxhi = min(r, W - 1 - cx);
+        const int dylo = max(-r, -cy), dyhi = min(r, H - 1 - cy);
+        const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
+        if (active) {
+            const float4* ringf = reinterpret_cast<const float4*>(sp.ring);
+            const uint4* ringm = reinterpret_cast<const uint4*>(sp.ring);
+            const int slot_t = sp.t % sp.T;
+            float c[7];
+            if (kMixed) {
+                float yc;
+                unpack_mixed(__ldg(ringm + (size_t)slot_t * N + pix), yc, c);
+            } else {
+                const float4 c0 = __ldg(ringf + (size_t)(2 * slot_t) * N + pix);
+                const float4 c1 = __ldg(ringf + (size_t)(2 * slot_t + 1) * N + pix);
+                c[0] = c0.y; c[1] = c0.z; c[2] = c0.w; c[3] = c1.x; c[4] = c1.y; c[5] = c1.z; c[6] = c1.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
+            for (int k = 0; k < sp.n_tau; ++k) {
+                const int slot = (sp.t - k) % sp.T;
+                const float4* __restrict__ R0 = ringf + (size_t)(2 * slot) * N + pix;
+                const float4* __restrict__ R1 = ringf + (size_t)(2 * slot + 1) * N + pix;
+                const uint4* __restrict__ RM = ringm + (size_t)slot * N + pix;
+                auto at = [&](int d, float u1, float u2, float en0) {
+                    if (kMixed)
+                        accumulate(acc, __ldg(RM + d), u1, u2, en0, sf, cf);
+                    else
+                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, en0, sf, cf);
+                };
+                if (nx == side && ny == side) {
+#pragma unroll 2
+                    for (int q = sub; q < nq; q += kLanes) {
+                        const float4 t4 = table[q];
+                        const int packed = __float_as_int(t4.x);
+                        const int ox = (int)(short)(packed & 0xffff), oy = packed >> 16;
+                        at(oy * W + ox, t4.y, t4.z, t4.w);
+                    }
+                } else {
+                    const int nvalid = nx * ny;
+                    int ox = dxlo + sub % nx;
+                    int oy = dylo + sub / nx;
+                    for (int q = sub; q < nvalid; q += kLanes) {
+                        const float u1 = (float)ox * g.s_px, u2 = (float)oy * g.s_px;
+                        at(oy * W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
+                        ox += kLanes;
+                        while (ox > dxhi) {
+                            ox -= nx;
+                            ++oy;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int off = kLanes >> 1; off >= 1; off >>= 1) {
+#pragma unroll
+            for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
+#pragma unroll
+            for (int i = 0; i < NZ; ++i) acc.B[i] += __shfl_xor_sync(0xffffffffu, acc.B[i], off);
+        }
+        if (active && sub == 0) {
+            atomicAdd(&s_pairs, (unsigned long long)(nx * ny * sp.n_tau));
+            atomicAdd(&s_pix, 1ull);
+            solve_and_emit<kMixed>(sp, acc, cx, cy, &s_fp64);
+        }
+    }
+    __syncthreads();
+    finish(gp, s_pairs, s_pix, s_fp64, false);
+}
+
+__global__ void __launch_bounds__(kTilePix) batch_event_write_kernel(BatchGlobal g)
+{
+    constexpr int kPer = kChunk / kTilePix;
+    __shared__ int s_warp[kTilePix / 32];
+    const int gc = blockIdx.x;
+    if (g.chunk_cnt[gc] == 0u) return;
+    const int seq = g.chunk_seq[gc];
+    const SeqStep& st = g.steps[seq];
+    const WlrParams& sp = st.wp;
+    const long long n_pix = (long long)sp.W * sp.H;
+    const long long p0 = (long long)(gc - st.chunk_base) * kChunk + (long long)threadIdx.x * kPer;
+    int v[kPer];
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = (p0 + k < n_pix) ? sp.nev[p0 + k] : 0;
+        c += abs(v[k]);
+    }
+    int total;
+    const int off = block_exclusive_scan(c, s_warp, total);
+    unsigned long long pos = g.chunk_off[gc] + (unsigned long long)off;
+    bool overflow = false;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int n = abs(v[k]);
+        if (n == 0) continue;
+        const long long pix = p0 + k;
+        const uint32_t x = (uint32_t)(pix % sp.W), y = (uint32_t)(pix / sp.W);
+        const uint32_t w1 = x | (y << 16);
+        const uint32_t w2 = (uint32_t)(uint8_t)(int8_t)(v[k] > 0 ? 1 : -1) | ((uint32_t)seq << 16);
+        for (int e = 0; e < n; ++e, ++pos) {
+            if (pos >= g.capacity) {
+                overflow = true;
+                continue;
+            }
+            uint32_t* rec = reinterpret_cast<uint32_t*>(g.events + pos);
+            rec[0] = st.frame;
+            rec[1] = w1;
+            rec[2] = w2;
+        }
+    }
+    if (overflow) atomicOr(&g.ctrl->status, kStatusOverflow);
+}
+
+typedef void (*WlrKernel)(BatchGlobal, const WlrParams);
+
+WlrKernel pick_kernel(int lanes, bool mixed)
+{
+    if (mixed) {
+        if (lanes == 8) return batch_wlr_kernel<8, true>;
+        if (lanes == 32) return batch_wlr_kernel<32, true>;
+        return batch_wlr_kernel<16, true>;
+    }
+    if (lanes == 8) return batch_wlr_kernel<8, false>;
+    if (lanes == 32) return batch_wlr_kernel<32, false>;
+    return batch_wlr_kernel<16, false>;
+}
+
+const double kExp2Scale = 0.84932180028801904272;
+
+}  // namespace
+}  // namespace esim
+
+using namespace esim;
+
+struct esim_ad_batch {
+    std::vector<esim_ad_config> cfg;
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    bool mixed = false;
+    // per sequence
+    std::vector<size_t> N;
+    std::vector<int> tiles_x, n_tiles, n_chunks, tile_base, chunk_base;
+    std::vector<void*> ring;
+    std::vector<float4*> state;
+    std::vector<float*> alpha;
+    std::vector<uint8_t*> flag;
+    std::vector<int32_t*> nev;
+    std::vector<uint64_t> t;        // frames pushed per sequence
+    // global
+    int total_tiles = 0, total_chunks = 0;
+    size_t total_pix = 0;
+    uint16_t* tile_seq = nullptr;
+    uint16_t* chunk_seq = nullptr;
+    uint32_t* flag_list = nullptr;
+    uint32_t* chunk_cnt = nullptr;
+    unsigned long long* chunk_off = nullptr;
+    esim_ad_batch_event* events = nullptr;
+    Ctrl* ctrl = nullptr;
+    SeqStep* d_steps = nullptr;
+    SeqStep* h_steps[2] = {nullptr, nullptr};   // pinned, alternating
+    cudaEvent_t h_free[2] = {nullptr, nullptr};
+    int cur = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_lanes = 0;
+    int grid = 0;
+    int lanes = 16;
+    bool tuned = false;
+    int tune_stage = 0;                         // candidates measured so far
+    float tune_ms[3] = {0, 0, 0};
+    unsigned long long tune_reg[3] = {0, 0, 0};
+    cudaEvent_t tune_ev[6] = {};
+    unsigned long long reg_before = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_cls;
+    size_t prof_used = 0;
+    uint64_t prof_kernels = 0;
+    esim_ad_status sticky = ESIM_AD_OK;
+    uint64_t steps = 0;
+};
+
+namespace {
+
+const int kCandidates[3] = {8, 16, 32};
+
+std::string cache_path()
+{
+    if (const char* p = getenv("ESIM_AD_CACHE")) return p;
+    const char* home = getenv("HOME");
+    return std::string(home ? home : ".") + "/.cache/esim_ad_autotune.txt";
+}
+
+std::string cache_key(const esim_ad_batch* b)
+{
+    char k[128];
+    snprintf(k, sizeof(k), "batch r=%d T=%d precision=%d sms=%d", b->cfg[0].radius, b->cfg[0].frames,
+             b->cfg[0].precision, b->num_sms);
+    return k;
+}
+
+int cache_lookup(const esim_ad_batch* b)
+{
+    FILE* f = fopen(cache_path().c_str(), "r");
+    if (!f) return 0;
+    const std::string key = cache_key(b);
+    char line[256];
+    int found = 0;
+    while (fgets(line, sizeof(line), f)) {
+        const size_t L = key.size();
+        if (strncmp(line, key.c_str(), L) == 0 && line[L] == ' ') {
+            const int v = atoi(line + L + 1);
+            if (v == 8 || v == 16 || v == 32) found = v;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const esim_ad_batch* b, int lanes)
+{
+    const std::string path = cache_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) mkdir(path.substr(0, slash).c_str(), 0755);   // may already exist
+    FILE* f = fopen(path.c_str(), "a");
+    if (!f) return;   // the cache is an optimisation only
+    fprintf(f, "%s %d\n", cache_key(b).c_str(), lanes);
+    fclose(f);
+}
+
+void batch_release(esim_ad_batch* b)
+{
+    for (int i = 0; i < b->n; ++i) {
+        if (i < (int)b->ring.size() && b->ring[i]) cudaFree(b->ring[i]);
+        if (i < (int)b->state.size() && b->state[i]) cudaFree(b->state[i]);
+        if (i < (int)b->alpha.size() && b->alpha[i]) cudaFree(b->alpha[i]);
+        if (i < (int)b->flag.size() && b->flag[i]) cudaFree(b->flag[i]);
+        if (i < (int)b->nev.size() && b->nev[i]) cudaFree(b->nev[i]);
+    }
+    void* g[] = {b->tile_seq, b->chunk_seq, b->flag_list, b->chunk_cnt, b->chunk_off, b->events, b->ctrl,
+                 b->d_steps};
+    for (void* p : g)
+        if (p) cudaFree(p);
+    for (int k = 0; k < 2; ++k) {
+        if (b->h_steps[k]) cudaFreeHost(b->h_steps[k]);
+        if (b->h_free[k]) cudaEventDestroy(b->h_free[k]);
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    }
+    for (cudaEvent_t e : b->tune_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
+}
+
+BatchGlobal globals(const esim_ad_batch* b)
+{
+    BatchGlobal g;
+    g.steps = b->d_steps;
+    g.tile_seq = b->tile_seq;
+    g.chunk_seq = b->chunk_seq;
+    g.flag_list = b->flag_list;
+    g.chunk_cnt = b->chunk_cnt;
+    g.chunk_off = b->chunk_off;
+    g.events = b->events;
+    g.capacity = b->cfg[0].event_capacity;
+    g.total_tiles = b->total_tiles;
+    g.total_chunks = b->total_chunks;
+    g.r = b->cfg[0].radius;
+    g.s_px = (float)(kExp2Scale / ((double)b->cfg[0].h * b->cfg[0].radius));
+    g.ctrl = b->ctrl;
+    return g;
+}
+
+// Global parameters of the regression launch's accounting (finish()).
+WlrParams global_wlr(const esim_ad_batch* b)
+{
+    WlrParams p;
+    memset(&p, 0, sizeof(p));
+    p.chunk_cnt = b->chunk_cnt;
+    p.chunk_off = b->chunk_off;
+    p.n_chunks = b->total_chunks;
+    p.emit_events = 1;
+    p.ctrl = b->ctrl;
+    return p;
+}
+
+// Fill the host step table for the frames of this step.
+void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames)
+{
+    const esim_ad_config& c0 = b->cfg[0];
+    for (int i = 0; i < b->n; ++i) {
+        SeqStep& st = h[i];
+        memset(&st, 0, sizeof(st));
+        const esim_ad_config& c = b->cfg[i];
+        const esim_ad_frame& f = frames[i];
+        const bool act = f.radiance != nullptr;
+        st.active = act ? 1 : 0;
+        st.tile_base = b->tile_base[i];
+        st.chunk_base = b->chunk_base[i];
+        const uint64_t t64 = b->t[i];
+        const int t = (int)(t64 % 0x7fffffff);
+        st.frame = (uint32_t)t64;
+        IngestParams& ip = st.ip;
+        ip.rad = f.radiance;
+        ip.normal = f.normal;
+        ip.albedo = f.albedo;
+        ip.depth = f.depth;
+        ip.feat_bf16 = reinterpret_cast<const unsigned short*>(f.features);
+        ip.rad_fmt = c0.radiance_fmt;
+        ip.feat_fmt = c0.feature_fmt;
+        ip.mixed = b->mixed ? 1 : 0;
+        for (int j = 0; j < 7; ++j) {
+            const float fs = (c0.feature_fmt == ESIM_AD_FEAT_BF16 || b->mixed) ? c0.feature_scale[j] : 1.0f;
+            ip.fscale[j] = fs;
+            ip.inv_fscale[j] = 1.0f / fs;
+        }
+        ip.W = c.width;
+        ip.H = c.height;
+        ip.tiles_x = b->tiles_x[i];
+        ip.slot = t % c0.frames;
+        ip.test = (c0.mode == ESIM_AD_ADAPTIVE && t64 > 0) ? 1 : 0;
+        ip.log_eps = c0.log_eps;
+        ip.C = c.contrast;
+        ip.ring = b->ring[i];
+        ip.state = b->state[i];
+        ip.flag = b->flag[i];
+        ip.nev = b->nev[i];
+        WlrParams& wp = st.wp;
+        wp.W = c.width;
+        wp.H = c.height;
+        wp.r = c0.radius;
+        wp.T = c0.frames;
+        wp.t = t;
+        wp.n_tau = (int)((t64 + 1) < (uint64_t)c0.frames ? (t64 + 1) : (uint64_t)c0.frames);
+        wp.tiles_x = b->tiles_x[i];
+        wp.n_tiles = b->n_tiles[i];
+        wp.mixed = b->mixed ? 1 : 0;
+        wp.init = t64 == 0 ? 1 : 0;
+        wp.C = c.contrast;
+        wp.s_coord = (float)(kExp2Scale / c0.h);
+        wp.s_coord_px = (float)(kExp2Scale / ((double)c0.h * c0.radius));
+        for (int j = 0; j < 7; ++j) {
+            wp.s_feat[j] = (float)(kExp2Scale / ((double)c0.h * c0.bandwidth[j]));
+            wp.fscale[j] = b->mixed ? c0.feature_scale[j] : 1.0f;
+            wp.q_scale[j] = (float)((double)wp.s_feat[j] * wp.fscale[j]);
+        }
+        wp.ridge = c0.ridge;
+        wp.ring = b->ring[i];
+        wp.state = b->state[i];
+        wp.alpha = b->alpha[i];
+        wp.nev = b->nev[i];
+        wp.chunk_cnt = b->chunk_cnt + b->chunk_base[i];
+        wp.chunk_off = b->chunk_off + b->chunk_base[i];
+        wp.n_chunks = b->n_chunks[i];
+        wp.emit_events = 1;
+        wp.ctrl = b->ctrl;
+    }
+}
+
+// Enqueue one step's work (after the step table has been copied) on stream s.
+cudaError_t enqueue_step_body(esim_ad_batch* b, int lanes, cudaStream_t s, bool profile)
+{
+    const BatchGlobal g = globals(b);
+    auto rec = [&](int cls, bool start) {
+        if (!profile) return;
+        if (start) {
+            if (2 * b->prof_used + 2 > b->prof_ev.size())
+                for (int k = 0; k < 2; ++k) {
+                    cudaEvent_t e;
+                    if (cudaEventCreate(&e) == cudaSuccess) b->prof_ev.push_back(e);
+                }
+            b->prof_cls.resize(b->prof_used + 1);
+            b->prof_cls[b->prof_used] = cls;
+            cudaEventRecord(b->prof_ev[2 * b->prof_used], s);
+        } else {
+            cudaEventRecord(b->prof_ev[2 * b->prof_used + 1], s);
+            ++b->prof_used;
+        }
+    };
+    cudaError_t e = cudaMemsetAsync(b->ctrl, 0, kCtrlPerFrameBytes, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b->chunk_cnt, 0, (size_t)b->total_chunks * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    rec(0, true);
+    batch_ingest_kernel<<<b->total_tiles, kTilePix, 0, s>>>(g);
+    rec(0, false);
+    rec(1, true);
+    pick_kernel(lanes, b->mixed)<<<b->grid, kTilePix, 0, s>>>(g, global_wlr(b));
+    rec(1, false);
+    rec(2, true);
+    batch_event_write_kernel<<<b->total_chunks, kTilePix, 0, s>>>(g);
+    rec(2, false);
+    b->prof_kernels += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t build_graphs(esim_ad_batch* b, int lanes)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (b->graph[k]) {
+            cudaGraphExecDestroy(b->graph[k]);
+            b->graph[k] = nullptr;
+        }
+        // captured on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); launched on the caller's stream
+        cudaGraph_t gr;
+        cudaStream_t cs;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return e;
+        }
+        cudaMemcpyAsync(b->d_steps, b->h_steps[k], sizeof(SeqStep) * b->n, cudaMemcpyHostToDevice, cs);
+        const uint64_t kern = b->prof_kernels;
+        enqueue_step_body(b, lanes, cs, false);
+        b->prof_kernels = kern;
+        e = cudaStreamEndCapture(cs, &gr);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&b->graph[k], gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return e;
+    }
+    b->graph_lanes = lanes;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, void* cuda_stream,
+                                  esim_ad_batch** out)
+{
+    if (!cfgs || !out || n_seq < 1 || n_seq > kMaxSeq) return ESIM_AD_EINVAL;
+    const esim_ad_config& c0 = cfgs[0];
+    for (int i = 0; i < n_seq; ++i) {
+        const esim_ad_config& c = cfgs[i];
+        if (c.struct_size != sizeof(esim_ad_config) || c.width < 1 || c.height < 1 || c.width > 65535 ||
+            c.height > 65535 || (long long)c.width * c.height > (1ll << kPixBits) || !(c.contrast > 0.0f))
+            return ESIM_AD_EINVAL;
+        if (c.radius != c0.radius || c.frames != c0.frames || c.mode != c0.mode ||
+            c.radiance_fmt != c0.radiance_fmt || c.feature_fmt != c0.feature_fmt || c.precision != c0.precision ||
+            c.h != c0.h || c.log_eps != c0.log_eps || c.ridge != c0.ridge ||
+            memcmp(c.bandwidth, c0.bandwidth, sizeof(c.bandwidth)) != 0 ||
+            memcmp(c.feature_scale, c0.feature_scale, sizeof(c.feature_scale)) != 0)
+            return ESIM_AD_EINVAL;
+    }
+    // the shared fields go through the single-sequence checks
+    {
+        const esim_ad_config& probe = c0;
+        if (probe.radius < 1 || probe.radius > kMaxRadius || probe.frames < 1 || probe.frames > kMaxFrames ||
+            (probe.mode != ESIM_AD_ADAPTIVE && probe.mode != ESIM_AD_EXHAUSTIVE) || !(probe.h > 0.0f) ||
+            !(probe.ridge > 0.0f) || probe.log_eps < 0.0f || probe.event_capacity < 1 ||
+            (probe.precision != ESIM_AD_FP32 && probe.precision != ESIM_AD_MIXED) ||
+            (probe.radiance_fmt != ESIM_AD_LUMA_F32 && probe.radiance_fmt != ESIM_AD_RGB_F32 &&
+             probe.radiance_fmt != ESIM_AD_LOGLUMA_F16) ||
+            (probe.feature_fmt != ESIM_AD_FEAT_F32 && probe.feature_fmt != ESIM_AD_FEAT_BF16))
+            return ESIM_AD_EINVAL;
+        for (int j = 0; j < 7; ++j)
+            if (!(probe.bandwidth[j] > 0.0f)) return ESIM_AD_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ESIM_AD_ECUDA;
+    }
+    esim_ad_batch* b = new (std::nothrow) esim_ad_batch();
+    if (!b) return ESIM_AD_ENOMEM;
+    b->cfg.assign(cfgs, cfgs + n_seq);
+    b->n = n_seq;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->device = dev;
+    b->mixed = c0.precision == ESIM_AD_MIXED;
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    b->N.resize(n_seq);
+    b->tiles_x.resize(n_seq);
+    b->n_tiles.resize(n_seq);
+    b->n_chunks.resize(n_seq);
+    b->tile_base.resize(n_seq);
+    b->chunk_base.resize(n_seq);
+    b->ring.assign(n_seq, nullptr);
+    b->state.assign(n_seq, nullptr);
+    b->alpha.assign(n_seq, nullptr);
+    b->flag.assign(n_seq, nullptr);
+    b->nev.assign(n_seq, nullptr);
+    b->t.assign(n_seq, 0);
+    std::vector<uint16_t> tseq, cseq;
+    for (int i = 0; i < n_seq; ++i) {
+        const esim_ad_config& c = cfgs[i];
+        b->N[i] = (size_t)c.width * c.height;
+        b->tiles_x[i] = (c.width + kTileX - 1) / kTileX;
+        b->n_tiles[i] = b->tiles_x[i] * ((c.height + kTileY - 1) / kTileY);
+        b->n_chunks[i] = (int)((b->N[i] + kChunk - 1) / kChunk);
+        b->tile_base[i] = b->total_tiles;
+        b->chunk_base[i] = b->total_chunks;
+        b->total_tiles += b->n_tiles[i];
+        b->total_chunks += b->n_chunks[i];
+        b->total_pix += b->N[i];
+        tseq.insert(tseq.end(), b->n_tiles[i], (uint16_t)i);
+        cseq.insert(cseq.end(), b->n_chunks[i], (uint16_t)i);
+    }
+    auto fail = [&](esim_ad_status st) {
+        cudaGetLastError();
+        batch_release(b);
+        delete b;
+        return st;
+    };
+    const size_t ring_rec = b->mixed ? 1 : 2;
+    for (int i = 0; i < n_seq; ++i) {
+        const size_t N = b->N[i];
+        if (cudaMalloc(&b->ring[i], ring_rec * c0.frames * N * 16) != cudaSuccess ||
+            cudaMalloc((void**)&b->state[i], 4 * N * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc((void**)&b->alpha[i], N * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&b->flag[i], N) != cudaSuccess ||
+            cudaMalloc((void**)&b->nev[i], N * sizeof(int32_t)) != cudaSuccess)
+            return fail(ESIM_AD_ENOMEM);
+        if (cudaMemset(b->state[i], 0, 4 * N * sizeof(float4)) != cudaSuccess ||
+            cudaMemset(b->nev[i], 0, N * sizeof(int32_t)) != cudaSuccess)
+            return fail(ESIM_AD_ECUDA);
+    }
+    if (cudaMalloc((void**)&b->tile_seq, tseq.size() * 2) != cudaSuccess ||
+        cudaMalloc((void**)&b->chunk_seq, cseq.size() * 2) != cudaSuccess ||
+        cudaMalloc((void**)&b->flag_list, b->total_pix * 4) != cudaSuccess ||
+        cudaMalloc((void**)&b->chunk_cnt, (size_t)b->total_chunks * 4) != cudaSuccess ||
+        cudaMalloc((void**)&b->chunk_off, (size_t)b->total_chunks * 8) != cudaSuccess ||
+        cudaMalloc((void**)&b->events, (size_t)c0.event_capacity * sizeof(esim_ad_batch_event)) != cudaSuccess ||
+        cudaMalloc((void**)&b->ctrl, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_steps, sizeof(SeqStep) * n_seq) != cudaSuccess)
+        return fail(ESIM_AD_ENOMEM);
+    for (int k = 0; k < 2; ++k) {
+        if (cudaMallocHost((void**)&b->h_steps[k], sizeof(SeqStep) * n_seq) != cudaSuccess)
+            return fail(ESIM_AD_ENOMEM);
+        if (cudaEventCreateWithFlags(&b->h_free[k], cudaEventDisableTiming) != cudaSuccess)
+            return fail(ESIM_AD_ECUDA);
+        memset(b->h_steps[k], 0, sizeof(SeqStep) * n_seq);
+    }
+    for (cudaEvent_t& e : b->tune_ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(ESIM_AD_ECUDA);
+    if (cudaMemcpy(b->tile_seq, tseq.data(), tseq.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->chunk_seq, cseq.data(), cseq.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->ctrl, 0, sizeof(Ctrl)) != cudaSuccess)
+        return fail(ESIM_AD_ECUDA);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(16, b->mixed), kTilePix, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    cudaGetLastError();
+    b->grid = per_sm * b->num_sms;
+    // lanes per pixel: forced, cached, or tuned on the first adaptive steps
+    if (const char* e = getenv("ESIM_AD_BATCH_LANES")) {
+        const int v = atoi(e);
+        if (v == 8 || v == 16 || v == 32) {
+            b->lanes = v;
+            b->tuned = true;
+        }
+    }
+    if (!b->tuned) {
+        const int v = cache_lookup(b);
+        if (v) {
+            b->lanes = v;
+            b->tuned = true;
+        }
+    }
+    if (build_graphs(b, b->lanes) != cudaSuccess) return fail(ESIM_AD_ECUDA);
+    *out = b;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_step(esim_ad_batch* b, const esim_ad_frame* frames)
+{
+    if (!b || !frames) return ESIM_AD_EINVAL;
+    if (b->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    for (int i = 0; i < b->n; ++i) {
+        const esim_ad_frame& f = frames[i];
+        if (!f.radiance) continue;
+        if (f.on_host) return ESIM_AD_EINVAL;
+        if (b->cfg[0].feature_fmt == ESIM_AD_FEAT_BF16 ? !f.features : (!f.normal || !f.albedo || !f.depth))
+            return ESIM_AD_EINVAL;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    const int k = b->cur;
+    // the pinned table k was last read by the step launched two steps ago
+    if (cudaEventSynchronize(b->h_free[k]) != cudaSuccess) return ESIM_AD_ECUDA;
+    fill_steps(b, b->h_steps[k], frames);
+    bool any_init = false, any_active = false;
+    for (int i = 0; i < b->n; ++i)
+        if (frames[i].radiance) {
+            any_active = true;
+            any_init |= b->t[i] == 0;
+        }
+    cudaError_t e = cudaSuccess;
+    // autotuning: the first adaptive steps without sequence starts time one candidate each
+    const bool tuning = !b->tuned && any_active && !any_init && b->cfg[0].mode == ESIM_AD_ADAPTIVE;
+    if (tuning || b->prof_on) {
+        // direct launches (timed) instead of the graph
+        e = cudaMemcpyAsync(b->d_steps, b->h_steps[k], sizeof(SeqStep) * b->n, cudaMemcpyHostToDevice, b->stream);
+        const int lanes = tuning ? kCandidates[b->tune_stage] : b->lanes;
+        if (tuning) cudaEventRecord(b->tune_ev[2 * b->tune_stage], b->stream);
+        if (e == cudaSuccess) e = enqueue_step_body(b, lanes, b->stream, b->prof_on);
+        if (tuning) cudaEventRecord(b->tune_ev[2 * b->tune_stage + 1], b->stream);
+    } else {
+        e = cudaGraphLaunch(b->graph[k], b->stream);
+        b->prof_kernels += 3;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->h_free[k], b->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+        return ESIM_AD_ECUDA;
+    }
+    if (tuning) {
+        // per-regression time of this candidate (the step's regressions from the counters)
+        Ctrl h;
+        cudaMemcpyAsync(&h, b->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream);
+        cudaStreamSynchronize(b->stream);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, b->tune_ev[2 * b->tune_stage], b->tune_ev[2 * b->tune_stage + 1]);
+        b->tune_ms[b->tune_stage] = ms;
+        b->tune_reg[b->tune_stage] = h.regressions - b->reg_before;
+        b->reg_before = h.regressions;
+        if (++b->tune_stage == 3) {
+            int best = 1;
+            double best_cost = 1e300;
+            for (int c = 0; c < 3; ++c) {
+                const double cost = b->tune_ms[c] / (double)(b->tune_reg[c] ? b->tune_reg[c] : 1);
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best = c;
+                }
+            }
+            b->lanes = kCandidates[best];
+            b->tuned = true;
+            cache_store(b, b->lanes);
+            if (build_graphs(b, b->lanes) != cudaSuccess) return ESIM_AD_ECUDA;
+        }
+    } else if (!b->tuned) {
+        // keep the regression count current for the tuning steps to come
+        Ctrl h;
+        cudaMemcpyAsync(&h, b->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream);
+        cudaStreamSynchronize(b->stream);
+        b->reg_before = h.regressions;
+    }
+    for (int i = 0; i < b->n; ++i)
+        if (frames[i].radiance) b->t[i] += 1;
+    b->cur ^= 1;
+    b->steps += 1;
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_events(esim_ad_batch* b, esim_ad_batch_event* dst, uint64_t cap, uint64_t* n_out,
+                                    int dst_is_device)
+{
+    if (!b || !n_out || (cap > 0 && !dst)) return ESIM_AD_EINVAL;
+    if (b->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    Ctrl h;
+    if (cudaMemcpyAsync(&h, b->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    if (h.status & kStatusTimeout) b->sticky = ESIM_AD_ETIMEOUT;
+    else if (h.status & kStatusOverflow) b->sticky = ESIM_AD_EOVERFLOW;
+    *n_out = h.ev_total;
+    if (b->sticky != ESIM_AD_OK) return b->sticky;
+    if (cap < h.ev_total) return ESIM_AD_ENOSPACE;
+    if (h.ev_total > 0) {
+        if (cudaMemcpyAsync(dst, b->events, h.ev_total * sizeof(esim_ad_batch_event),
+                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+            cudaMemsetAsync(&b->ctrl->ev_total, 0, sizeof(unsigned long long), b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+    }
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_reset_sequence(esim_ad_batch* b, int32_t seq)
+{
+    if (!b || seq < 0 || seq >= b->n) return ESIM_AD_EINVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    b->t[seq] = 0;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_denoised(esim_ad_batch* b, int32_t seq, float* alpha, uint8_t* flags,
+                                      int dst_is_device)
+{
+    if (!b || seq < 0 || seq >= b->n) return ESIM_AD_EINVAL;
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t N = b->N[seq];
+    if ((alpha && cudaMemcpyAsync(alpha, b->alpha[seq], N * sizeof(float), k, b->stream) != cudaSuccess) ||
+        (flags && cudaMemcpyAsync(flags, b->flag[seq], N, k, b->stream) != cudaSuccess) ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_get_state(esim_ad_batch* b, int32_t seq, float* l_last, float* beta, float* xc)
+{
+    if (!b || seq < 0 || seq >= b->n) return ESIM_AD_EINVAL;
+    const size_t N = b->N[seq];
+    std::vector<float4> h(4 * N);
+    if (cudaMemcpyAsync(h.data(), b->state[seq], 4 * N * sizeof(float4), cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    for (size_t i = 0; i < N; ++i) {
+        const float4 b0 = h[i], b1 = h[N + i], x0 = h[2 * N + i], x1 = h[3 * N + i];
+        if (l_last) l_last[i] = x1.w;
+        if (beta) {
+            float* q = beta + 7 * i;
+            q[0] = b0.x; q[1] = b0.y; q[2] = b0.z; q[3] = b0.w; q[4] = b1.x; q[5] = b1.y; q[6] = b1.z;
+        }
+        if (xc) {
+            float* q = xc + 7 * i;
+            q[0] = x0.x; q[1] = x0.y; q[2] = x0.z; q[3] = x0.w; q[4] = x1.x; q[5] = x1.y; q[6] = x1.z;
+        }
+    }
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_stats(esim_ad_batch* b, esim_ad_stats* out, int32_t* lanes_out)
+{
+    if (!b || !out) return ESIM_AD_EINVAL;
+    Ctrl h;
+    if (cudaMemcpyAsync(&h, b->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    out->frames = b->steps;
+    out->regressions = h.regressions;
+    out->events = h.ev_cum;
+    out->pixels = b->total_pix;
+    out->fp64_solves = h.fp64_solves;
+    if (lanes_out) *lanes_out = b->lanes;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_profile_enable(esim_ad_batch* b, int on)
+{
+    if (!b) return ESIM_AD_EINVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    b->prof_on = on != 0;
+    b->prof_used = 0;
+    b->prof_kernels = 0;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_profile_get(esim_ad_batch* b, esim_ad_profile* out)
+{
+    if (!b || !out) return ESIM_AD_EINVAL;
+    Ctrl h;
+    if (cudaMemcpyAsync(&h, b->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    memset(out, 0, sizeof(*out));
+    for (size_t k = 0; k < b->prof_used; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, b->prof_ev[2 * k], b->prof_ev[2 * k + 1]) != cudaSuccess) return ESIM_AD_ECUDA;
+        out->launches[b->prof_cls[k]] += 1;
+        out->ms[b->prof_cls[k]] += ms;
+    }
+    out->kernels = b->prof_kernels;
+    out->neighbours = h.neighbours;
+    out->regressions = h.regressions;
+    return ESIM_AD_OK;
+}
+
+void esim_ad_batch_destroy(esim_ad_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    delete b;
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 // simulator's regression kernels and by the differentiation-form kernels.
 #pragma once
 
+#include "block_scan.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -244,6 +245,117 @@ __device__ __noinline__ int solve_mixed(Acc& a, const float (&s2)[NZ], float rid
     return used64;
 }
 
+
+// Eq. 1 at a fixed frame time, and the model update of Fig. 1.
+template <bool kMixed>
+__device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const float (&theta)[NZ])
+{
+    const size_t N = (size_t)p.W * p.H;
+    const size_t i = (size_t)cy * p.W + cx;
+    const float alpha = theta[0];
+    float bf[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) bf[j] = theta[3 + j] * p.s_feat[j];
+    p.alpha[i] = alpha;
+    float L;
+    if (p.init) {
+        L = alpha;
+    } else {
+        L = p.state[3 * N + i].w;
+        const float dl = alpha - L;
+        const float n = floorf(fabsf(dl) / p.C);
+        if (!(n >= 1.0f)) return;  // no event: keep the model
+        const float pol = dl > 0.0f ? 1.0f : -1.0f;
+        L = fmaf(pol * n, p.C, L);
+        p.nev[i] = (int32_t)(pol * n);
+        atomicAdd(&p.chunk_cnt[i / kChunk], (uint32_t)n);
+    }
+    const int slot = p.t % p.T;
+    float x[7];
+    if (kMixed) {
+        float y, q[7];
+        unpack_mixed(reinterpret_cast<const uint4*>(p.ring)[(size_t)slot * N + i], y, q);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) x[j] = q[j] * p.fscale[j];
+    } else {
+        const float4* ring = reinterpret_cast<const float4*>(p.ring);
+        const float4 x0 = ring[(size_t)(2 * slot) * N + i];
+        const float4 x1 = ring[(size_t)(2 * slot + 1) * N + i];
+        x[0] = x0.y; x[1] = x0.z; x[2] = x0.w; x[3] = x1.x; x[4] = x1.y; x[5] = x1.z; x[6] = x1.w;
+    }
+    const float4 b0 = make_float4(bf[0], bf[1], bf[2], bf[3]);
+    float4 b1 = make_float4(bf[4], bf[5], bf[6], 0.0f);
+    b1.w = dot7(b0, b1, x[0], x[1], x[2], x[3], x[4], x[5], x[6]);
+    p.state[i] = b0;
+    p.state[N + i] = b1;
+    p.state[2 * N + i] = make_float4(x[0], x[1], x[2], x[3]);
+    p.state[3 * N + i] = make_float4(x[4], x[5], x[6], L);
+}
+
+// Regress one pixel from its reduced sums, then emit (both forms).
+template <bool kMixed>
+__device__ __forceinline__ void solve_and_emit(const WlrParams& p, Acc& acc, int cx, int cy,
+                                               unsigned long long* fp64_count)
+{
+    float s2[NZ];
+    s2[0] = 0.0f;
+    s2[1] = p.s_coord * p.s_coord;
+    s2[2] = s2[1];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) s2[3 + j] = p.s_feat[j] * p.s_feat[j];
+    float theta[NZ];
+    if (kMixed) {
+        if (solve_mixed(acc, s2, p.ridge, theta)) atomicAdd(fp64_count, 1ull);
+    } else {
+        solve(acc, s2, p.ridge, theta);
+    }
+    emit<kMixed>(p, cx, cy, theta);
+}
+
+// End of a regression launch: add this CTA's work counters, record a timeout,
+// and, when events are emitted, take a ticket; the last CTA to finish scans
+// the per-chunk event counts into output offsets (no CTA waits on another).
+__device__ __forceinline__ void finish(const WlrParams& p, unsigned long long pairs,
+                                       unsigned long long pix, unsigned long long fp64, bool timed_out)
+{
+    __shared__ int s_timeout, s_last;
+    __shared__ int s_warp[8];
+    if (threadIdx.x == 0) {
+        s_timeout = 0;
+        s_last = 0;
+    }
+    __syncthreads();
+    if (timed_out) s_timeout = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (pairs) atomicAdd(&p.ctrl->neighbours, pairs);
+        if (pix) atomicAdd(&p.ctrl->regressions, pix);
+        if (fp64) atomicAdd(&p.ctrl->fp64_solves, fp64);
+        if (s_timeout) atomicOr(&p.ctrl->status, kStatusTimeout);
+        if (p.emit_events) {
+            __threadfence();
+            const uint32_t ticket = atomicAdd(&p.ctrl->chunk_done, 1u);
+            s_last = (ticket == gridDim.x - 1u) ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long running = *(volatile unsigned long long*)&p.ctrl->ev_total;
+    const unsigned long long start = running;
+    for (int base = 0; base < p.n_chunks; base += blockDim.x) {
+        const int j = base + (int)threadIdx.x;
+        const int v = (j < p.n_chunks) ? (int)*(volatile uint32_t*)&p.chunk_cnt[j] : 0;
+        int seg;
+        const int off = block_exclusive_scan(v, s_warp, seg);
+        if (j < p.n_chunks) p.chunk_off[j] = running + (unsigned long long)off;
+        running += (unsigned long long)seg;
+    }
+    if (threadIdx.x == 0) {
+        p.ctrl->ev_total = running;
+        p.ctrl->ev_cum += running - start;
+    }
+}
 
 }  // namespace
 }  // namespace esim
