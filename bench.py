@@ -350,10 +350,12 @@ def run_ours(args):
         "gpu_launches": int(prof_a["kernels"]),
         "clocks": clocks,
     }
-    if rank == 0 and not args.no_diff:
-        line["differentiation_form"] = _differentiation(dev)
     if rank == 0 and not args.no_e2e:
         line["e2e"] = _e2e(args, scene, wl, N, stream)
+    if rank == 0 and not args.no_diff:
+        line["differentiation_form"] = _differentiation(dev)
+    if rank == 0 and not args.no_batch:
+        line["batching_form"] = _batching(dev)
     if rank == 0 and not args.no_cpu_baseline:
         nb = min(len(frames), 48)
         frames_cpu = [_dequantised_cpu(f) for f in sframes[:nb]]
@@ -362,6 +364,66 @@ def run_ours(args):
         dist.barrier()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _batching(dev, warmup=4, steps=12):
+    """The batching workload: 48 sequences (resolutions from {256^2, 640x480,
+    1280x720, 1920x1080}, 32-128 frames, 2-16 spp, 15x15x5 window, C = 0.15),
+    stepped together through the batch API (one graph per step), against the
+    same sequences stepped through one context each.  Frames are generated
+    before each step's timed region."""
+    import torch
+    from paper_2303_02608_gb300 import Batch, SimConfig, Simulator
+    from scenes import Scene, batch_configs
+    cfgs = batch_configs(48, seed=0)
+    scenes = [Scene(c) for c in cfgs]
+    sims = [SimConfig(width=c.width, height=c.height, radius=7, frames=5, contrast=0.15,
+                      event_capacity=1 << 24) for c in cfgs]
+    stream = torch.cuda.current_stream()
+    batch = Batch(sims, stream)
+    ctxs = [Simulator(sc, stream) for sc in sims]
+    cap = 1 << 24
+    sink = torch.empty(cap * 12, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_batch = t_ctx = 0.0
+    px_total = 0
+    for step in range(warmup + steps):
+        frames = []
+        for sc in scenes:
+            if step < sc.cfg.frames:
+                f = sc.frame(step, dev)
+                frames.append({k: f[k] for k in ("radiance", "normal", "albedo", "depth")})
+            else:
+                frames.append(None)
+        px = sum(c.width * c.height for c, f in zip(cfgs, frames) if f is not None)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        batch.step(frames)
+        ev[1].record(stream)
+        batch.events_device(sink, cap)
+        ev[2].record(stream)
+        for c, f in zip(ctxs, frames):
+            if f is not None:
+                c.push(f)
+        ev[3].record(stream)
+        for c in ctxs:
+            c.events_device(sink, cap)
+        torch.cuda.synchronize()
+        if step >= warmup:
+            t_batch += ev[0].elapsed_time(ev[1])
+            t_ctx += ev[2].elapsed_time(ev[3])
+            px_total += px
+    st = batch.stats()
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "48 sequences, resolutions {256^2, 640x480, 1280x720, 1920x1080}, 32-128 frames, "
+                        "2-16 spp, 15x15x5 window, C=0.15, fp32",
+            "value": round(px_total / (t_batch * 1e-3), 1), "unit": UNIT, "steps": steps,
+            "ms_per_step": round(t_batch / steps, 3), "pixels_per_step": round(px_total / steps),
+            "per_sequence_contexts": {"value": round(px_total / (t_ctx * 1e-3), 1),
+                                      "ms_per_step": round(t_ctx / steps, 3)},
+            "autotuned_lanes_per_pixel": st["lanes"], "graph_per_step": True}
 
 
 def _differentiation(dev, reps=5):
@@ -506,11 +568,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rects1080p")
-    ap.add_argument("--e2e-steps", type=int, default=61)
+    ap.add_argument("--e2e-steps", type=int, default=117)
     ap.add_argument("--event-capacity", type=int, default=1 << 27)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
