@@ -325,13 +325,6 @@ namespace {
 
 const int kCandidates[3] = {8, 16, 32};
 
-std::string cache_path()
-{
-    if (const char* p = getenv("ESIM_AD_CACHE")) return p;
-    const char* home = getenv("HOME");
-    return std::string(home ? home : ".") + "/.cache/esim_ad_autotune.txt";
-}
-
 std::string cache_key(const esim_ad_batch* b)
 {
     char k[128];
@@ -342,32 +335,11 @@ std::string cache_key(const esim_ad_batch* b)
 
 int cache_lookup(const esim_ad_batch* b)
 {
-    FILE* f = fopen(cache_path().c_str(), "r");
-    if (!f) return 0;
-    const std::string key = cache_key(b);
-    char line[256];
-    int found = 0;
-    while (fgets(line, sizeof(line), f)) {
-        const size_t L = key.size();
-        if (strncmp(line, key.c_str(), L) == 0 && line[L] == ' ') {
-            const int v = atoi(line + L + 1);
-            if (v == 8 || v == 16 || v == 32) found = v;
-        }
-    }
-    fclose(f);
-    return found;
+    const int v = tune_cache_lookup(cache_key(b).c_str());
+    return (v == 8 || v == 16 || v == 32) ? v : 0;
 }
 
-void cache_store(const esim_ad_batch* b, int lanes)
-{
-    const std::string path = cache_path();
-    const size_t slash = path.rfind('/');
-    if (slash != std::string::npos) mkdir(path.substr(0, slash).c_str(), 0755);   // may already exist
-    FILE* f = fopen(path.c_str(), "a");
-    if (!f) return;   // the cache is an optimisation only
-    fprintf(f, "%s %d\n", cache_key(b).c_str(), lanes);
-    fclose(f);
-}
+void cache_store(const esim_ad_batch* b, int lanes) { tune_cache_store(cache_key(b).c_str(), lanes); }
 
 void batch_release(esim_ad_batch* b)
 {

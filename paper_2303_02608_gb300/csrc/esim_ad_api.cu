@@ -2,6 +2,7 @@
 // device memory, the TMA descriptor of the frame ring, and the per-frame
 // launch sequence of the hot path.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -65,6 +66,13 @@ struct esim_ad_ctx {
     int sparse_grid = 0;
     bool mixed = false;
     uint32_t sparse_max = 0;     // adaptive frames with at most this many flagged pixels use the sparse kernel
+    int sparse_lanes = 16;       // lanes per pixel of the sparse kernel (8 or 16)
+    // autotuning of sparse_lanes: candidates timed on the first sparse adaptive frames
+    bool lanes_tuned = false;
+    int tune_stage = 0;
+    double tune_cost[2] = {0.0, 0.0};
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+    char tune_key[96] = {0};
     float4* ring = nullptr;
     float4* state = nullptr;
     float* alpha = nullptr;
@@ -145,6 +153,8 @@ void release(esim_ad_ctx* c)
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     c->prof_events.clear();
+    for (cudaEvent_t e : c->tune_ev)
+        if (e) cudaEventDestroy(e);
 }
 
 // Bracket one launch with a pair of pooled events when profiling is on.
@@ -310,6 +320,23 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     if (const char* e = getenv("ESIM_AD_SPARSE_MAX")) {
         if (*e) c->sparse_max = (uint32_t)strtoul(e, nullptr, 10);
     }
+    snprintf(c->tune_key, sizeof(c->tune_key), "sparse r=%d T=%d precision=%d sms=%d", cfg->radius,
+             cfg->frames, cfg->precision, num_sms);
+    if (const char* e = getenv("ESIM_AD_SPARSE_LANES")) {
+        const int v = atoi(e);
+        if (v == 8 || v == 16) {
+            c->sparse_lanes = v;
+            c->lanes_tuned = true;
+        }
+    }
+    if (!c->lanes_tuned) {
+        const int v = tune_cache_lookup(c->tune_key);
+        if (v == 8 || v == 16) {
+            c->sparse_lanes = v;
+            c->lanes_tuned = true;
+        }
+    }
+    if (cfg->mode != ESIM_AD_ADAPTIVE) c->lanes_tuned = true;   // the sparse kernel never runs
     *out = c;
     return ESIM_AD_OK;
 }
@@ -478,8 +505,34 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
             return ESIM_AD_ECUDA;
         // adaptive frames: the sparse kernel takes the frame when few pixels are
         // flagged; each of the two launches returns at once on the other's frames
-        if (!wp.dense && launch_wlr_sparse(wp, c->mixed, c->sparse_grid, c->stream) != cudaSuccess)
+        const bool tuning = !wp.dense && !c->lanes_tuned;
+        const int lanes = tuning ? (c->tune_stage == 0 ? 16 : 8) : c->sparse_lanes;
+        if (tuning && !c->tune_ev[0]) {
+            if (cudaEventCreate(&c->tune_ev[0]) != cudaSuccess || cudaEventCreate(&c->tune_ev[1]) != cudaSuccess)
+                return ESIM_AD_ECUDA;
+        }
+        if (tuning) cudaEventRecord(c->tune_ev[0], c->stream);
+        if (!wp.dense && launch_wlr_sparse(wp, c->mixed, lanes, c->sparse_grid, c->stream) != cudaSuccess)
             return ESIM_AD_ECUDA;
+        if (tuning) {
+            // time this candidate per regression; frames that went to the
+            // tile-staged kernel (too many flags) do not count
+            cudaEventRecord(c->tune_ev[1], c->stream);
+            Ctrl h;
+            if (cudaMemcpyAsync(&h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return ESIM_AD_ECUDA;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]);
+            if (h.flag_total > 0 && h.flag_total <= c->sparse_max) {
+                c->tune_cost[c->tune_stage] = (double)ms / (double)h.flag_total;
+                if (++c->tune_stage == 2) {
+                    c->sparse_lanes = c->tune_cost[1] < c->tune_cost[0] ? 8 : 16;
+                    c->lanes_tuned = true;
+                    tune_cache_store(c->tune_key, c->sparse_lanes);
+                }
+            }
+        }
         c->prof_kernels += wp.dense ? 1 : 2;
     }
 

@@ -161,13 +161,17 @@ struct EventParams {
 };
 
 cudaError_t launch_ingest(const IngestParams& p, int n_tiles, cudaStream_t s);
+
+// Autotuning cache (tune_cache.cu): value for key, or 0 if none.
+int tune_cache_lookup(const char* key);
+void tune_cache_store(const char* key, int value);
 cudaError_t wlr_prepare(int smem_bytes, bool mixed);
 size_t wlr_smem_bytes(int r, bool mixed, int max_smem_per_sm, int* nbuf);
 int wlr_grid(int smem_bytes, int num_sms, bool mixed);
 int wlr_sparse_grid(int num_sms, bool mixed);
 cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, bool mixed, int grid,
                        int smem_bytes, cudaStream_t s);
-cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s);
+cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int lanes, int grid, cudaStream_t s);
 cudaError_t launch_events(const EventParams& p, cudaStream_t s);
 cudaError_t launch_event_write(const EventParams& p, cudaStream_t s);
 

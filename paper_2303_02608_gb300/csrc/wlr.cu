@@ -354,12 +354,13 @@ __global__ void __launch_bounds__(kTilePix, 2)
 // warp owns two of them, 16 lanes per pixel split its window, and the lanes
 // are shuffle-reduced.  Interior pixels all cost the same, so the per-block
 // barrier waits little.
-template <bool kMixed>
+template <bool kMixed, int kLanes>
 __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams p)
 {
     if (p.sparse_max == 0 || *(volatile uint32_t*)&p.ctrl->flag_total > p.sparse_max)
         return;  // the tile-staged kernel's frame
-    constexpr int kLanes = 16;
+    constexpr int kPerWarp = 32 / kLanes;              // pixels per warp
+    constexpr int kBlock = (kTilePix / 32) * kPerWarp;  // list entries per CTA block
     __shared__ float4 table[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];
     __shared__ unsigned long long s_pairs, s_pix, s_fp64;
     const int side = 2 * p.r + 1, nq = side * side;
@@ -382,21 +383,20 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
     const uint4* ringm = reinterpret_cast<const uint4*>(p.ring);
     const int lane = threadIdx.x & 31;
     const int sub = lane & (kLanes - 1);
-    const int half = lane >> 4;
+    const int grp = lane / kLanes;
     const int slot_t = p.t % p.T;
     Acc acc;
     float cf[7];
     __shared__ uint32_t s_base;
     for (;;) {
-        // the CTA takes 16 consecutive list entries (neighbours in one tile, so
-        // the warps' windows overlap in L1); warp w owns entries 2w and 2w+1
-        if (threadIdx.x == 0) s_base = atomicAdd(&p.ctrl->work_next, 16u);
+        // the CTA takes kBlock consecutive list entries (neighbours in one tile,
+        // so the warps' windows overlap in L1); each warp owns kPerWarp of them
+        if (threadIdx.x == 0) s_base = atomicAdd(&p.ctrl->work_next, (uint32_t)kBlock);
         __syncthreads();
         const uint32_t blk = s_base;
         __syncthreads();   // all have read the block before thread 0 takes the next
         if (blk >= n_flag) break;
-        const uint32_t base = blk + 2u * (threadIdx.x >> 5);
-        const uint32_t my = base + (uint32_t)half;
+        const uint32_t my = blk + (uint32_t)((threadIdx.x >> 5) * kPerWarp + grp);
         const bool active = my < n_flag;
         const uint32_t pix = active ? p.flag_list[my] : 0u;
         const int cx = (int)(pix % (uint32_t)p.W), cy = (int)(pix / (uint32_t)p.W);
@@ -470,6 +470,7 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
                 }
             }
         }
+#pragma unroll
         for (int off = kLanes >> 1; off >= 1; off >>= 1) {
 #pragma unroll
             for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
@@ -486,25 +487,29 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
     finish(p, s_pairs, s_pix, s_fp64, false);
 }
 
+typedef void (*SparseKernel)(const WlrParams);
+
+SparseKernel sparse_kernel(bool mixed, int lanes)
+{
+    if (mixed) return lanes == 8 ? wlr_sparse_kernel<true, 8> : wlr_sparse_kernel<true, 16>;
+    return lanes == 8 ? wlr_sparse_kernel<false, 8> : wlr_sparse_kernel<false, 16>;
+}
+
 int wlr_sparse_grid(int num_sms, bool mixed)
 {
     int per_sm = 0;
-    const cudaError_t e = mixed
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel<true>, kTilePix, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel<false>, kTilePix, 0);
-    if (e != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel(mixed, 16), kTilePix, 0) !=
+            cudaSuccess ||
+        per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
     return per_sm * num_sms;
 }
 
-cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s)
+cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int lanes, int grid, cudaStream_t s)
 {
-    if (mixed)
-        wlr_sparse_kernel<true><<<grid, kTilePix, 0, s>>>(p);
-    else
-        wlr_sparse_kernel<false><<<grid, kTilePix, 0, s>>>(p);
+    sparse_kernel(mixed, lanes)<<<grid, kTilePix, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,10 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # keep autotuning choices of the tests out of the user's cache
+    if "ESIM_AD_CACHE" not in os.environ:
+        import tempfile
+        os.environ["ESIM_AD_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="esim_ad_tests_"), "autotune.txt")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
 
