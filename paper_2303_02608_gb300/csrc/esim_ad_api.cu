@@ -64,15 +64,9 @@ struct esim_ad_ctx {
     int nbuf = 2;
     int wlr_grid = 0;
     int sparse_grid = 0;
+    int sparse_stage = 1;        // sparse kernel stages window boxes (ESIM_AD_SPARSE_STAGE=0: L1 only)
     bool mixed = false;
     uint32_t sparse_max = 0;     // adaptive frames with at most this many flagged pixels use the sparse kernel
-    int sparse_lanes = 16;       // lanes per pixel of the sparse kernel (8 or 16)
-    // autotuning of sparse_lanes: candidates timed on the first sparse adaptive frames
-    bool lanes_tuned = false;
-    int tune_stage = 0;
-    double tune_cost[2] = {0.0, 0.0};
-    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
-    char tune_key[96] = {0};
     float4* ring = nullptr;
     float4* state = nullptr;
     float* alpha = nullptr;
@@ -153,8 +147,6 @@ void release(esim_ad_ctx* c)
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     c->prof_events.clear();
-    for (cudaEvent_t e : c->tune_ev)
-        if (e) cudaEventDestroy(e);
 }
 
 // Bracket one launch with a pair of pooled events when profiling is on.
@@ -282,7 +274,7 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         {(void**)&c->tile_queue, (size_t)c->n_tiles * sizeof(uint32_t)},
         {(void**)&c->tile_nflag, (size_t)c->n_tiles * sizeof(int32_t)},
         {(void**)&c->tile_pix, (size_t)c->n_tiles * kTilePix},
-        {(void**)&c->flag_list, N * sizeof(uint32_t)},
+        {(void**)&c->flag_list, (N + 4 * (size_t)c->n_tiles) * sizeof(uint32_t)},   // + tile padding
         {(void**)&c->chunk_cnt, (size_t)c->n_chunks * sizeof(uint32_t)},
         {(void**)&c->chunk_off, (size_t)c->n_chunks * sizeof(unsigned long long)},
         {(void**)&c->events, (size_t)cfg->event_capacity * sizeof(esim_ad_event)},
@@ -304,14 +296,15 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         delete c;
         return ESIM_AD_ECUDA;
     }
-    if (encode_ring_map(c) != ESIM_AD_OK || wlr_prepare(c->smem_bytes, c->mixed) != cudaSuccess) {
+    if (encode_ring_map(c) != ESIM_AD_OK || wlr_prepare(c->smem_bytes, c->mixed) != cudaSuccess ||
+        wlr_sparse_prepare(cfg->radius, c->mixed) != cudaSuccess) {
         cudaGetLastError();
         release(c);
         delete c;
         return ESIM_AD_ECUDA;
     }
     c->wlr_grid = wlr_grid(c->smem_bytes, num_sms, c->mixed);
-    c->sparse_grid = wlr_sparse_grid(num_sms, c->mixed);
+    c->sparse_grid = wlr_sparse_grid(num_sms, c->mixed, cfg->radius);
     // default: frames with up to 1/8 of the pixels flagged take the sparse kernel
     // (measured faster than tile staging at the 1-2% densities of edge-like
     // flag patterns); ESIM_AD_SPARSE_MAX overrides it (0: always the tile-staged
@@ -320,23 +313,9 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     if (const char* e = getenv("ESIM_AD_SPARSE_MAX")) {
         if (*e) c->sparse_max = (uint32_t)strtoul(e, nullptr, 10);
     }
-    snprintf(c->tune_key, sizeof(c->tune_key), "sparse r=%d T=%d precision=%d sms=%d", cfg->radius,
-             cfg->frames, cfg->precision, num_sms);
-    if (const char* e = getenv("ESIM_AD_SPARSE_LANES")) {
-        const int v = atoi(e);
-        if (v == 8 || v == 16) {
-            c->sparse_lanes = v;
-            c->lanes_tuned = true;
-        }
+    if (const char* e = getenv("ESIM_AD_SPARSE_STAGE")) {
+        if (*e == '0') c->sparse_stage = 0;
     }
-    if (!c->lanes_tuned) {
-        const int v = tune_cache_lookup(c->tune_key);
-        if (v == 8 || v == 16) {
-            c->sparse_lanes = v;
-            c->lanes_tuned = true;
-        }
-    }
-    if (cfg->mode != ESIM_AD_ADAPTIVE) c->lanes_tuned = true;   // the sparse kernel never runs
     *out = c;
     return ESIM_AD_OK;
 }
@@ -497,6 +476,7 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     wp.emit_events = c->t > 0 ? 1 : 0;
     wp.sparse_max = c->sparse_max;
     wp.flag_list = c->flag_list;
+    wp.sparse_stage = c->sparse_stage;
     wp.ctrl = c->ctrl;
     {
         ProfScope ps(c, 1);
@@ -505,34 +485,8 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
             return ESIM_AD_ECUDA;
         // adaptive frames: the sparse kernel takes the frame when few pixels are
         // flagged; each of the two launches returns at once on the other's frames
-        const bool tuning = !wp.dense && !c->lanes_tuned;
-        const int lanes = tuning ? (c->tune_stage == 0 ? 16 : 8) : c->sparse_lanes;
-        if (tuning && !c->tune_ev[0]) {
-            if (cudaEventCreate(&c->tune_ev[0]) != cudaSuccess || cudaEventCreate(&c->tune_ev[1]) != cudaSuccess)
-                return ESIM_AD_ECUDA;
-        }
-        if (tuning) cudaEventRecord(c->tune_ev[0], c->stream);
-        if (!wp.dense && launch_wlr_sparse(wp, c->mixed, lanes, c->sparse_grid, c->stream) != cudaSuccess)
+        if (!wp.dense && launch_wlr_sparse(wp, c->mixed, c->sparse_grid, c->stream) != cudaSuccess)
             return ESIM_AD_ECUDA;
-        if (tuning) {
-            // time this candidate per regression; frames that went to the
-            // tile-staged kernel (too many flags) do not count
-            cudaEventRecord(c->tune_ev[1], c->stream);
-            Ctrl h;
-            if (cudaMemcpyAsync(&h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-                cudaStreamSynchronize(c->stream) != cudaSuccess)
-                return ESIM_AD_ECUDA;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]);
-            if (h.flag_total > 0 && h.flag_total <= c->sparse_max) {
-                c->tune_cost[c->tune_stage] = (double)ms / (double)h.flag_total;
-                if (++c->tune_stage == 2) {
-                    c->sparse_lanes = c->tune_cost[1] < c->tune_cost[0] ? 8 : 16;
-                    c->lanes_tuned = true;
-                    tune_cache_store(c->tune_key, c->sparse_lanes);
-                }
-            }
-        }
         c->prof_kernels += wp.dense ? 1 : 2;
     }
 

@@ -11,7 +11,8 @@
 // seven feature slopes enter.  Flagged pixels of the CTA's 32x8 tile are
 // compacted in raster order with warp ballots and a block prefix; the tile is
 // appended to the active-tile queue, and its pixels to a frame-wide flagged
-// list, with one atomic each per tile.
+// list (the tile's run padded to a multiple of four entries, so that groups of
+// four aligned entries never straddle two tiles), with one atomic each per tile.
 //
 // Memory traffic per pixel (fp32 RGB input): 40 B in (radiance 12, normal 12,
 // albedo 12, depth 4; variance is not read), 32 B ring write, 32 B model read
@@ -54,10 +55,13 @@ __global__ void __launch_bounds__(kTilePix) ingest_test_kernel(IngestParams p)
         if (total > 0) {
             const uint32_t slot = atomicAdd(&p.ctrl->tile_count, 1u);
             p.tile_queue[slot] = (uint32_t)tile;
-            s_list_base = atomicAdd(&p.ctrl->flag_total, (uint32_t)total);
+            atomicAdd(&p.ctrl->flag_total, (uint32_t)total);
+            s_list_base = atomicAdd(&p.ctrl->list_len, (uint32_t)((total + 3) & ~3));
         }
     }
     __syncthreads();
+    if (total > 0 && (int)threadIdx.x < ((-total) & 3))
+        p.flag_list[s_list_base + total + threadIdx.x] = 0xffffffffu;
     if (flag) {
         const int pos = base + __popc(ballot & ((1u << lx) - 1u));
         p.tile_pix[(size_t)tile * kTilePix + pos] = (uint8_t)threadIdx.x;

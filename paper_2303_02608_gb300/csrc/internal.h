@@ -32,6 +32,8 @@ struct Ctrl {
     uint32_t chunk_done;            // ticket of the event-count kernel
     uint32_t work_next;             // next work item of the persistent regression
     uint32_t flag_total;            // pixels flagged by the test kernel this frame
+    uint32_t list_len;              // flagged-list length: each tile's run padded to a multiple of 4
+    uint32_t pad0;
     unsigned long long ev_total;    // events produced since the last drain
     unsigned long long ev_cum;      // events since init/reset
     unsigned long long regressions; // pixels regressed since init/reset
@@ -40,7 +42,7 @@ struct Ctrl {
     uint32_t status;                // sticky kStatus* bits
     uint32_t pad2;
 };
-constexpr size_t kCtrlPerFrameBytes = 16;
+constexpr size_t kCtrlPerFrameBytes = 24;
 
 // Ring of the last T frames.  FP32 form: float4 planes [2T][H][W]; plane
 // 2*slot holds (y, normal xyz), plane 2*slot+1 holds (depth, albedo rgb).
@@ -113,7 +115,8 @@ struct IngestParams {
     uint8_t* tile_pix;
     uint32_t* chunk_cnt;   // per event chunk, cleared here for the regression's counts
     int n_chunks;
-    uint32_t* flag_list;   // frame-wide list of flagged pixel indices (tile order)
+    uint32_t* flag_list;   // frame-wide list of flagged pixel indices: each tile's run, in raster
+                           // order, padded with 0xffffffff to a multiple of 4 entries
     Ctrl* ctrl;
 };
 
@@ -143,7 +146,8 @@ struct WlrParams {
     int n_chunks;
     int emit_events;                 // 0 on frame 0 (no events)
     uint32_t sparse_max;             // queue mode: at most this many flagged pixels -> sparse kernel
-    const uint32_t* flag_list;       // flagged pixel indices, flag_total of them
+    const uint32_t* flag_list;       // flagged pixel indices per tile, each run padded to 4 entries
+    int sparse_stage;                // sparse kernel: 1 stage window boxes in shared memory, 0 read via L1
     Ctrl* ctrl;
 };
 
@@ -168,10 +172,12 @@ void tune_cache_store(const char* key, int value);
 cudaError_t wlr_prepare(int smem_bytes, bool mixed);
 size_t wlr_smem_bytes(int r, bool mixed, int max_smem_per_sm, int* nbuf);
 int wlr_grid(int smem_bytes, int num_sms, bool mixed);
-int wlr_sparse_grid(int num_sms, bool mixed);
+int wlr_sparse_smem(int r, bool mixed);
+cudaError_t wlr_sparse_prepare(int r, bool mixed);
+int wlr_sparse_grid(int num_sms, bool mixed, int r);
 cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, bool mixed, int grid,
                        int smem_bytes, cudaStream_t s);
-cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int lanes, int grid, cudaStream_t s);
+cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s);
 cudaError_t launch_events(const EventParams& p, cudaStream_t s);
 cudaError_t launch_event_write(const EventParams& p, cudaStream_t s);
 

@@ -346,22 +346,59 @@ __global__ void __launch_bounds__(kTilePix, 2)
 
 // Sparse-frame regression.  When few pixels are flagged they lie on thin
 // feature edges, a handful per tile, and staging a whole tile window per work
-// item would move far more data than it feeds.  This kernel instead reads each
-// neighbour's two float4 half-planes straight from the ring through L1 (it
-// reserves almost no shared memory, so L1 keeps the overlapping windows of
-// nearby pixels).  A CTA takes the next 16 entries of the frame's flagged-pixel
-// list (neighbours within one tile, so its warps' windows overlap in L1); each
-// warp owns two of them, 16 lanes per pixel split its window, and the lanes
-// are shuffle-reduced.  Interior pixels all cost the same, so the per-block
-// barrier waits little.
-template <bool kMixed, int kLanes>
+// item would move far more data than it feeds.  Here each warp takes four
+// consecutive entries of the frame's flagged list (the test kernel pads every
+// tile's run to a multiple of four, so the four pixels share a tile and are
+// usually adjacent along an edge), 8 lanes per pixel (16 or 32 when the item
+// holds only two or one pixel, the tail of a tile's run).  For each frame of the
+// temporal window the warp copies the bounding box of its pixels' windows
+// from the ring into its own shared-memory buffer with 16-byte asynchronous
+// copies (and hints the next frame's box into L2), then the lanes split each
+// window's offsets and accumulate from shared memory; boxes too large for the
+// buffer are read through L1 instead.  Warps fetch work independently; there
+// is no block barrier inside the loop.
+template <bool kMixed>
+struct SparseStage;
+template <>
+struct SparseStage<true> {   // one 16-byte record per pixel
+    static constexpr int pitch = 32, rows = 24, rec = 16;
+};
+template <>
+struct SparseStage<false> {  // two float4 half-planes per pixel
+    static constexpr int pitch = 20, rows = 19, rec = 32;
+};
+constexpr int kSparsePerWarp = 4;                  // list entries per work item (one warp)
+constexpr uint32_t kListPad = 0xffffffffu;          // padding entry of the flagged list
+
+struct SparseLayout {
+    int buf_off, buf_bytes, total;
+};
+
+// window table [(2r+1)^2] float4 (buffer offset, u_dx, u_dy, -(u_dx^2 + u_dy^2)) | 8 warp buffers
+__host__ __device__ inline SparseLayout sparse_layout(int r, bool mixed)
+{
+    const int side = 2 * r + 1, nq = side * side;
+    const int pitch = mixed ? SparseStage<true>::pitch : SparseStage<false>::pitch;
+    const int rows = mixed ? SparseStage<true>::rows : SparseStage<false>::rows;
+    const int rec = mixed ? SparseStage<true>::rec : SparseStage<false>::rec;
+    const bool stage = side <= pitch && side <= rows;
+    SparseLayout L;
+    L.buf_bytes = stage ? pitch * rows * rec : 0;
+    L.buf_off = nq * 16;
+    L.total = L.buf_off + (kTilePix / 32) * L.buf_bytes;
+    return L;
+}
+
+template <bool kMixed>
 __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams p)
 {
     if (p.sparse_max == 0 || *(volatile uint32_t*)&p.ctrl->flag_total > p.sparse_max)
         return;  // the tile-staged kernel's frame
-    constexpr int kPerWarp = 32 / kLanes;              // pixels per warp
-    constexpr int kBlock = (kTilePix / 32) * kPerWarp;  // list entries per CTA block
-    __shared__ float4 table[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];
+    using S = SparseStage<kMixed>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const SparseLayout L = sparse_layout(p.r, kMixed);
+    float4* table = reinterpret_cast<float4*>(sm);
+    const bool can_stage = L.buf_bytes > 0 && p.sparse_stage;
     __shared__ unsigned long long s_pairs, s_pix, s_fp64;
     const int side = 2 * p.r + 1, nq = side * side;
     const float spx = p.s_coord_px;
@@ -369,7 +406,7 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
         const int ox = q % side - p.r, oy = q / side - p.r;
         const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-        table[q] = make_float4(__int_as_float(oy * p.W + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
+        table[q] = make_float4(__int_as_float(oy * S::pitch + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
     }
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
@@ -377,28 +414,33 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         s_fp64 = 0ull;
     }
     __syncthreads();
-    const uint32_t n_flag = *(volatile uint32_t*)&p.ctrl->flag_total;
+    const uint32_t n_list = *(volatile uint32_t*)&p.ctrl->list_len;
     const float* sf = kMixed ? p.q_scale : p.s_feat;
     const float4* ringf = reinterpret_cast<const float4*>(p.ring);
     const uint4* ringm = reinterpret_cast<const uint4*>(p.ring);
     const int lane = threadIdx.x & 31;
-    const int sub = lane & (kLanes - 1);
-    const int grp = lane / kLanes;
     const int slot_t = p.t % p.T;
+    unsigned char* wbuf = sm + L.buf_off + (threadIdx.x >> 5) * L.buf_bytes;
+    uint4* bufm = reinterpret_cast<uint4*>(wbuf);
+    float4* buf0 = reinterpret_cast<float4*>(wbuf);
+    float4* buf1 = buf0 + S::pitch * S::rows;
     Acc acc;
     float cf[7];
-    __shared__ uint32_t s_base;
     for (;;) {
-        // the CTA takes kBlock consecutive list entries (neighbours in one tile,
-        // so the warps' windows overlap in L1); each warp owns kPerWarp of them
-        if (threadIdx.x == 0) s_base = atomicAdd(&p.ctrl->work_next, (uint32_t)kBlock);
-        __syncthreads();
-        const uint32_t blk = s_base;
-        __syncthreads();   // all have read the block before thread 0 takes the next
-        if (blk >= n_flag) break;
-        const uint32_t my = blk + (uint32_t)((threadIdx.x >> 5) * kPerWarp + grp);
-        const bool active = my < n_flag;
-        const uint32_t pix = active ? p.flag_list[my] : 0u;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctrl->work_next, (uint32_t)kSparsePerWarp);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_list) break;
+        // the item's m real entries come first (padding closes a tile's run);
+        // 8 lanes per pixel for m = 3, 4, 16 for m = 2, 32 for m = 1
+        const uint32_t e4 = p.flag_list[base + (lane & 3)];   // n_list is a multiple of 4
+        const int m = __popc(__ballot_sync(0xffffffffu, e4 != kListPad) & 0xfu);
+        const int lg = m >= 3 ? 3 : 6 - m;
+        const int g = 1 << lg;
+        const int grp = lane >> lg, sub = lane & (g - 1);
+        const uint32_t entry = __shfl_sync(0xffffffffu, e4, grp);
+        const bool active = grp < m;
+        const uint32_t pix = active ? entry : 0u;
         const int cx = (int)(pix % (uint32_t)p.W), cy = (int)(pix / (uint32_t)p.W);
 #pragma unroll
         for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
@@ -407,6 +449,13 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
         const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
         const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
+        // bounding box of the warp's windows (clipped to the image)
+        const int bx0 = __reduce_min_sync(0xffffffffu, active ? cx + dxlo : 0x7fffffff);
+        const int by0 = __reduce_min_sync(0xffffffffu, active ? cy + dylo : 0x7fffffff);
+        const int bx1 = __reduce_max_sync(0xffffffffu, active ? cx + dxhi : -1);
+        const int by1 = __reduce_max_sync(0xffffffffu, active ? cy + dyhi : -1);
+        const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
+        const bool staged = can_stage && bw > 0 && bw <= S::pitch && bh <= S::rows;   // warp-uniform
         if (active) {
             float c[7];
             if (kMixed) {
@@ -419,8 +468,73 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
             }
 #pragma unroll
             for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
-            for (int k = 0; k < p.n_tau; ++k) {
-                const int slot = (p.t - k) % p.T;
+        }
+        const bool interior = nx == side && ny == side;
+        for (int k = 0; k < p.n_tau; ++k) {
+            const int slot = (p.t - k) % p.T;
+            if (staged) {
+                // box of this frame -> the warp's buffer (bw <= 32: one record per lane per row)
+                __syncwarp();   // every lane is done with the previous frame's box
+                const size_t row0 = (size_t)by0 * p.W + bx0 + lane;
+                if (lane < bw) {
+                    for (int i = 0; i < bh; ++i) {
+                        const size_t g = row0 + (size_t)i * p.W;
+                        if (kMixed) {
+                            cp_async16(bufm + i * S::pitch + lane, ringm + (size_t)slot * N + g);
+                        } else {
+                            cp_async16(buf0 + i * S::pitch + lane, ringf + (size_t)(2 * slot) * N + g);
+                            cp_async16(buf1 + i * S::pitch + lane, ringf + (size_t)(2 * slot + 1) * N + g);
+                        }
+                    }
+                }
+                if (k + 1 < p.n_tau) {
+                    // hint the next frame's box into L2 while this one lands and is summed
+                    const int nslot = (p.t - k - 1) % p.T;
+                    const int lines = (bw * S::rec + 127) >> 7;
+                    for (int j = lane; j < bh * lines; j += 32) {
+                        const int i = j / lines, l = j - i * lines;
+                        const size_t g = (size_t)(by0 + i) * p.W + bx0;
+                        const char* row = kMixed
+                            ? reinterpret_cast<const char*>(ringm + (size_t)nslot * N + g)
+                            : reinterpret_cast<const char*>(ringf + (size_t)(2 * nslot) * N + g);
+                        prefetch_l2(row + l * 128);
+                        if (!kMixed) prefetch_l2(row + (size_t)N * 16 + l * 128);
+                    }
+                }
+                cp_async_wait_all();
+                __syncwarp();   // the box is visible to every lane of the warp
+                if (active) {
+                    const int cb = (cy - by0) * S::pitch + (cx - bx0);
+                    auto at = [&](int si, float u1, float u2, float en0) {
+                        if (kMixed)
+                            accumulate(acc, bufm[si], u1, u2, en0, sf, cf);
+                        else
+                            accumulate(acc, buf0[si], buf1[si], u1, u2, en0, sf, cf);
+                    };
+                    if (interior) {
+#pragma unroll 2
+                        for (int q = sub; q < nq; q += g) {
+                            const float4 e = table[q];
+                            at(cb + __float_as_int(e.x), e.y, e.z, e.w);
+                        }
+                    } else {
+                        const int nvalid = nx * ny;
+                        int ox = dxlo + sub % nx;
+                        int oy = dylo + sub / nx;
+#pragma unroll 1
+                        for (int q = sub; q < nvalid; q += g) {
+                            const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+                            at(cb + oy * S::pitch + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
+                            ox += g;
+                            while (ox > dxhi) {
+                                ox -= nx;
+                                ++oy;
+                            }
+                        }
+                    }
+                }
+            } else if (active) {
+                // box too large for the buffer: read the windows through L1
                 const float4* __restrict__ R0 = ringf + (size_t)(2 * slot) * N + pix;
                 const float4* __restrict__ R1 = ringf + (size_t)(2 * slot + 1) * N + pix;
                 const uint4* __restrict__ RM = ringm + (size_t)slot * N + pix;
@@ -430,48 +544,24 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
                     else
                         accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, en0, sf, cf);
                 };
-                if (nx == side && ny == side) {
-                    if (k + 1 < p.n_tau && sub < side) {
-                        // pull the next frame's window rows towards L1 while this one is summed
-                        const int nslot = (p.t - k - 1) % p.T;
-                        const size_t off = (size_t)pix + (size_t)((sub - p.r) * p.W - p.r);
-                        if (kMixed) {
-                            const uint4* row = ringm + (size_t)nslot * N + off;
-                            for (int c2 = 0; c2 < side; c2 += 8) prefetch_l1(row + c2);
-                            prefetch_l1(row + side - 1);
-                        } else {
-                            const float4* row = ringf + (size_t)(2 * nslot) * N + off;
-                            for (int c2 = 0; c2 < side; c2 += 8) {
-                                prefetch_l1(row + c2);
-                                prefetch_l1(row + N + c2);
-                            }
-                            prefetch_l1(row + side - 1);
-                            prefetch_l1(row + N + side - 1);
-                        }
-                    }
-#pragma unroll 2
-                    for (int q = sub; q < nq; q += kLanes) {
-                        const float4 e = table[q];
-                        at(__float_as_int(e.x), e.y, e.z, e.w);
-                    }
-                } else {
-                    const int nvalid = nx * ny;
-                    int ox = dxlo + sub % nx;
-                    int oy = dylo + sub / nx;
-                    for (int q = sub; q < nvalid; q += kLanes) {
-                        const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-                        at(oy * p.W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
-                        ox += kLanes;
-                        while (ox > dxhi) {
-                            ox -= nx;
-                            ++oy;
-                        }
+                // (rare: the window walked offset by offset, clipped or not)
+                const int nvalid = nx * ny;
+                int ox = dxlo + sub % nx;
+                int oy = dylo + sub / nx;
+#pragma unroll 1
+                for (int q = sub; q < nvalid; q += g) {
+                    const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+                    at(oy * p.W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
+                    ox += g;
+                    while (ox > dxhi) {
+                        ox -= nx;
+                        ++oy;
                     }
                 }
             }
         }
 #pragma unroll
-        for (int off = kLanes >> 1; off >= 1; off >>= 1) {
+        for (int off = g >> 1; off >= 1; off >>= 1) {
 #pragma unroll
             for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
 #pragma unroll
@@ -480,36 +570,43 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         if (active && sub == 0) {
             atomicAdd(&s_pairs, (unsigned long long)(nx * ny * p.n_tau));
             atomicAdd(&s_pix, 1ull);
-            solve_and_emit<kMixed>(p, acc, cx, cy, &s_fp64);
+            solve_and_emit<kMixed, true>(p, acc, cx, cy, &s_fp64);
         }
     }
     __syncthreads();
     finish(p, s_pairs, s_pix, s_fp64, false);
 }
 
-typedef void (*SparseKernel)(const WlrParams);
+int wlr_sparse_smem(int r, bool mixed) { return sparse_layout(r, mixed).total; }
 
-SparseKernel sparse_kernel(bool mixed, int lanes)
+cudaError_t wlr_sparse_prepare(int r, bool mixed)
 {
-    if (mixed) return lanes == 8 ? wlr_sparse_kernel<true, 8> : wlr_sparse_kernel<true, 16>;
-    return lanes == 8 ? wlr_sparse_kernel<false, 8> : wlr_sparse_kernel<false, 16>;
+    const int bytes = wlr_sparse_smem(r, mixed);
+    return mixed ? cudaFuncSetAttribute(wlr_sparse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                 : cudaFuncSetAttribute(wlr_sparse_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-int wlr_sparse_grid(int num_sms, bool mixed)
+int wlr_sparse_grid(int num_sms, bool mixed, int r)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel(mixed, 16), kTilePix, 0) !=
-            cudaSuccess ||
-        per_sm < 1) {
+    const int bytes = wlr_sparse_smem(r, mixed);
+    const cudaError_t e = mixed
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel<true>, kTilePix, bytes)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wlr_sparse_kernel<false>, kTilePix, bytes);
+    if (e != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
     return per_sm * num_sms;
 }
 
-cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int lanes, int grid, cudaStream_t s)
+cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s)
 {
-    sparse_kernel(mixed, lanes)<<<grid, kTilePix, 0, s>>>(p);
+    const int bytes = wlr_sparse_smem(p.r, mixed);
+    if (mixed)
+        wlr_sparse_kernel<true><<<grid, kTilePix, bytes, s>>>(p);
+    else
+        wlr_sparse_kernel<false><<<grid, kTilePix, bytes, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -132,12 +132,45 @@ __device__ __forceinline__ void solve(Acc& a, const float (&s2)[NZ], float ridge
     for (int i = 0; i < NZ; ++i) theta[i] *= dsc[i];
 }
 
+// FP64 Cholesky re-solve of the equilibrated FP32 system (rarely taken; kept
+// out of line so that its arrays do not burden the callers' registers).
+__device__ __noinline__ void solve_fp64(const float (&A)[NG], const float (&b)[NZ], float (&th)[NZ])
+{
+    double L[NG];
+    double dinv[NZ];
+    for (int j = 0; j < NZ; ++j) {
+        double sj = (double)A[tri(j, j)];
+        for (int k = 0; k < j; ++k) sj -= L[tri(j, k)] * L[tri(j, k)];
+        sj = sj > 1e-300 ? sj : 1e-300;
+        const double l = sqrt(sj);
+        L[tri(j, j)] = l;
+        dinv[j] = 1.0 / l;
+        for (int i = j + 1; i < NZ; ++i) {
+            double v = (double)A[tri(i, j)];
+            for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
+            L[tri(i, j)] = v * dinv[j];
+        }
+    }
+    double z[NZ], x[NZ];
+    for (int i = 0; i < NZ; ++i) {
+        double v = (double)b[i];
+        for (int k = 0; k < i; ++k) v -= L[tri(i, k)] * z[k];
+        z[i] = v * dinv[i];
+    }
+    for (int i = NZ - 1; i >= 0; --i) {
+        double v = z[i];
+        for (int k = i + 1; k < NZ; ++k) v -= L[tri(k, i)] * x[k];
+        x[i] = v * dinv[i];
+    }
+    for (int i = 0; i < NZ; ++i) th[i] = (float)x[i];
+}
+
 // Mixed-form solve: FP32 Cholesky of the equilibrated system plus one step of
 // iterative refinement (the residual taken against the unfactored matrix),
 // and an FP64 Cholesky re-solve when the condition number estimated from the
 // factor's diagonal, (max L_ii / min L_ii)^2, exceeds 1e6.  Returns 1 if the
 // FP64 path ran.
-__device__ __noinline__ int solve_mixed(Acc& a, const float (&s2)[NZ], float ridge,
+__device__ __forceinline__ int solve_mixed_inl(Acc& a, const float (&s2)[NZ], float ridge,
                                         float (&theta)[NZ])
 {
     const float W = a.G[0];
@@ -210,34 +243,7 @@ __device__ __noinline__ int solve_mixed(Acc& a, const float (&s2)[NZ], float rid
     int used64 = 0;
     const float ratio = lmax / lmin;
     if (ratio * ratio > 1e6f) {
-        // FP64 Cholesky of the same equilibrated FP32 system
-        double L[NG];
-        double dinv[NZ];
-        for (int j = 0; j < NZ; ++j) {
-            double sj = (double)A[tri(j, j)];
-            for (int k = 0; k < j; ++k) sj -= L[tri(j, k)] * L[tri(j, k)];
-            sj = sj > 1e-300 ? sj : 1e-300;
-            const double l = sqrt(sj);
-            L[tri(j, j)] = l;
-            dinv[j] = 1.0 / l;
-            for (int i = j + 1; i < NZ; ++i) {
-                double v = (double)A[tri(i, j)];
-                for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
-                L[tri(i, j)] = v * dinv[j];
-            }
-        }
-        double z[NZ], x[NZ];
-        for (int i = 0; i < NZ; ++i) {
-            double v = (double)b[i];
-            for (int k = 0; k < i; ++k) v -= L[tri(i, k)] * z[k];
-            z[i] = v * dinv[i];
-        }
-        for (int i = NZ - 1; i >= 0; --i) {
-            double v = z[i];
-            for (int k = i + 1; k < NZ; ++k) v -= L[tri(k, i)] * x[k];
-            x[i] = v * dinv[i];
-        }
-        for (int i = 0; i < NZ; ++i) th[i] = (float)x[i];
+        solve_fp64(A, b, th);
         used64 = 1;
     }
 #pragma unroll
@@ -245,6 +251,13 @@ __device__ __noinline__ int solve_mixed(Acc& a, const float (&s2)[NZ], float rid
     return used64;
 }
 
+
+// Out-of-line copy for callers whose accumulation loop already holds the
+// register budget (the solve then runs on the call's own frame).
+__device__ __noinline__ int solve_mixed_call(Acc& a, const float (&s2)[NZ], float ridge, float (&theta)[NZ])
+{
+    return solve_mixed_inl(a, s2, ridge, theta);
+}
 
 // Eq. 1 at a fixed frame time, and the model update of Fig. 1.
 template <bool kMixed>
@@ -292,8 +305,9 @@ __device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const f
     p.state[3 * N + i] = make_float4(x[4], x[5], x[6], L);
 }
 
-// Regress one pixel from its reduced sums, then emit (both forms).
-template <bool kMixed>
+// Regress one pixel from its reduced sums, then emit (both forms).  kInline:
+// the mixed-form solve is inlined rather than called.
+template <bool kMixed, bool kInline = false>
 __device__ __forceinline__ void solve_and_emit(const WlrParams& p, Acc& acc, int cx, int cy,
                                                unsigned long long* fp64_count)
 {
@@ -305,7 +319,9 @@ __device__ __forceinline__ void solve_and_emit(const WlrParams& p, Acc& acc, int
     for (int j = 0; j < 7; ++j) s2[3 + j] = p.s_feat[j] * p.s_feat[j];
     float theta[NZ];
     if (kMixed) {
-        if (solve_mixed(acc, s2, p.ridge, theta)) atomicAdd(fp64_count, 1ull);
+        const int used64 = kInline ? solve_mixed_inl(acc, s2, p.ridge, theta)
+                                   : solve_mixed_call(acc, s2, p.ridge, theta);
+        if (used64) atomicAdd(fp64_count, 1ull);
     } else {
         solve(acc, s2, p.ridge, theta);
     }

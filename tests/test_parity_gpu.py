@@ -17,17 +17,17 @@ pytestmark = pytest.mark.gpu
 
 
 # which regression kernel serves adaptive frames: the library's choice, the
-# tile-staged kernel always, or the sparse (L1 window) kernel always with 16 or
-# 8 lanes per pixel: (sparse threshold, sparse lanes per pixel); None = the
-# library's default (for the lanes: autotuned on the first sparse frames)
-PATHS = {"auto": (None, None), "staged": ("0", None), "sparse": ("4294967295", "16"),
-         "sparse8": ("4294967295", "8"), "sparse_tuned": ("4294967295", None)}
+# tile-staged kernel always, or the sparse kernel always, with its window boxes
+# staged in shared memory (where they fit) or read through L1 only:
+# (sparse threshold, sparse staging); None = the library's default
+PATHS = {"auto": (None, None), "staged": ("0", None), "sparse": ("4294967295", None),
+         "sparse_l1": ("4294967295", "0")}
 
 
 def _sim(W, H, r, T, C, mode, rgb, capacity=1 << 22, path="auto"):
     import os
     from paper_2303_02608_gb300 import SimConfig, Simulator
-    keys = ("ESIM_AD_SPARSE_MAX", "ESIM_AD_SPARSE_LANES")
+    keys = ("ESIM_AD_SPARSE_MAX", "ESIM_AD_SPARSE_STAGE")
     old = {k: os.environ.pop(k, None) for k in keys}
     for k, v in zip(keys, PATHS[path]):
         if v is not None:
@@ -57,7 +57,7 @@ def _case(scene_cfg, r, T, C, mode, n_frames, rows=None, strict=True, path="auto
     return rep
 
 
-@pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse"), (ADAPTIVE, "sparse8"),
+@pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse"), (ADAPTIVE, "sparse_l1"),
                                        (EXHAUSTIVE, "auto")])
 @pytest.mark.parametrize("strict", [True, False])
 def test_disc_64(mode, path, strict):
@@ -68,7 +68,7 @@ def test_disc_64(mode, path, strict):
     assert rep["flag_ambiguous"] + rep["event_ambiguous"] < 0.001 * total + 2
 
 
-@pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse"), (ADAPTIVE, "sparse8"),
+@pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse"), (ADAPTIVE, "sparse_l1"),
                                        (EXHAUSTIVE, "auto")])
 def test_ragged_rects(mode, path):
     """77x45 RGB rectangles (ragged tiles both ways), 5x5x2 window."""
@@ -121,18 +121,3 @@ def test_1080p_band():
     """1920x1080, 1 spp-equivalent noise, 15x15x5, C = 0.1 (adaptive); band of rows."""
     rep = _case(preset("rects1080p"), 7, 5, 0.1, ADAPTIVE, 6, rows=(536, 544))
     assert rep["regressed"] > 0
-
-
-def test_sparse_lanes_autotuner_caches(tmp_path, monkeypatch):
-    """A context without a forced lane count times 16 and 8 lanes per pixel on
-    its first two sparse frames, keeps the faster (results stay exact either
-    way) and stores the choice under its configuration."""
-    cache = tmp_path / "autotune.txt"
-    monkeypatch.setenv("ESIM_AD_CACHE", str(cache))
-    cfg = SceneConfig(kind="rects", width=77, height=45, frames=6, spp=4, seed=3, rgb=True,
-                      n_rects=6, bg_depth=10.0)
-    rep = _case(cfg, 2, 2, 0.15, ADAPTIVE, cfg.frames, path="sparse_tuned")
-    assert rep["regressed"] > 0
-    lines = [ln.split() for ln in cache.read_text().splitlines() if ln.startswith("sparse r=2 T=2")]
-    assert len(lines) == 1 and lines[0][-1] in ("8", "16")
-
