@@ -33,7 +33,7 @@ struct Ctrl {
     uint32_t work_next;             // next work item of the persistent regression
     uint32_t flag_total;            // pixels flagged by the test kernel this frame
     uint32_t list_len;              // flagged-list length: each tile's run padded to a multiple of 4
-    uint32_t pad0;
+    uint32_t tail_next;             // sparse regression: next single entry of the list's tail
     unsigned long long ev_total;    // events produced since the last drain
     unsigned long long ev_cum;      // events since init/reset
     unsigned long long regressions; // pixels regressed since init/reset

@@ -415,6 +415,8 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
     }
     __syncthreads();
     const uint32_t n_list = *(volatile uint32_t*)&p.ctrl->list_len;
+    const uint32_t tail_len = 2u * gridDim.x * (kTilePix / 32);
+    const uint32_t tail0 = n_list > tail_len ? (n_list - tail_len) & ~3u : 0u;   // multiple of 4
     const float* sf = kMixed ? p.q_scale : p.s_feat;
     const float4* ringf = reinterpret_cast<const float4*>(p.ring);
     const uint4* ringm = reinterpret_cast<const uint4*>(p.ring);
@@ -427,14 +429,25 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
     Acc acc;
     float cf[7];
     for (;;) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&p.ctrl->work_next, (uint32_t)kSparsePerWarp);
+        // Four-entry items until the last stretch of the list; that stretch
+        // (half an item per warp of the grid) goes out one pixel at a time, so
+        // the warps run out of work together instead of one item apart.
+        uint32_t base = 0, single = 0;
+        if (lane == 0) {
+            base = atomicAdd(&p.ctrl->work_next, (uint32_t)kSparsePerWarp);
+            if (base >= tail0) {
+                base = tail0 + atomicAdd(&p.ctrl->tail_next, 1u);
+                single = 1;
+            }
+        }
         base = __shfl_sync(0xffffffffu, base, 0);
+        single = __shfl_sync(0xffffffffu, single, 0);
         if (base >= n_list) break;
-        // the item's m real entries come first (padding closes a tile's run);
+        const uint32_t e4 = (single && (lane & 3)) ? kListPad : p.flag_list[base + (single ? 0 : (lane & 3))];
+        // an item's m real entries come first (padding closes a tile's run);
         // 8 lanes per pixel for m = 3, 4, 16 for m = 2, 32 for m = 1
-        const uint32_t e4 = p.flag_list[base + (lane & 3)];   // n_list is a multiple of 4
         const int m = __popc(__ballot_sync(0xffffffffu, e4 != kListPad) & 0xfu);
+        if (m == 0) continue;   // a padding entry of the tail
         const int lg = m >= 3 ? 3 : 6 - m;
         const int g = 1 << lg;
         const int grp = lane >> lg, sub = lane & (g - 1);
