@@ -129,6 +129,31 @@ def _dist():
     return rank, ws, dist if ws > 1 else None
 
 
+def rank_scene(name: str, rank: int):
+    """Each rank simulates its own independent sequence: the preset's scene
+    with sequence id and seed equal to the rank (weak scaling, no data-path
+    exchange between ranks)."""
+    from scenes import preset
+    return preset(name, seq=rank, seed=rank)
+
+
+def max_over_ranks(values: list, dist, device) -> list:
+    """Element-wise maximum of per-rank timings over all ranks (the whole job
+    is as slow as its slowest rank); identity on one rank."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(world_size: int, pixels: int, steps: int, ms: float) -> float:
+    """Pixel-frames/s of the whole job: every rank pushed `steps` frames of
+    `pixels` pixels within `ms` (the maximum over ranks)."""
+    return world_size * pixels * steps / (ms * 1e-3)
+
+
 def _gen_frames(scene, n, device):
     frames = []
     for t in range(n):
@@ -238,14 +263,14 @@ def run_ours(args):
     import torch
     import paper_2303_02608_gb300 as lib
     from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, ESIM_AD_EXHAUSTIVE, SimConfig, Simulator
-    from scenes import Scene, preset
+    from scenes import Scene
 
     rank, ws, dist = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
-    scfg = preset(wl["scene"], seq=rank, seed=rank)
+    scfg = rank_scene(wl["scene"], rank)
     scene = Scene(scfg)
     Wd, H = scfg.width, scfg.height
     N = Wd * H
@@ -285,15 +310,13 @@ def run_ours(args):
             runs[name] = (ms, prof, ev)
     clocks = clk.summary()
 
-    if dist:
-        t = torch.tensor([runs[k][0] for k in runs], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        for i, k in enumerate(list(runs)):
-            runs[k] = (float(t[i]),) + runs[k][1:]
+    slowest = max_over_ranks([runs[k][0] for k in runs], dist, dev)
+    for i, k in enumerate(list(runs)):
+        runs[k] = (slowest[i],) + runs[k][1:]
     K = args.steps
 
     def rate(name):
-        return ws * N * K / (runs[name][0] * 1e-3)
+        return whole_job_rate(ws, N, K, runs[name][0])
 
     ms_a, prof_a, ev_a = runs["mixed_adaptive"]
     value = rate("mixed_adaptive")
