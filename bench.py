@@ -50,7 +50,9 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regression
 # kernel from one ncu capture, valid only while wlr.cu is unchanged (the
 # capture's workload and scaling are recorded under profiles/).
-NCU_TRAFFIC = {}   # {sha256(wlr.cu)[:16]: bytes per launch at the bench workload}
+# {sha256(wlr.cu)[:16]: bytes per launch at the bench workload}; captured on
+# the sparse launch of frame 3 (same 1080p workload, unscaled)
+NCU_TRAFFIC = {"1a9b7271f993bfeb": 67868928 + 25148416}
 
 
 def _peaks():
