@@ -414,6 +414,7 @@ class Simulator:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = esim_ad_init(cfg.c_config(), self.stream.cuda_stream)
         self._keep = []
+        self._ev_host = None   # pinned landing buffer of events(), grown on demand
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -433,18 +434,25 @@ class Simulator:
         ptr = {k: v.data_ptr() for k, v in zip(keys, planes)}
         esim_ad_push_frame(self.ctx, ptr["radiance"], ptr.get("normal", 0), ptr.get("albedo", 0),
                            ptr.get("depth", 0), on_host=on_host, features=ptr.get("features", 0))
-        if not on_host:
-            # inputs are read in stream order; keep them alive until the next sync point
-            self._keep.append(planes)
+        # inputs (device planes, or pinned host planes copied asynchronously) are
+        # read in stream order; keep them alive until the next sync point
+        self._keep.append(planes)
 
     def events(self) -> np.ndarray:
-        st, n = esim_ad_events(self.ctx, 0, 0)
-        if st not in (ESIM_AD_OK, ESIM_AD_ENOSPACE):
-            raise EsimError(st, "esim_ad_events")
+        """Drain the events produced so far (one synchronising call when they
+        fit the pinned landing buffer, which grows to the largest drain)."""
+        t = self._torch
+        buf = self._ev_host
+        cap = 0 if buf is None else buf.numel() // EVENT_DTYPE.itemsize
+        st, n = esim_ad_events(self.ctx, buf.data_ptr() if cap else 0, cap)
+        if st == ESIM_AD_ENOSPACE:
+            cap = max(n, 2 * cap, 1 << 16)
+            self._ev_host = buf = t.empty(cap * EVENT_DTYPE.itemsize, dtype=t.uint8, pin_memory=True)
+            st, n = esim_ad_events(self.ctx, buf.data_ptr(), cap)
+        _check(st, "esim_ad_events")
         out = np.empty(n, EVENT_DTYPE)
         if n:
-            st, n2 = esim_ad_events(self.ctx, out.ctypes.data, n)
-            _check(st, "esim_ad_events")
+            out.view(np.uint8)[:] = buf.numpy()[: n * EVENT_DTYPE.itemsize]
         self._keep.clear()
         return out
 
