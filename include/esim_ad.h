@@ -382,6 +382,67 @@ esim_ad_status esim_ad_write_events_noalloc(const int32_t* counts, int32_t width
                                             uint32_t frame, esim_ad_event* events, uint64_t capacity,
                                             uint64_t* total_device, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Evaluation (Section 4, quantitative comparison).
+ *
+ * esim_ad_esim_frame: one frame of the plain ESIM simulator the paper compares
+ * against (and, run on noise-free frames, the stand-in for its reference
+ * events): Eq. 1 applied to the log brightness y = ln(Y + log_eps) of the frame
+ * itself (Y = Rec.709 luminance of RGB radiance, or the radiance itself with
+ * one channel), with the simulator's crossing rule: dL = y - L_last,
+ * n = floor(|dL| / C), counts = sign(dL) n, L_last += counts C.  init != 0:
+ * L_last = y and counts = 0 (frame 0).
+ *
+ * radiance  [channels][n_pix] float32, device (input, caller-owned); channels 1 or 3.
+ * l_last    [n_pix] float32, device (in/out, caller-owned).
+ * counts    [n_pix] int32, device (output, caller-owned).
+ * Asynchronous on cuda_stream.  EINVAL for NULL pointers, channels not 1 or
+ * 3, n_pix < 0 or contrast <= 0; ECUDA if the launch fails.
+ */
+esim_ad_status esim_ad_esim_frame(const float* radiance, int32_t channels, float log_eps, float contrast,
+                                  int32_t init, float* l_last, int32_t* counts, int64_t n_pix,
+                                  void* cuda_stream);
+
+/* Result of esim_ad_quality; tau values as passed, up to 16. */
+typedef struct {
+    int32_t n_tau;
+    float tau[16];
+    double precision[16];   /* P(tau), Eq. 10a */
+    double recall[16];      /* R(tau), Eq. 10b */
+    double fscore[16];      /* harmonic mean of the two (0 where both are 0) */
+    double chamfer;         /* polarity-aware chamfer distance; +inf if an event has no same-polarity partner */
+    uint64_t n_gen, n_ref;  /* events in each set */
+} esim_ad_quality_result;
+
+/*
+ * Precision, recall, F-score and chamfer distance of generated events against
+ * reference events, both given as signed per-pixel count maps (p*n per pixel
+ * and frame, as the simulators produce).  Events are signed points
+ * (x / width, y / height, t / frames); for every event the distance to the
+ * nearest event of the same polarity in the other set is found exactly on the
+ * GPU: a per-column pass records, for each pixel, the squared distance to the
+ * nearest event in its column (per frame and polarity), then each event
+ * searches outward in x and t with the bound of its best distance so far.
+ * P(tau) = fraction of generated events within tau of a reference event,
+ * R(tau) = fraction of reference events within tau of a generated event; the
+ * chamfer distance is the mean squared distance generated -> reference plus
+ * the mean squared distance reference -> generated.  Distances are evaluated
+ * in FP32 (squared, then compared with tau^2); sums in FP64, reduced in a
+ * fixed order (the result is deterministic).
+ *
+ * gen, ref   [frames][height][width] int32, device (input, caller-owned).
+ * tau        n_tau (1..16) thresholds, host.
+ * workspace  device memory of esim_ad_quality_workspace_size() bytes,
+ *            caller-owned, any content.
+ * out        host (output); written after the stream has been synchronised.
+ * Synchronises cuda_stream.  EINVAL for NULL pointers, sizes <= 0, n_tau out
+ * of range or a workspace that is too small; ECUDA if a CUDA call fails.
+ */
+size_t esim_ad_quality_workspace_size(int32_t width, int32_t height, int32_t frames);
+esim_ad_status esim_ad_quality(const int32_t* gen, const int32_t* ref, int32_t width, int32_t height,
+                               int32_t frames, const float* tau, int32_t n_tau, void* workspace,
+                               size_t workspace_bytes, esim_ad_quality_result* out, void* cuda_stream);
+
 /* Restart the sequence at frame 0 and clear events, counters and sticky errors. */
 esim_ad_status esim_ad_reset(esim_ad_ctx* ctx);
 

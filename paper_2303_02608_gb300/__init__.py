@@ -46,7 +46,7 @@ EXPORTS = (
     "esim_ad_wlr_backward", "esim_ad_batch_init", "esim_ad_batch_step", "esim_ad_batch_events",
     "esim_ad_batch_reset_sequence", "esim_ad_batch_denoised", "esim_ad_batch_get_state",
     "esim_ad_batch_stats", "esim_ad_batch_profile_enable", "esim_ad_batch_profile_get",
-    "esim_ad_batch_destroy",
+    "esim_ad_batch_destroy", "esim_ad_esim_frame", "esim_ad_quality_workspace_size", "esim_ad_quality",
 )
 
 
@@ -167,6 +167,14 @@ def load_library():
     lib.esim_ad_batch_profile_get.argtypes = [P, ctypes.POINTER(esim_ad_profile)]
     lib.esim_ad_batch_destroy.restype = None
     lib.esim_ad_batch_destroy.argtypes = [P]
+    lib.esim_ad_esim_frame.restype = st
+    lib.esim_ad_esim_frame.argtypes = [P, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_int32, P, P,
+                                       ctypes.c_int64, P]
+    lib.esim_ad_quality_workspace_size.restype = ctypes.c_size_t
+    lib.esim_ad_quality_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.esim_ad_quality.restype = st
+    lib.esim_ad_quality.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
+                                    ctypes.c_size_t, ctypes.POINTER(esim_ad_quality_result), P]
     lib.esim_ad_status_string.restype = ctypes.c_char_p
     lib.esim_ad_status_string.argtypes = [st]
     _lib = lib
@@ -283,6 +291,53 @@ def esim_ad_write_events_noalloc(counts: int, width: int, height: int, frame: in
     return load_library().esim_ad_write_events_noalloc(
         ctypes.c_void_p(counts or None), width, height, frame, ctypes.c_void_p(events or None),
         ctypes.c_uint64(capacity), ctypes.c_void_p(total_device or None), ctypes.c_void_p(cuda_stream or None))
+
+
+class esim_ad_quality_result(ctypes.Structure):
+    _fields_ = [("n_tau", ctypes.c_int32), ("tau", ctypes.c_float * 16), ("precision", ctypes.c_double * 16),
+                ("recall", ctypes.c_double * 16), ("fscore", ctypes.c_double * 16), ("chamfer", ctypes.c_double),
+                ("n_gen", ctypes.c_uint64), ("n_ref", ctypes.c_uint64)]
+
+
+def esim_frame(radiance, l_last, counts, contrast: float, init: bool, log_eps: float = 1e-3) -> None:
+    """One frame of plain ESIM (the evaluation's reference and baseline
+    simulator) on device tensors: radiance [C][H][W] float32 (C = 1 or 3),
+    l_last [H][W] float32 (in/out), counts [H][W] int32 (out)."""
+    import torch
+    for t, dt in ((radiance, torch.float32), (l_last, torch.float32), (counts, torch.int32)):
+        if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise ValueError("esim_frame: contiguous device tensors of the documented types")
+    n = l_last.numel()
+    if radiance.numel() != radiance.shape[0] * n or counts.numel() != n:
+        raise ValueError("esim_frame: shapes do not match")
+    _check(load_library().esim_ad_esim_frame(
+        ctypes.c_void_p(radiance.data_ptr()), radiance.shape[0], log_eps, contrast, int(init),
+        ctypes.c_void_p(l_last.data_ptr()), ctypes.c_void_p(counts.data_ptr()), n,
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "esim_ad_esim_frame")
+
+
+def quality(gen, ref, taus) -> dict:
+    """P(tau), R(tau), F(tau) and the chamfer distance of generated events
+    against reference events, both signed count maps [F][H][W] int32 on the
+    device (the workspace comes from torch)."""
+    import torch
+    if gen.shape != ref.shape or gen.dim() != 3:
+        raise ValueError("quality: two [F][H][W] count maps of one shape")
+    for t in (gen, ref):
+        if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+            raise ValueError("quality: contiguous int32 device tensors")
+    F, H, W = gen.shape
+    lib = load_library()
+    ws_bytes = int(lib.esim_ad_quality_workspace_size(W, H, F))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=gen.device)
+    tau = (ctypes.c_float * len(taus))(*taus)
+    r = esim_ad_quality_result()
+    _check(lib.esim_ad_quality(ctypes.c_void_p(gen.data_ptr()), ctypes.c_void_p(ref.data_ptr()), W, H, F, tau,
+                               len(taus), ctypes.c_void_p(ws.data_ptr()), ws_bytes, ctypes.byref(r),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "esim_ad_quality")
+    k = r.n_tau
+    return {"tau": list(r.tau[:k]), "precision": list(r.precision[:k]), "recall": list(r.recall[:k]),
+            "fscore": list(r.fscore[:k]), "chamfer": r.chamfer, "n_gen": int(r.n_gen), "n_ref": int(r.n_ref)}
 
 
 def make_wlr_desc(width: int, height: int, sequence: int, radius: int = 3, frames: int = 3, rgb: bool = True,
