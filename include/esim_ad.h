@@ -101,7 +101,13 @@ typedef struct esim_ad_config {
     float    feature_scale[7]; /* > 0; BF16 feature j stores x_j / scale_j (inputs
                                   in FEAT_BF16 and the MIXED ring); powers of two
                                   keep the round trip exact. Ignored otherwise. */
-    float    reserved1;
+    float    guard_kappa;    /* optional variance guard of the test (a project
+                                extension, off for parity with the paper): with
+                                guard_kappa > 0 an adaptive frame also flags a
+                                pixel when |y_t(c) - L_last| >= C + guard_kappa *
+                                sigma_y, sigma_y = sqrt(Var[Y]) / (Y + eps) (delta
+                                method, Var[Y] from the frame's variance plane;
+                                0 when that plane is NULL).  <= 0: off.        */
     uint64_t event_capacity; /* device event buffer size in events, >= 1        */
 } esim_ad_config;
 
@@ -115,8 +121,9 @@ typedef struct esim_ad_config {
  */
 typedef struct esim_ad_frame {
     const void*  radiance;   /* [1 or 3][H][W] float32, or [H][W] FP16 log (radiance_fmt) */
-    const float* variance;   /* [H][W] sample variance, may be NULL (unused by
-                                the method; carried for callers' bookkeeping)  */
+    const float* variance;   /* [H][W] sample variance of the luminance Y, may be
+                                NULL; read only by the optional guard
+                                (guard_kappa > 0), unused by the paper's method */
     const float* normal;     /* [3][H][W] float32 (FEAT_F32)                    */
     const float* albedo;     /* [3][H][W] float32 (FEAT_F32)                    */
     const float* depth;      /* [H][W] float32 (FEAT_F32)                       */

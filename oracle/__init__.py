@@ -42,7 +42,7 @@ class _Cfg(ctypes.Structure):
                 ("pixel_units", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("contrast", ctypes.c_double), ("h", ctypes.c_double),
                 ("bandwidth", ctypes.c_double * 7), ("log_eps", ctypes.c_double),
-                ("ridge", ctypes.c_double)]
+                ("ridge", ctypes.c_double), ("guard_kappa", ctypes.c_double)]
 
 
 _lib = None
@@ -58,6 +58,8 @@ def _load():
         lib.or_destroy.argtypes = [P]
         lib.or_push.restype = ctypes.c_int
         lib.or_push.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_int32]
+        lib.or_push_var.restype = ctypes.c_int
+        lib.or_push_var.argtypes = [P, P, P, P, P, P, ctypes.c_int32, ctypes.c_int32]
         lib.or_frame_outputs.argtypes = [P, P, P, P, P, P]
         lib.or_event_count.restype = ctypes.c_int64
         lib.or_event_count.argtypes = [P]
@@ -91,6 +93,7 @@ class OracleConfig:
     bandwidth: list = field(default_factory=lambda: [1.0] * 7)
     log_eps: float = 1e-3
     ridge: float = 1e-4
+    guard_kappa: float = 0.0   # optional variance guard (extension); <= 0: off
 
 
 def _f32(a) -> np.ndarray:
@@ -112,6 +115,7 @@ class Oracle:
         c.width, c.height, c.radius, c.frames = cfg.width, cfg.height, cfg.radius, cfg.frames
         c.channels, c.mode, c.pixel_units = cfg.channels, cfg.mode, int(cfg.pixel_units)
         c.contrast, c.h, c.log_eps, c.ridge = cfg.contrast, cfg.h, cfg.log_eps, cfg.ridge
+        c.guard_kappa = cfg.guard_kappa
         for j in range(7):
             c.bandwidth[j] = float(cfg.bandwidth[j])
         self._lib = _load()
@@ -131,7 +135,10 @@ class Oracle:
         rad = _f32(frame["radiance"])
         nor, alb, dep = _f32(frame["normal"]), _f32(frame["albedo"]), _f32(frame["depth"])
         r0, r1 = (0, -1) if rows is None else rows
-        rc = self._lib.or_push(self._h, _ptr(rad), _ptr(nor), _ptr(alb), _ptr(dep), r0, r1)
+        var = frame.get("variance") if self.cfg.guard_kappa > 0 else None
+        var = None if var is None else _f32(var)
+        rc = self._lib.or_push_var(self._h, _ptr(rad), None if var is None else _ptr(var), _ptr(nor), _ptr(alb),
+                                   _ptr(dep), r0, r1)
         if rc != 0:
             raise RuntimeError(f"oracle push failed ({rc})")
         self.t += 1

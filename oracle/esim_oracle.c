@@ -289,6 +289,12 @@ static void push_event(or_sim* s, int32_t t, int32_t x, int32_t y, int32_t p)
 int or_push(or_sim* s, const float* radiance, const float* normal, const float* albedo,
             const float* depth, int32_t row0, int32_t row1)
 {
+    return or_push_var(s, radiance, NULL, normal, albedo, depth, row0, row1);
+}
+
+int or_push_var(or_sim* s, const float* radiance, const float* variance, const float* normal,
+                const float* albedo, const float* depth, int32_t row0, int32_t row1)
+{
     if (!s || !radiance || !normal || !albedo || !depth) return -1;
     const or_config* c = &s->cfg;
     if (row1 < 0 || row1 > c->height) row1 = c->height;
@@ -326,6 +332,14 @@ int or_push(or_sim* s, const float* radiance, const float* normal, const float* 
                 for (int j = 0; j < NF; ++j) st += s->beta[p * ND + 2 + j] * (s->xc[p * NF + j] - xnow[j]);
                 s->stat_o[p] = st;
                 run = (st * st >= C * C);
+                if (!run && c->guard_kappa > 0) {
+                    /* guard: the log brightness itself moved past C by more than
+                     * guard_kappa deviations; sigma_y = sqrt(Var[Y]) / (Y + eps)
+                     * with Y + eps = exp(y) */
+                    const double yc = ring_y(s, t, p);
+                    const double sig = variance ? sqrt(fmax((double)variance[p], 0.0)) / exp(yc) : 0.0;
+                    run = fabs(yc - s->l_last[p]) >= C + c->guard_kappa * sig;
+                }
             }
             if (!run) continue;
             double theta[NP], R, Wsum;

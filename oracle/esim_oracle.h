@@ -33,6 +33,10 @@ typedef struct or_config {
     double bandwidth[7];  /* b_j of the 7 feature dimensions (coords: 1)     */
     double log_eps;       /* eps in y = ln(Y + eps)                          */
     double ridge;         /* lambda: objective gets + lambda * W * |beta|^2   */
+    double guard_kappa;   /* optional variance guard (a project extension, not
+                             in the paper): > 0 also regresses a pixel whose
+                             |y_t(c) - L_last| >= C + guard_kappa * sigma_y,
+                             sigma_y = sqrt(Var[Y]) / (Y + eps); <= 0: off   */
 } or_config;
 
 typedef struct or_sim or_sim;
@@ -47,6 +51,11 @@ void    or_destroy(or_sim* s);
  * Returns 0, or -1 on a bad argument. */
 int     or_push(or_sim* s, const float* radiance, const float* normal,
                 const float* albedo, const float* depth, int32_t row0, int32_t row1);
+
+/* or_push with the frame's luminance variance [H][W] for the guard (may be
+ * NULL: sigma_y = 0). */
+int     or_push_var(or_sim* s, const float* radiance, const float* variance, const float* normal,
+                    const float* albedo, const float* depth, int32_t row0, int32_t row1);
 
 /* Per-pixel results of the last pushed frame (any pointer may be NULL):
  * alpha (NaN where no regression ran), stat = beta^T (x^c - xhat^c) of the

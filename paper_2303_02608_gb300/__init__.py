@@ -58,7 +58,7 @@ class esim_ad_config(ctypes.Structure):
         ("reserved0", ctypes.c_int32),
         ("contrast", ctypes.c_float), ("h", ctypes.c_float), ("bandwidth", ctypes.c_float * 7),
         ("log_eps", ctypes.c_float), ("ridge", ctypes.c_float), ("feature_scale", ctypes.c_float * 7),
-        ("reserved1", ctypes.c_float), ("event_capacity", ctypes.c_uint64),
+        ("guard_kappa", ctypes.c_float), ("event_capacity", ctypes.c_uint64),
     ]
 
 
@@ -199,7 +199,7 @@ def make_config(width: int, height: int, radius: int = 7, frames: int = 5, contr
                 mode: int = ESIM_AD_ADAPTIVE, rgb: bool = True, h: float = 1.0, bandwidth=None,
                 log_eps: float = 1e-3, ridge: float = 1e-4, event_capacity: int = 1 << 22,
                 radiance_fmt: int | None = None, feature_fmt: int = ESIM_AD_FEAT_F32,
-                precision: int = ESIM_AD_FP32, feature_scale=None) -> esim_ad_config:
+                precision: int = ESIM_AD_FP32, feature_scale=None, guard_kappa: float = 0.0) -> esim_ad_config:
     c = esim_ad_config()
     c.struct_size = ctypes.sizeof(esim_ad_config)
     c.width, c.height, c.radius, c.frames = width, height, radius, frames
@@ -215,6 +215,7 @@ def make_config(width: int, height: int, radius: int = 7, frames: int = 5, contr
     for j in range(7):
         c.bandwidth[j] = float(bw[j])
     c.event_capacity = int(event_capacity)
+    c.guard_kappa = float(guard_kappa)
     return c
 
 
@@ -444,11 +445,13 @@ class SimConfig:
     feature_fmt: int = ESIM_AD_FEAT_F32
     precision: int = ESIM_AD_FP32
     feature_scale: list = field(default_factory=lambda: [1.0] * 7)
+    guard_kappa: float = 0.0             # optional variance guard of the test; <= 0: off
 
     def c_config(self) -> esim_ad_config:
         return make_config(self.width, self.height, self.radius, self.frames, self.contrast, self.mode,
                            self.rgb, self.h, self.bandwidth, self.log_eps, self.ridge, self.event_capacity,
-                           self.radiance_fmt, self.feature_fmt, self.precision, self.feature_scale)
+                           self.radiance_fmt, self.feature_fmt, self.precision, self.feature_scale,
+                           self.guard_kappa)
 
 
 class Simulator:
@@ -481,6 +484,8 @@ class Simulator:
     def push(self, frame: dict) -> None:
         t = self._torch
         keys = ["radiance"] + (["features"] if "features" in frame else ["normal", "albedo", "depth"])
+        if self.cfg.guard_kappa > 0 and frame.get("variance") is not None:
+            keys.append("variance")
         planes = [frame[k] for k in keys]
         on_host = not planes[0].is_cuda
         for p in planes:
@@ -488,7 +493,8 @@ class Simulator:
                 raise ValueError("frame planes must be contiguous, all on the GPU or all on the host")
         ptr = {k: v.data_ptr() for k, v in zip(keys, planes)}
         esim_ad_push_frame(self.ctx, ptr["radiance"], ptr.get("normal", 0), ptr.get("albedo", 0),
-                           ptr.get("depth", 0), on_host=on_host, features=ptr.get("features", 0))
+                           ptr.get("depth", 0), variance=ptr.get("variance", 0), on_host=on_host,
+                           features=ptr.get("features", 0))
         # inputs (device planes, or pinned host planes copied asynchronously) are
         # read in stream order; keep them alive until the next sync point
         self._keep.append(planes)

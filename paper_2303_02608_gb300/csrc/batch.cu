@@ -433,6 +433,8 @@ void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames)
         ip.test = (c0.mode == ESIM_AD_ADAPTIVE && t64 > 0) ? 1 : 0;
         ip.log_eps = c0.log_eps;
         ip.C = c.contrast;
+        ip.guard_kappa = c.guard_kappa > 0.0f ? c.guard_kappa : 0.0f;
+        ip.variance = ip.guard_kappa > 0.0f ? f.variance : nullptr;
         ip.ring = b->ring[i];
         ip.state = b->state[i];
         ip.flag = b->flag[i];

@@ -80,7 +80,7 @@ struct esim_ad_ctx {
     unsigned long long* chunk_off = nullptr;
     esim_ad_event* events = nullptr;
     Ctrl* ctrl = nullptr;
-    float* staging[2] = {nullptr, nullptr};   // host-frame landing buffers [10][H][W]
+    float* staging[2] = {nullptr, nullptr};   // host-frame landing buffers [11][H][W]
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
     int staging_next = 0;
@@ -129,6 +129,7 @@ esim_ad_status check_config(const esim_ad_config* c)
     for (int j = 0; j < 7; ++j)
         if (!finite_pos(c->bandwidth[j])) return ESIM_AD_EINVAL;
     if (!isfinite(c->log_eps) || c->log_eps < 0.0f) return ESIM_AD_EINVAL;
+    if (!isfinite(c->guard_kappa)) return ESIM_AD_EINVAL;
     if (c->event_capacity < 1 || c->event_capacity > (1ull << 36)) return ESIM_AD_EINVAL;
     return ESIM_AD_OK;
 }
@@ -339,19 +340,20 @@ static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, e
         }
     }
     if (!c->staging[s]) {
-        esim_ad_status st = dev_alloc((void**)&c->staging[s], 10 * N * sizeof(float));
+        esim_ad_status st = dev_alloc((void**)&c->staging[s], 11 * N * sizeof(float));
         if (st != ESIM_AD_OK) return st;
     }
     unsigned char* base = reinterpret_cast<unsigned char*>(c->staging[s]);
     if (cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[s], 0) != cudaSuccess) return ESIM_AD_ECUDA;
-    // landing layout: radiance at 0 (up to 3N floats), features after it
+    // landing layout: radiance at 0 (up to 3N floats), features after it, the
+    // guard's variance plane last
     const size_t rad_bytes = c->cfg.radiance_fmt == ESIM_AD_LOGLUMA_F16 ? N * 2
                            : (c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1) * N * 4;
     struct Copy {
         const void* src;
         size_t off, bytes;
     };
-    Copy cp[4];
+    Copy cp[5];
     int n = 0;
     cp[n++] = {f->radiance, 0, rad_bytes};
     *dev = *f;
@@ -367,6 +369,12 @@ static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, e
         dev->normal = reinterpret_cast<const float*>(base + 12 * N);
         dev->albedo = reinterpret_cast<const float*>(base + 24 * N);
         dev->depth = reinterpret_cast<const float*>(base + 36 * N);
+    }
+    if (c->cfg.guard_kappa > 0.0f && f->variance) {
+        cp[n++] = {f->variance, 40 * N, N * 4};
+        dev->variance = reinterpret_cast<const float*>(base + 40 * N);
+    } else {
+        dev->variance = nullptr;
     }
     for (int k = 0; k < n; ++k)
         if (cudaMemcpyAsync(base + cp[k].off, cp[k].src, cp[k].bytes, cudaMemcpyHostToDevice,
@@ -420,6 +428,8 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     ip.test = adaptive_test ? 1 : 0;
     ip.log_eps = c->cfg.log_eps;
     ip.C = c->cfg.contrast;
+    ip.guard_kappa = c->cfg.guard_kappa > 0.0f ? c->cfg.guard_kappa : 0.0f;
+    ip.variance = ip.guard_kappa > 0.0f ? f->variance : nullptr;
     ip.ring = c->ring;
     ip.state = c->state;
     ip.flag = c->flag;

@@ -18,6 +18,7 @@ __device__ __forceinline__ int ingest_pixel(const IngestParams& p, int x, int y)
     if (inside) {
         const size_t i = (size_t)y * p.W + x;
         float yv;
+        float Yeps = -1.0f;   // Y + eps when the input is linear radiance
         if (p.rad_fmt == ESIM_AD_LOGLUMA_F16) {
             yv = __half2float(reinterpret_cast<const __half*>(p.rad)[i]);
         } else {
@@ -29,7 +30,8 @@ __device__ __forceinline__ int ingest_pixel(const IngestParams& p, int x, int y)
             } else {
                 Y = __ldg(rad + i);
             }
-            yv = logf(Y + p.log_eps);
+            Yeps = Y + p.log_eps;
+            yv = logf(Yeps);
         }
         float f[7];   // normal xyz, depth, albedo rgb
         if (p.feat_fmt == ESIM_AD_FEAT_BF16) {
@@ -68,6 +70,17 @@ __device__ __forceinline__ int ingest_pixel(const IngestParams& p, int x, int y)
             const float4 b1 = p.state[N + i];
             const float s = b1.w - dot7(b0, b1, n0, n1, n2, d, a0, a1, a2);
             flag = (s * s >= p.C * p.C) ? 1 : 0;
+            if (!flag && p.guard_kappa > 0.0f) {
+                // optional guard: the log brightness itself has moved past C by
+                // more than guard_kappa noise deviations (sigma_y by the delta method)
+                float sigma = 0.0f;
+                if (p.variance) {
+                    const float ye = Yeps > 0.0f ? Yeps : expf(yv);
+                    sigma = sqrtf(fmaxf(__ldg(p.variance + i), 0.0f)) / ye;
+                }
+                const float L = p.state[3 * N + i].w;
+                flag = fabsf(yv - L) >= fmaf(p.guard_kappa, sigma, p.C) ? 1 : 0;
+            }
         } else {
             flag = 1;
         }

@@ -106,6 +106,8 @@ struct IngestParams {
     int slot;              // ring slot of this frame
     int test;              // 1: Proposition-1 test; 0: flag every pixel
     float log_eps, C;
+    float guard_kappa;     // > 0: also flag |y - L_last| >= C + guard_kappa * sigma_y
+    const float* variance; // [H][W] Var[Y] for the guard, or NULL (sigma_y = 0)
     void* ring;
     const float4* state;
     uint8_t* flag;

@@ -70,6 +70,16 @@ def adopt_gpu_state(orc, g_st):
     orc.set_state(g_st["l_last"].astype(np.float64), beta9, g_st["xc"].astype(np.float64))
 
 
+def _guard_margin(fr, l_last, kappa, eps=1e-3):
+    """|y - L_last| - (C-free part of the guard threshold kappa * sigma_y), FP64,
+    from the frame's radiance (RGB or luminance) and variance."""
+    rad = np.asarray(fr["radiance"], np.float64)
+    Y = rad[0] if rad.shape[0] == 1 else 0.2126 * rad[0] + 0.7152 * rad[1] + 0.0722 * rad[2]
+    y = np.log(Y + eps)
+    sig = np.sqrt(np.maximum(np.asarray(fr["variance"], np.float64), 0.0)) / (Y + eps)
+    return np.abs(y - l_last) - kappa * sig
+
+
 def compare_frame(t, fr, g_alpha, g_flag, g_ev, g_st, orc, C, band, adaptive, rep, alpha_tol=ALPHA_TOL,
                   strict=True, gpu_state_after=None):
     """Compare one frame after both sides processed it.  g_st is the GPU model
@@ -86,6 +96,12 @@ def compare_frame(t, fr, g_alpha, g_flag, g_ev, g_st, orc, C, band, adaptive, re
                                 np.asarray(fr["albedo"])], 0).reshape(7, n).T.astype(np.float64)
         s_g = np.sum(g_st["beta"].astype(np.float64) * (g_st["xc"].astype(np.float64) - feats), 1)
         amb_f = band & _straddles(s_g.reshape(H, W), o["stat"], C, DECISION_TOL)
+        kappa = getattr(orc.cfg, "guard_kappa", 0.0)
+        if kappa > 0:
+            # the guard's decision quantity, from the GPU's level (both sides
+            # hold it in strict mode): ambiguous within the tolerance of C
+            m = _guard_margin(fr, g_st["l_last"].reshape(H, W).astype(np.float64), kappa)
+            amb_f |= band & (np.abs(m - C) <= DECISION_TOL)
     bad_flag = band & ~amb_f & (g_flag != o_flag)
     assert not bad_flag.any(), f"frame {t}: {int(bad_flag.sum())} flag decisions differ " \
                                f"(first at {np.argwhere(bad_flag)[0]})"
@@ -157,7 +173,7 @@ def run(frames, sim, orc, C, rows=None, strict=True, adaptive=True, report=None,
         if "gpu" in fr:            # inputs in a storage format; fr holds their dequantised values
             gpu_in = {k: v.cuda() for k, v in fr["gpu"].items()}
         else:
-            gpu_in = {k: fr[k].cuda() for k in ("radiance", "normal", "albedo", "depth")}
+            gpu_in = {k: fr[k].cuda() for k in ("radiance", "normal", "albedo", "depth", "variance") if k in fr}
         sim.push(gpu_in)
         orc.push(fr, None if rows is None else rows)
         g_alpha, g_flag = sim.denoised()

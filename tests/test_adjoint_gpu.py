@@ -45,7 +45,7 @@ def _gpu(rad, feat, clean, b):
     alpha = wlr(rd, feat.cuda(), bd, radius=R, frames=T, log_eps=EPS, ridge=RIDGE)
     loss = ((alpha - log_luminance(clean.cuda(), EPS)) ** 2).mean()
     loss.backward()
-    return alpha.detach().cpu(), rd.grad.cpu(), bd.grad.cpu(), float(loss)
+    return alpha.detach().cpu(), rd.grad.cpu(), bd.grad.cpu(), float(loss.detach())
 
 
 RECTS = SceneConfig(kind="rects", width=160, height=120, frames=6, spp=2, seed=4, rgb=True, n_rects=12,

@@ -323,6 +323,35 @@ def test_global_step_closed_form_events():
             assert per_frame == [H * W * e for e in expect]
 
 
+def test_global_step_with_variance_guard():
+    """The optional guard flags a pixel whose log brightness moved by at least
+    C + kappa * sigma_y since its last event.  On the global step the guard
+    alone lets the adaptive mode fire, and then every flagged pixel regresses
+    exactly the exhaustive window, so the events equal the closed-form
+    exhaustive ones; with a noise deviation larger than the step the guard
+    stays silent (sigma_y = sqrt(Var[Y]) / (Y + eps), Y + eps = e^y)."""
+    gold = _load_step_golden()
+    T, C, k = gold["T"], gold["C"], gold["k"]
+    s_log = math.log(gold["gain"])
+    from scenes import Scene, preset
+    sc = Scene(preset("disc64", disc_velocity=(0.0, 0.0)))
+    c = sc.clean(0)
+    base = {"normal": c["normal"].float().numpy(), "albedo": c["albedo"].float().numpy(),
+            "depth": c["depth"].float().numpy()}
+    y0 = np.log(c["radiance"][0].double().numpy() + 1e-3)
+    H, W = y0.shape
+    for var_scale, expect in ((0.0, gold["events_per_pixel_by_frame"]), (4.0, [0] * (k + 5))):
+        o = Oracle(OracleConfig(W, H, radius=3, frames=T, channels=0, mode=ADAPTIVE, contrast=C, guard_kappa=3.0))
+        per_frame = []
+        for t in range(k + 5):
+            y = y0 + (s_log if t >= k else 0.0)
+            # Var[Y] = (var_scale (Y + eps))^2: sigma_y = var_scale, kappa sigma_y = 12 > s
+            var = (var_scale * np.exp(y)) ** 2
+            o.push(dict(base, radiance=y.astype(np.float32), variance=var.astype(np.float32)))
+            per_frame.append(len(o.take_events()))
+        assert per_frame == [H * W * e for e in expect]
+
+
 @pytest.mark.parametrize("jump,C,n_exp", [(1.1, 0.2, 5), (-0.5, 0.2, -2), (0.19, 0.2, 0), (0.2, 0.1, 2)])
 def test_multiple_crossings_and_reference_update(jump, C, n_exp):
     """n = floor(|dL|/C) events of polarity sign(dL); L_last moves by p*n*C, so

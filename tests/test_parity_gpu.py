@@ -121,3 +121,32 @@ def test_1080p_band():
     """1920x1080, 1 spp-equivalent noise, 15x15x5, C = 0.1 (adaptive); band of rows."""
     rep = _case(preset("rects1080p"), 7, 5, 0.1, ADAPTIVE, 6, rows=(536, 544))
     assert rep["regressed"] > 0
+
+
+@pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse")])
+def test_variance_guard(mode, path):
+    """Optional guard (kappa = 3, the frame's variance plane): flags also where
+    the log brightness itself moved past C + 3 sigma_y; both sides apply it."""
+    import os
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    cfg = SceneConfig(kind="rects", width=96, height=72, frames=8, spp=8, seed=21, rgb=True, n_rects=8,
+                      bg_depth=10.0)
+    frames = Scene(cfg).sequence(8)
+    keys = ("ESIM_AD_SPARSE_MAX", "ESIM_AD_SPARSE_STAGE")
+    old = {k: os.environ.pop(k, None) for k in keys}
+    if PATHS[path][0] is not None:
+        os.environ["ESIM_AD_SPARSE_MAX"] = PATHS[path][0]
+    try:
+        sim = Simulator(SimConfig(width=96, height=72, radius=3, frames=3, contrast=0.15, mode=mode, rgb=True,
+                                  guard_kappa=3.0))
+    finally:
+        for k in keys:
+            os.environ.pop(k, None)
+            if old[k] is not None:
+                os.environ[k] = old[k]
+    orc = Oracle(OracleConfig(96, 72, radius=3, frames=3, channels=3, mode=mode, contrast=0.15, guard_kappa=3.0))
+    rep = run(frames, sim, orc, 0.15, adaptive=True)
+    sim.close()
+    plain = _case(cfg, 3, 3, 0.15, mode, 8, path=path)
+    # the guard only adds regressions
+    assert rep["regressed"] >= plain["regressed"] and rep["events"] > 0
