@@ -386,6 +386,8 @@ def run_ours(args):
         line["e2e"] = _e2e(args, scene, wl, N, stream)
     if rank == 0 and not args.no_diff:
         line["differentiation_form"] = _differentiation(dev)
+    if rank == 0 and not args.no_quality:
+        line["quality"] = _quality(dev)
     if rank == 0 and not args.no_batch:
         line["batching_form"] = _batching(dev)
     if rank == 0 and not args.no_cpu_baseline:
@@ -456,6 +458,83 @@ def _batching(dev, warmup=4, steps=12):
             "per_sequence_contexts": {"value": round(px_total / (t_ctx * 1e-3), 1),
                                       "ms_per_step": round(t_ctx / steps, 3)},
             "autotuned_lanes_per_pixel": st["lanes"], "graph_per_step": True}
+
+
+def _events_to_counts(sink, n, counts):
+    """Accumulate n 12-byte event records (frame, x | y << 16, polarity) from
+    the device buffer `sink` into the signed count map counts [F][H][W]."""
+    import torch
+    if n == 0:
+        return
+    rec = sink[: n * 12].view(torch.int32).view(n, 3)
+    t = rec[:, 0].long()
+    x = (rec[:, 1] & 0xFFFF).long()
+    y = ((rec[:, 1] >> 16) & 0xFFFF).long()
+    pol = (rec[:, 2] & 0xFF).to(torch.int8).to(torch.int32)
+    counts.index_put_((t, y, x), pol, accumulate=True)
+
+
+def _quality(dev, C_values=(0.25, 0.5, 0.75, 1.0), taus=(5e-4, 1e-3, 2e-3, 5e-3, 1e-2)):
+    """Event quality on the 1280x720x120 rectangles workload (4 spp, 15x15x5
+    window): reference = ESIM on the noise-free frames; compared: ESIM on the
+    noisy frames, exhaustive WLR + ESIM, the adaptive simulator (FP32 form),
+    and the adaptive simulator with the optional variance guard (kappa = 3),
+    for the thresholds of the paper's threshold study.  Points are
+    (x/W, y/H, t/F)."""
+    import torch
+    from paper_2303_02608_gb300 import (ESIM_AD_ADAPTIVE, ESIM_AD_EXHAUSTIVE, SimConfig, Simulator,
+                                        esim_frame, quality)
+    from scenes import Scene, preset
+    scfg = preset("rects720p")
+    scene = Scene(scfg)
+    F, Wd, H = scfg.frames, scfg.width, scfg.height
+    frames = [scene.frame(t, dev) for t in range(F)]
+    cap = 1 << 24
+    sink = torch.empty(cap * 12, dtype=torch.uint8, device=dev)
+
+    def esim_counts(C, key):
+        l_last = torch.empty(H, Wd, dtype=torch.float32, device=dev)
+        counts = torch.zeros(F, H, Wd, dtype=torch.int32, device=dev)
+        for t, f in enumerate(frames):
+            esim_frame(f[key], l_last, counts[t], C, init=(t == 0))
+        return counts
+
+    def sim_counts(C, mode, kappa=0.0):
+        sim = Simulator(SimConfig(width=Wd, height=H, radius=7, frames=5, contrast=C, mode=mode, rgb=True,
+                                  event_capacity=cap, guard_kappa=kappa))
+        counts = torch.zeros(F, H, Wd, dtype=torch.int32, device=dev)
+        for f in frames:
+            sim.push({k: f[k] for k in ("radiance", "normal", "albedo", "depth", "variance")})
+            _events_to_counts(sink, sim.events_device(sink, cap), counts)
+        regressions = sim.stats()["regressions"]
+        sim.close()
+        return counts, regressions
+
+    out = {"workload": "rects720p: 1280x720 RGB, 120 frames, 4 spp, 15x15x5 window (FP32 form)",
+           "reference": "ESIM on the noise-free frames", "points": "(x/W, y/H, t/F)", "tau": list(taus),
+           "by_C": {}}
+    metric_s, n_eval = 0.0, 0
+    for C in C_values:
+        ref = esim_counts(C, "clean")
+        res = {}
+        for name, counts, reg in (("ESIM", esim_counts(C, "radiance"), None),
+                                  ("WLR+ESIM", *sim_counts(C, ESIM_AD_EXHAUSTIVE)),
+                                  ("ours", *sim_counts(C, ESIM_AD_ADAPTIVE)),
+                                  ("ours+guard3", *sim_counts(C, ESIM_AD_ADAPTIVE, 3.0))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q = quality(counts, ref, list(taus))
+            metric_s += time.perf_counter() - t0
+            n_eval += q["n_gen"] + q["n_ref"]
+            res[name] = {"P": [round(v, 5) for v in q["precision"]], "R": [round(v, 5) for v in q["recall"]],
+                         "F": [round(v, 5) for v in q["fscore"]], "CD": q["chamfer"], "events": q["n_gen"]}
+            if reg is not None:
+                res[name]["regressed_fraction"] = round(reg / (Wd * H * F), 4)
+        res["reference_events"] = q["n_ref"]
+        out["by_C"][str(C)] = res
+    out["metric_seconds"] = round(metric_s, 3)
+    out["events_evaluated_per_s"] = round(n_eval / metric_s, 1) if metric_s > 0 else None
+    return out
 
 
 def _differentiation(dev, reps=5):
@@ -606,6 +685,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
