@@ -478,7 +478,8 @@ def _quality(dev, C_values=(0.25, 0.5, 0.75, 1.0), taus=(5e-4, 1e-3, 2e-3, 5e-3,
     """Event quality on the 1280x720x120 rectangles workload (4 spp, 15x15x5
     window): reference = ESIM on the noise-free frames; compared: ESIM on the
     noisy frames, exhaustive WLR + ESIM, the adaptive simulator (FP32 form),
-    and the adaptive simulator with the optional variance guard (kappa = 3),
+    the adaptive simulator with the optional variance guard (kappa = 3), and
+    the adaptive simulator with bandwidths fitted by the differentiation form,
     for the thresholds of the paper's threshold study.  Points are
     (x/W, y/H, t/F)."""
     import torch
@@ -510,7 +511,35 @@ def _quality(dev, C_values=(0.25, 0.5, 0.75, 1.0), taus=(5e-4, 1e-3, 2e-3, 5e-3,
         sim.close()
         return counts, regressions
 
+    # bandwidths fitted by the differentiation form on a training crop
+    # (frames 0-15, centre 256x256) and fed back into the adaptive simulator
+    from paper_2303_02608_gb300.bandwidth import fit_bandwidths
+    y0, x0 = H // 2 - 128, Wd // 2 - 128
+    crop = (slice(None), slice(y0, y0 + 256), slice(x0, x0 + 256))
+    tr = frames[:16]
+    rad_c = torch.stack([f["radiance"][crop] for f in tr]).contiguous()
+    feat_c = torch.stack([torch.cat([f["normal"], f["depth"][None], f["albedo"]])[crop] for f in tr]).contiguous()
+    clean_c = torch.stack([f["clean"][crop] for f in tr]).contiguous()
+    t0 = time.perf_counter()
+    b_fit, hist = fit_bandwidths(rad_c, feat_c, clean_c, radius=7, frames=5, steps=60, lr=0.1)
+    fit_s = time.perf_counter() - t0
+    del rad_c, feat_c, clean_c
+
+    def sim_counts_b(C, bandwidth):
+        sim = Simulator(SimConfig(width=Wd, height=H, radius=7, frames=5, contrast=C, mode=ESIM_AD_ADAPTIVE,
+                                  rgb=True, event_capacity=cap, bandwidth=bandwidth))
+        counts = torch.zeros(F, H, Wd, dtype=torch.int32, device=dev)
+        for f in frames:
+            sim.push({k: f[k] for k in ("radiance", "normal", "albedo", "depth")})
+            _events_to_counts(sink, sim.events_device(sink, cap), counts)
+        regressions = sim.stats()["regressions"]
+        sim.close()
+        return counts, regressions
+
     out = {"workload": "rects720p: 1280x720 RGB, 120 frames, 4 spp, 15x15x5 window (FP32 form)",
+           "fitted_bandwidth": {"b": [round(v, 4) for v in b_fit], "loss_start": hist[0], "loss_end": hist[-1],
+                                "steps": len(hist), "seconds": round(fit_s, 3),
+                                "train": "frames 0-15, centre 256x256, Adam on log b"},
            "reference": "ESIM on the noise-free frames", "points": "(x/W, y/H, t/F)", "tau": list(taus),
            "by_C": {}}
     metric_s, n_eval = 0.0, 0
@@ -520,7 +549,8 @@ def _quality(dev, C_values=(0.25, 0.5, 0.75, 1.0), taus=(5e-4, 1e-3, 2e-3, 5e-3,
         for name, counts, reg in (("ESIM", esim_counts(C, "radiance"), None),
                                   ("WLR+ESIM", *sim_counts(C, ESIM_AD_EXHAUSTIVE)),
                                   ("ours", *sim_counts(C, ESIM_AD_ADAPTIVE)),
-                                  ("ours+guard3", *sim_counts(C, ESIM_AD_ADAPTIVE, 3.0))):
+                                  ("ours+guard3", *sim_counts(C, ESIM_AD_ADAPTIVE, 3.0)),
+                                  ("ours, fitted b", *sim_counts_b(C, b_fit))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             q = quality(counts, ref, list(taus))
