@@ -450,6 +450,66 @@ esim_ad_status esim_ad_quality(const int32_t* gen, const int32_t* ref, int32_t w
                                int32_t frames, const float* tau, int32_t n_tau, void* workspace,
                                size_t workspace_bytes, esim_ad_quality_result* out, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Monte Carlo renderer for analytic test scenes (a stand-in for the paper's
+ * PBRT-v4 renders, Section 3): it produces exactly the simulator's inputs -
+ * noisy RGB radiance at spp samples per pixel, the variance of the luminance
+ * estimate, and first-hit normal, depth and albedo.
+ *
+ * Scene: an open-fronted room x in [-box0, box0], y in [-box1, box1],
+ * z in [-box2, box2] (no wall at z = +box2) with diffuse walls (the back wall
+ * checkered when checker > 0), a rectangular area light of radiance
+ * light_radiance on the ceiling over [light0, light1] x [light2, light3] in
+ * x and z, and up to 8 diffuse spheres whose centres move by `velocity` per
+ * frame.  Pinhole camera at cam_pos looking along -z (up +y).
+ *
+ * Estimator per sample: a jittered camera ray; at each of up to max_bounces
+ * surface interactions, next-event estimation towards one uniform point of
+ * the light (shadowed by spheres), then a cosine-weighted bounce; emission
+ * counted for camera rays only.  Random numbers: Philox4x32-10 (Salmon et al.
+ * 2011) with key (seed, frame) and counter (pixel, sample, call, 0).  All
+ * arithmetic is IEEE FP32 with one rounding per operation (no contraction),
+ * so the result is a fixed function of the scene, frame and seed.
+ * Features are means over the samples of the camera rays' first hits; depth
+ * is the distance along the ray.
+ * ------------------------------------------------------------------------ */
+typedef struct esim_ad_sphere {
+    float center[3];    /* at frame 0 */
+    float velocity[3];  /* per frame  */
+    float radius;       /* > 0        */
+    float albedo[3];
+} esim_ad_sphere;
+
+typedef struct esim_ad_render_scene {
+    uint32_t struct_size;       /* = sizeof(esim_ad_render_scene)               */
+    int32_t  width, height;     /* >= 1, width * height < 2^31                  */
+    int32_t  spp;               /* samples per pixel, 1..65536                  */
+    int32_t  max_bounces;       /* surface interactions per path, 1..8          */
+    int32_t  n_spheres;         /* 0..8                                         */
+    uint32_t seed;
+    float    cam_pos[3];        /* inside the room                              */
+    float    tan_half_fov_y;    /* > 0                                          */
+    float    box[3];            /* half extents > 0                             */
+    float    wall_albedo[5][3]; /* left, right, floor, ceiling, back            */
+    float    back_albedo2[3];   /* second colour of the back wall's checker     */
+    float    checker;           /* checker cell size; <= 0: plain back wall     */
+    float    light[4];          /* x0 < x1, z0 < z1 of the ceiling light        */
+    float    light_radiance[3];
+    float    eps;               /* minimum hit distance > 0                     */
+    esim_ad_sphere spheres[8];
+} esim_ad_render_scene;
+
+/*
+ * Render frame `frame` of the scene into caller-owned device buffers:
+ * radiance [3][H][W], variance [H][W] (variance of the mean luminance,
+ * unbiased over the samples; 0 when spp == 1), normal [3][H][W],
+ * albedo [3][H][W], depth [H][W], all float32.  Asynchronous on cuda_stream.
+ * EINVAL for NULL pointers or out-of-range fields; ECUDA if the launch fails.
+ */
+esim_ad_status esim_ad_render(const esim_ad_render_scene* scene, int32_t frame, float* radiance,
+                              float* variance, float* normal, float* albedo, float* depth,
+                              void* cuda_stream);
+
 /* Restart the sequence at frame 0 and clear events, counters and sticky errors. */
 esim_ad_status esim_ad_reset(esim_ad_ctx* ctx);
 

@@ -47,6 +47,7 @@ EXPORTS = (
     "esim_ad_batch_reset_sequence", "esim_ad_batch_denoised", "esim_ad_batch_get_state",
     "esim_ad_batch_stats", "esim_ad_batch_profile_enable", "esim_ad_batch_profile_get",
     "esim_ad_batch_destroy", "esim_ad_esim_frame", "esim_ad_quality_workspace_size", "esim_ad_quality",
+    "esim_ad_render",
 )
 
 
@@ -175,6 +176,8 @@ def load_library():
     lib.esim_ad_quality.restype = st
     lib.esim_ad_quality.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
                                     ctypes.c_size_t, ctypes.POINTER(esim_ad_quality_result), P]
+    lib.esim_ad_render.restype = st
+    lib.esim_ad_render.argtypes = [ctypes.POINTER(esim_ad_render_scene), ctypes.c_int32, P, P, P, P, P, P]
     lib.esim_ad_status_string.restype = ctypes.c_char_p
     lib.esim_ad_status_string.argtypes = [st]
     _lib = lib
@@ -292,6 +295,64 @@ def esim_ad_write_events_noalloc(counts: int, width: int, height: int, frame: in
     return load_library().esim_ad_write_events_noalloc(
         ctypes.c_void_p(counts or None), width, height, frame, ctypes.c_void_p(events or None),
         ctypes.c_uint64(capacity), ctypes.c_void_p(total_device or None), ctypes.c_void_p(cuda_stream or None))
+
+
+class esim_ad_sphere(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_float * 3), ("velocity", ctypes.c_float * 3), ("radius", ctypes.c_float),
+                ("albedo", ctypes.c_float * 3)]
+
+
+class esim_ad_render_scene(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("spp", ctypes.c_int32), ("max_bounces", ctypes.c_int32), ("n_spheres", ctypes.c_int32),
+                ("seed", ctypes.c_uint32), ("cam_pos", ctypes.c_float * 3), ("tan_half_fov_y", ctypes.c_float),
+                ("box", ctypes.c_float * 3), ("wall_albedo", (ctypes.c_float * 3) * 5),
+                ("back_albedo2", ctypes.c_float * 3), ("checker", ctypes.c_float), ("light", ctypes.c_float * 4),
+                ("light_radiance", ctypes.c_float * 3), ("eps", ctypes.c_float),
+                ("spheres", esim_ad_sphere * 8)]
+
+
+def make_render_scene(sc) -> esim_ad_render_scene:
+    """C description of a scenes.cornell.RenderScene."""
+    r = esim_ad_render_scene()
+    r.struct_size = ctypes.sizeof(esim_ad_render_scene)
+    r.width, r.height, r.spp, r.max_bounces = sc.width, sc.height, sc.spp, sc.max_bounces
+    r.n_spheres, r.seed = len(sc.spheres), sc.seed
+    r.cam_pos[:] = list(sc.cam_pos)
+    r.tan_half_fov_y = sc.tan_half_fov_y
+    r.box[:] = list(sc.box)
+    for k in range(5):
+        r.wall_albedo[k][:] = list(sc.wall_albedo[k])
+    r.back_albedo2[:] = list(sc.back_albedo2)
+    r.checker = sc.checker
+    r.light[:] = list(sc.light)
+    r.light_radiance[:] = list(sc.light_radiance)
+    r.eps = sc.eps
+    for j, sp in enumerate(sc.spheres):
+        r.spheres[j].center[:] = list(sp.center)
+        r.spheres[j].velocity[:] = list(sp.velocity)
+        r.spheres[j].radius = sp.radius
+        r.spheres[j].albedo[:] = list(sp.albedo)
+    return r
+
+
+def render(sc, frame: int, device=None) -> dict:
+    """Render one frame of a test scene on the GPU: radiance [3][H][W],
+    variance [H][W], normal [3][H][W], albedo [3][H][W], depth [H][W]
+    (float32 CUDA tensors, the simulator's input format)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    H, W = sc.height, sc.width
+    out = {"radiance": torch.empty(3, H, W, device=dev), "variance": torch.empty(H, W, device=dev),
+           "normal": torch.empty(3, H, W, device=dev), "albedo": torch.empty(3, H, W, device=dev),
+           "depth": torch.empty(H, W, device=dev)}
+    desc = make_render_scene(sc)
+    _check(load_library().esim_ad_render(ctypes.byref(desc), int(frame),
+                                         *(ctypes.c_void_p(out[k].data_ptr()) for k in
+                                           ("radiance", "variance", "normal", "albedo", "depth")),
+                                         ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)),
+           "esim_ad_render")
+    return out
 
 
 class esim_ad_quality_result(ctypes.Structure):
