@@ -388,6 +388,8 @@ def run_ours(args):
         line["differentiation_form"] = _differentiation(dev)
     if rank == 0 and not args.no_quality:
         line["quality"] = _quality(dev)
+    if rank == 0 and not args.no_render:
+        line["rendered"] = _rendered(dev)
     if rank == 0 and not args.no_batch:
         line["batching_form"] = _batching(dev)
     if rank == 0 and not args.no_cpu_baseline:
@@ -472,6 +474,81 @@ def _events_to_counts(sink, n, counts):
     y = ((rec[:, 1] >> 16) & 0xFFFF).long()
     pol = (rec[:, 2] & 0xFF).to(torch.int8).to(torch.int32)
     counts.index_put_((t, y, x), pol, accumulate=True)
+
+
+def _rendered(dev, taus=(5e-4, 1e-3, 2e-3, 5e-3, 1e-2)):
+    """The renderer: throughput at 1920x1080, 4 spp, two interactions per
+    path; then the paper's comparison on a rendered sequence (320x240, 48
+    frames): events from 4-spp frames against ESIM on 256-spp frames of the
+    same scene, for ESIM, WLR + ESIM, the adaptive simulator and the adaptive
+    simulator with the variance guard."""
+    import torch
+    from paper_2303_02608_gb300 import (ESIM_AD_ADAPTIVE, ESIM_AD_EXHAUSTIVE, SimConfig, Simulator,
+                                        esim_frame, quality, render)
+    from scenes.cornell import cornell
+    big = cornell(width=1920, height=1080, spp=4, max_bounces=2)
+    for t in range(2):
+        render(big, t)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_fr = 10
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for t in range(n_fr):
+        render(big, t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n_fr
+    samples = big.width * big.height * big.spp
+    out = {"throughput": {"workload": "box scene 1920x1080, 4 spp, 2 interactions, 3 moving spheres",
+                          "ms_per_frame": round(ms, 3), "samples_per_s": round(samples / (ms * 1e-3), 1),
+                          "pixel_frames_per_s": round(big.width * big.height / (ms * 1e-3), 1)}}
+    W, H, F = 320, 240, 48
+    noisy_sc = cornell(width=W, height=H, spp=4, max_bounces=2, seed=1)
+    ref_sc = cornell(width=W, height=H, spp=256, max_bounces=2, seed=2)
+    t0 = time.perf_counter()
+    noisy = [render(noisy_sc, t) for t in range(F)]
+    ref_frames = [render(ref_sc, t)["radiance"] for t in range(F)]
+    torch.cuda.synchronize()
+    out["render_seconds"] = round(time.perf_counter() - t0, 3)
+    cap = 1 << 22
+    sink = torch.empty(cap * 12, dtype=torch.uint8, device=dev)
+
+    def esim_counts(frames, C):
+        l_last = torch.empty(H, W, dtype=torch.float32, device=dev)
+        counts = torch.zeros(F, H, W, dtype=torch.int32, device=dev)
+        for t, rad in enumerate(frames):
+            esim_frame(rad, l_last, counts[t], C, init=(t == 0))
+        return counts
+
+    def sim_counts(C, mode, kappa=0.0):
+        sim = Simulator(SimConfig(width=W, height=H, radius=7, frames=5, contrast=C, mode=mode, rgb=True,
+                                  event_capacity=cap, guard_kappa=kappa))
+        counts = torch.zeros(F, H, W, dtype=torch.int32, device=dev)
+        for f in noisy:
+            sim.push(f)
+            _events_to_counts(sink, sim.events_device(sink, cap), counts)
+        reg = sim.stats()["regressions"]
+        sim.close()
+        return counts, reg
+
+    out["comparison"] = {"workload": f"box scene {W}x{H}, {F} frames, 4 spp; reference: ESIM on 256-spp frames",
+                         "tau": list(taus), "by_C": {}}
+    for C in (0.25, 0.5):
+        ref = esim_counts(ref_frames, C)
+        res = {}
+        for name, counts, reg in (("ESIM", esim_counts([f["radiance"] for f in noisy], C), None),
+                                  ("WLR+ESIM", *sim_counts(C, ESIM_AD_EXHAUSTIVE)),
+                                  ("ours", *sim_counts(C, ESIM_AD_ADAPTIVE)),
+                                  ("ours+guard3", *sim_counts(C, ESIM_AD_ADAPTIVE, 3.0))):
+            q = quality(counts, ref, list(taus))
+            res[name] = {"P": [round(v, 5) for v in q["precision"]], "R": [round(v, 5) for v in q["recall"]],
+                         "F": [round(v, 5) for v in q["fscore"]], "CD": q["chamfer"], "events": q["n_gen"]}
+            if reg is not None:
+                res[name]["regressed_fraction"] = round(reg / (W * H * F), 4)
+        res["reference_events"] = q["n_ref"]
+        out["comparison"]["by_C"][str(C)] = res
+    return out
 
 
 def _quality(dev, C_values=(0.25, 0.5, 0.75, 1.0), taus=(5e-4, 1e-3, 2e-3, 5e-3, 1e-2)):
@@ -727,6 +804,7 @@ def main():
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-render", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
