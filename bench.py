@@ -722,15 +722,18 @@ def _e2e(args, scene, wl, N, stream):
     try:
         t0 = time.perf_counter()
         d2h = 0
-        step_ms = []
+        step_ms, push_ms = [], []
         for s in range(W, W + K):
             ts = time.perf_counter()
             idx = s % n
             if idx == 0:
                 sim.reset()
             sim.push(host[idx])
+            tm = time.perf_counter()
             d2h += len(sim.events()) * 12 + 64
-            step_ms.append((time.perf_counter() - ts) * 1e3)
+            te = time.perf_counter()
+            push_ms.append((tm - ts) * 1e3)
+            step_ms.append((te - ts) * 1e3)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     finally:
@@ -740,7 +743,8 @@ def _e2e(args, scene, wl, N, stream):
     return {"value": round(N * K / dt, 1), "unit": UNIT, "steps": K, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": int(d2h / K), "ms_per_step": round(dt * 1e3 / K, 3),
             "step_ms_p50": round(float(statistics.median(step_ms)), 3),
-            "step_ms_max": round(float(max(step_ms)), 3), "warmup": W,
+            "step_ms_max": round(float(max(step_ms)), 3), "push_ms_p50": round(float(statistics.median(push_ms)), 3),
+            "warmup": W,
             "form": "precision, pinned host FP16/BF16 frames"}
 
 
