@@ -678,7 +678,8 @@ class Batch:
                 if not v.is_cuda or not v.is_contiguous():
                     raise ValueError("batched frames must be contiguous device tensors")
             g = lambda k: f[k].data_ptr() if k in f else None
-            out.append(esim_ad_frame(g("radiance"), None, g("normal"), g("albedo"), g("depth"), g("features"), 0, 0))
+            out.append(esim_ad_frame(g("radiance"), g("variance"), g("normal"), g("albedo"), g("depth"),
+                                     g("features"), 0, 0))
             self._keep.append(f)
         esim_ad_batch_step(self.b, out)
         del t

@@ -28,7 +28,7 @@ def _scenes(n_frames):
     return out
 
 
-def _run(mode, lanes, tmp_path, strict=True):
+def _run(mode, lanes, tmp_path, strict=True, kappa=0.0):
     import paper_2303_02608_gb300 as m
     from paper_2303_02608_gb300 import Batch, SimConfig
     os.environ["ESIM_AD_CACHE"] = str(tmp_path / "autotune.txt")
@@ -40,9 +40,12 @@ def _run(mode, lanes, tmp_path, strict=True):
     seqs = _scenes(n_steps)
     # sequence i runs during steps [start_i, stop_i)
     spans = [(0, 9), (0, 6), (2, 9), (1, 8), (0, 9)]
-    cfgs = [SimConfig(width=w, height=h, radius=R, frames=T, contrast=C, mode=mode) for (w, h) in SHAPES]
+    cfgs = [SimConfig(width=w, height=h, radius=R, frames=T, contrast=C, mode=mode, guard_kappa=kappa)
+            for (w, h) in SHAPES]
     b = Batch(cfgs)
-    orcs = [Oracle(OracleConfig(w, h, radius=R, frames=T, channels=3, mode=mode, contrast=C)) for (w, h) in SHAPES]
+    orcs = [Oracle(OracleConfig(w, h, radius=R, frames=T, channels=3, mode=mode, contrast=C, guard_kappa=kappa))
+            for (w, h) in SHAPES]
+    keys = ("radiance", "normal", "albedo", "depth") + (("variance",) if kappa > 0 else ())
     reps = [new_report() for _ in SHAPES]
     tcount = [0] * len(SHAPES)
     try:
@@ -58,7 +61,7 @@ def _run(mode, lanes, tmp_path, strict=True):
             for i, on in enumerate(active):
                 fr = seqs[i][tcount[i]] if on else None
                 frames.append(None if fr is None else
-                              {k: fr[k].cuda() for k in ("radiance", "normal", "albedo", "depth")})
+                              {k: fr[k].cuda() for k in keys})
             b.step(frames)
             ev = b.events()
             for i, on in enumerate(active):
@@ -70,7 +73,8 @@ def _run(mode, lanes, tmp_path, strict=True):
                 w, h = SHAPES[i]
                 band = np.ones((h, w), bool)
                 g_ev = ev[ev["seq"] == i]
-                compare_frame(tcount[i], {k: fr[k].numpy() for k in ("normal", "albedo", "depth")},
+                inputs = {k: fr[k].numpy() for k in ("normal", "albedo", "depth", "radiance", "variance")}
+                compare_frame(tcount[i], inputs,
                               a.cpu().numpy().astype(np.float64), f.cpu().numpy().astype(bool), g_ev,
                               before.get(i), orcs[i], C, band, mode == ADAPTIVE, reps[i], strict=strict,
                               gpu_state_after=lambda i=i: b.get_state(i))
@@ -99,3 +103,11 @@ def test_batch_autotuner_picks_and_caches(tmp_path):
     assert stats["lanes"] in (8, 16, 32)
     text = (tmp_path / "autotune.txt").read_text()
     assert "batch r=3 T=3" in text and text.strip().endswith(str(stats["lanes"]))
+
+
+def test_batch_variance_guard(tmp_path):
+    """The optional variance guard in the batched ingest (each sequence's
+    variance plane), against per-sequence oracles with the same guard."""
+    reps, _ = _run(ADAPTIVE, 8, tmp_path, kappa=3.0)
+    assert sum(r["events"] for r in reps) > 0
+

@@ -44,3 +44,16 @@ def test_rendered_sequence_through_simulator():
         rep = run(frames, sim, orc, 0.2)
         sim.close()
         assert rep["regressed"] > 0 and rep["events"] > 0
+
+
+def test_render_empty_room_and_wide_view():
+    """No spheres, plain back wall, a view that takes in the light: still bit-identical."""
+    from paper_2303_02608_gb300 import render
+    sc = cornell(width=24, height=40, spp=2, seed=9, max_bounces=3)
+    sc.spheres = []
+    sc.checker = 0.0
+    sc.tan_half_fov_y = 0.9
+    g = {k: v.cpu().numpy() for k, v in render(sc, 4).items()}
+    o = R.render(sc, 4)
+    for k in g:
+        assert np.array_equal(g[k].view(np.uint32), o[k].astype(np.float32).view(np.uint32)), k
