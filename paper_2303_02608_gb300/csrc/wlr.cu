@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
                             accumulate(acc, buf0[si], buf1[si], u1, u2, en0, sf, cf);
                     };
                     if (interior) {
-#pragma unroll 2
+#pragma unroll 1
                         for (int q = sub; q < nq; q += g) {
                             const float4 e = table[q];
                             at(cb + __float_as_int(e.x), e.y, e.z, e.w);
