@@ -52,7 +52,7 @@ FP32_LANES_PER_SM = 128
 # capture's workload and scaling are recorded under profiles/).
 # {sha256(wlr.cu)[:16]: bytes per launch at the bench workload}; captured on
 # the sparse launch of frame 3 (same 1080p workload, unscaled)
-NCU_TRAFFIC = {"1a9b7271f993bfeb": 67868928 + 25148416}
+NCU_TRAFFIC = {"c41cfae5a49fe3a8": 68113152 + 25372416}
 
 
 def _peaks():
