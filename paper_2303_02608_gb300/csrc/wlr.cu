@@ -280,7 +280,9 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     const float en_row = -u2 * u2;
                     const int row = (sy + oy) * p.sw + sx;
                     float u1 = (float)dxlo * spx;
-#pragma unroll 3
+                    // the mixed form's larger loop body runs faster without unrolling
+                    constexpr int kRowUnroll = kMixed ? 1 : 3;
+#pragma unroll kRowUnroll
                     for (int ox = dxlo; ox <= dxhi; ++ox) {
                         at(row + ox, u1, u2, fmaf(-u1, u1, en_row));
                         u1 += spx;
