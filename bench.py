@@ -52,7 +52,7 @@ FP32_LANES_PER_SM = 128
 # capture's workload and scaling are recorded under profiles/).
 # {sha256(wlr.cu)[:16]: bytes per launch at the bench workload}; captured on
 # the sparse launch of frame 3 (same 1080p workload, unscaled)
-NCU_TRAFFIC = {"c41cfae5a49fe3a8": 68113152 + 25372416}
+NCU_TRAFFIC = {"4ef75b7e8b3f5379": 67984640 + 24835840}
 
 
 def _peaks():
@@ -752,10 +752,20 @@ def _e2e(args, scene, wl, N, stream):
         gc.enable()
     sim.close()
     h2d = sum(v.numel() * v.element_size() for v in host[0].values())
+    # the host side's own copy rate from this pool, for reading the number
+    probe = torch.empty(h2d, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    tc = time.perf_counter()
+    for _ in range(5):
+        probe.copy_(pool[:h2d], non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = 5 * h2d / (time.perf_counter() - tc) / 1e9
+    del probe
     return {"value": round(N * K / dt, 1), "unit": UNIT, "steps": K, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": int(d2h / K), "ms_per_step": round(dt * 1e3 / K, 3),
             "step_ms_p50": round(float(statistics.median(step_ms)), 3),
             "step_ms_max": round(float(max(step_ms)), 3), "push_ms_p50": round(float(statistics.median(push_ms)), 3),
+            "host_pool_pinned": bool(pool.is_pinned()), "host_copy_gbs": round(h2d_gbs, 1),
             "warmup": W,
             "form": "precision, pinned host FP16/BF16 frames"}
 
