@@ -214,10 +214,12 @@ __global__ void __launch_bounds__(kTilePix, 2)
     if (threadIdx.x == 0)
         for (int i = 0; i < L.nbuf; ++i) produce(i);
 
+    int s_fail = 0;
     for (int s = 0;; ++s) {
         const int b = s % L.nbuf;
         if (!mbar_wait_bounded(&full[b], (uint32_t)((s / L.nbuf) & 1))) {
             timed_out = true;
+            s_fail = s;
             break;
         }
         const StageInfo in = info[b];
@@ -342,6 +344,14 @@ __global__ void __launch_bounds__(kTilePix, 2)
         }
     }
 
+    if (timed_out) {
+        // give copies already issued into the other buffers (and a late one into
+        // the buffer that timed out) a bounded chance to land before the CTA exits
+        for (int k = 1; k <= L.nbuf; ++k) {
+            const int st = s_fail + (k % L.nbuf);
+            mbar_wait_bounded(&full[st % L.nbuf], (uint32_t)((st / L.nbuf) & 1), 1u << 20);
+        }
+    }
     __syncthreads();   // every thread's counter updates are in before thread 0 reads them
     finish(p, s_pairs, s_pix, s_fp64, timed_out || (threadIdx.x == 0 && !pr->ok));
 }
