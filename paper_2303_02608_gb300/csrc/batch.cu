@@ -5,8 +5,9 @@
 //   3. one ingest/test launch over the tiles of every sequence; flagged pixels
 //      of all sequences are compacted into one queue of (sequence, pixel)
 //      entries (sequence in the top 8 bits),
-//   4. one persistent regression launch over that queue (windows read through
-//      L1; lanes per pixel chosen by the autotuner),
+//   4. one persistent regression launch over that queue (per-warp window boxes
+//      staged in shared memory, as in the single-sequence sparse kernel; the
+//      work-item size, hence lanes per pixel, chosen by the autotuner),
 //   5. one event-writer launch over the chunks of every sequence.
 // Each sequence keeps its own ring, model state and maps, exactly as a
 // single-sequence context does; the per-pixel arithmetic is shared with it.
@@ -22,6 +23,7 @@
 
 #include "block_scan.cuh"
 #include "ingest_pixel.cuh"
+#include "sparse_stage.cuh"
 #include "internal.h"
 #include "wlr_math.cuh"
 
@@ -81,30 +83,43 @@ __global__ void __launch_bounds__(kTilePix) batch_ingest_kernel(BatchGlobal g)
         base += (w < ly) ? c : 0;
         total += c;
     }
-    if (threadIdx.x == 0 && total > 0) s_base = atomicAdd(&g.ctrl->flag_total, (uint32_t)total);
+    if (threadIdx.x == 0 && total > 0) {
+        atomicAdd(&g.ctrl->flag_total, (uint32_t)total);
+        // the tile's run is padded to a multiple of 4 entries (items never straddle tiles)
+        s_base = atomicAdd(&g.ctrl->list_len, (uint32_t)((total + 3) & ~3));
+    }
     __syncthreads();
+    if (total > 0 && (int)threadIdx.x < ((-total) & 3)) g.flag_list[s_base + total + threadIdx.x] = kListPad;
     if (flag) {
         const int pos = base + __popc(ballot & ((1u << lx) - 1u));
         g.flag_list[s_base + pos] = ((uint32_t)seq << kPixBits) | (uint32_t)((size_t)y * p.W + x);
     }
 }
 
-// One persistent launch over the queue of every sequence.  A CTA takes
-// 8 * (32 / kLanes) consecutive entries (neighbours in one tile of one
-// sequence); kLanes lanes split each pixel's window and are shuffle-reduced.
-template <int kLanes, bool kMixed>
+// One persistent launch over the queue of every sequence.  A warp takes an
+// item of kItem consecutive queue entries (4, 2 or 1; each tile's run is
+// padded to a multiple of 4, so an item stays inside one tile of one
+// sequence), 32 / kItem lanes per pixel (wider when the item holds fewer real
+// entries).  For each frame of the window the warp copies the bounding box of
+// its pixels' windows from that sequence's ring into its shared-memory buffer
+// (16-byte asynchronous copies; boxes that do not fit are read through L1),
+// and the lanes split each window and are shuffle-reduced.  The last stretch
+// of the queue goes out one entry at a time so that warps finish together.
+template <int kItem, bool kMixed>
 __global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, const WlrParams gp)
 {
-    constexpr int kPerWarp = 32 / kLanes;
-    constexpr int kBlock = (kTilePix / 32) * kPerWarp;
-    __shared__ float4 table[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];
+    using S = SparseStage<kMixed>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const SparseLayout L = sparse_layout(g.r, kMixed);
+    float4* table = reinterpret_cast<float4*>(sm);
+    const bool can_stage = L.buf_bytes > 0;
     __shared__ unsigned long long s_pairs, s_pix, s_fp64;
-    __shared__ uint32_t s_blk;
     const int r = g.r, side = 2 * r + 1, nq = side * side;
+    const float spx = g.s_px;
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
         const int ox = q % side - r, oy = q / side - r;
-        const float u1 = (float)ox * g.s_px, u2 = (float)oy * g.s_px;
-        table[q] = make_float4(__int_as_float((oy << 16) | (ox & 0xffff)), u1, u2, -fmaf(u1, u1, u2 * u2));
+        const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+        table[q] = make_float4(__int_as_float(oy * S::pitch + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
     }
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
@@ -112,28 +127,49 @@ __global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, c
         s_fp64 = 0ull;
     }
     __syncthreads();
-    const uint32_t n_flag = *(volatile uint32_t*)&g.ctrl->flag_total;
+    const uint32_t n_list = *(volatile uint32_t*)&g.ctrl->list_len;
+    const uint32_t tail_len = 2u * gridDim.x * (kTilePix / 32);
+    const uint32_t tail0 = n_list > tail_len ? (n_list - tail_len) & ~3u : 0u;   // multiple of 4
     const int lane = threadIdx.x & 31;
-    const int sub = lane & (kLanes - 1);
-    const int grp = lane / kLanes;
+    unsigned char* wbuf = sm + L.buf_off + (threadIdx.x >> 5) * L.buf_bytes;
+    uint4* bufm = reinterpret_cast<uint4*>(wbuf);
+    float4* buf0 = reinterpret_cast<float4*>(wbuf);
+    float4* buf1 = buf0 + S::pitch * S::rows;
     Acc acc;
     float cf[7];
     for (;;) {
-        if (threadIdx.x == 0) s_blk = atomicAdd(&g.ctrl->work_next, (uint32_t)kBlock);
-        __syncthreads();
-        const uint32_t blk = s_blk;
-        __syncthreads();
-        if (blk >= n_flag) break;
-        const uint32_t my = blk + (uint32_t)((threadIdx.x >> 5) * kPerWarp + grp);
-        const bool active = my < n_flag;
-        const uint32_t e = active ? g.flag_list[my] : 0u;
-        const int seq = (int)(e >> kPixBits);
-        const uint32_t pix = e & kPixMask;
+        uint32_t base = 0, single = 0;
+        if (lane == 0) {
+            base = atomicAdd(&g.ctrl->work_next, (uint32_t)kItem);
+            if (base >= tail0) {
+                base = tail0 + atomicAdd(&g.ctrl->tail_next, 1u);
+                single = 1;
+            }
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        single = __shfl_sync(0xffffffffu, single, 0);
+        if (base >= n_list) break;
+        const int lim = single ? 1 : kItem;
+        const uint32_t e4 = ((lane & 3) < lim) ? g.flag_list[base + (lane & 3)] : kListPad;
+        // an item's m real entries come first (padding closes a tile's run)
+        const int m = __popc(__ballot_sync(0xffffffffu, e4 != kListPad) & 0xfu);
+        if (m == 0) continue;   // a padding entry of the tail
+        const int lg = m >= 3 ? 3 : 6 - m;
+        const int gl = 1 << lg;
+        const int grp = lane >> lg, sub = lane & (gl - 1);
+        const uint32_t entry = __shfl_sync(0xffffffffu, e4, grp);
+        const bool active = grp < m;
+        // every entry of an item belongs to one sequence (entry 0 is real)
+        const int seq = (int)(__shfl_sync(0xffffffffu, e4, 0) >> kPixBits);
         const WlrParams& sp = g.steps[seq].wp;
         const int W = sp.W, H = sp.H;
         const size_t N = (size_t)W * H;
+        const uint32_t pix = active ? (entry & kPixMask) : 0u;
         const int cx = (int)(pix % (uint32_t)W), cy = (int)(pix / (uint32_t)W);
         const float* sf = kMixed ? sp.q_scale : sp.s_feat;
+        const float4* ringf = reinterpret_cast<const float4*>(sp.ring);
+        const uint4* ringm = reinterpret_cast<const uint4*>(sp.ring);
+        const int slot_t = sp.t % sp.T;
 #pragma unroll
         for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
 #pragma unroll
@@ -141,10 +177,14 @@ __global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, c
         const int dxlo = max(-r, -cx), dxhi = min(r, W - 1 - cx);
         const int dylo = max(-r, -cy), dyhi = min(r, H - 1 - cy);
         const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
+        // bounding box of the warp's windows (clipped to the image)
+        const int bx0 = __reduce_min_sync(0xffffffffu, active ? cx + dxlo : 0x7fffffff);
+        const int by0 = __reduce_min_sync(0xffffffffu, active ? cy + dylo : 0x7fffffff);
+        const int bx1 = __reduce_max_sync(0xffffffffu, active ? cx + dxhi : -1);
+        const int by1 = __reduce_max_sync(0xffffffffu, active ? cy + dyhi : -1);
+        const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
+        const bool staged = can_stage && bw > 0 && bw <= S::pitch && bh <= S::rows;   // warp-uniform
         if (active) {
-            const float4* ringf = reinterpret_cast<const float4*>(sp.ring);
-            const uint4* ringm = reinterpret_cast<const uint4*>(sp.ring);
-            const int slot_t = sp.t % sp.T;
             float c[7];
             if (kMixed) {
                 float yc;
@@ -156,8 +196,72 @@ __global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, c
             }
 #pragma unroll
             for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
-            for (int k = 0; k < sp.n_tau; ++k) {
-                const int slot = (sp.t - k) % sp.T;
+        }
+        const bool interior = nx == side && ny == side;
+        for (int k = 0; k < sp.n_tau; ++k) {
+            const int slot = (sp.t - k) % sp.T;
+            if (staged) {
+                __syncwarp();   // every lane is done with the previous frame's box
+                const size_t row0 = (size_t)by0 * W + bx0 + lane;
+                if (lane < bw) {
+                    for (int i = 0; i < bh; ++i) {
+                        const size_t gi = row0 + (size_t)i * W;
+                        if (kMixed) {
+                            cp_async16(bufm + i * S::pitch + lane, ringm + (size_t)slot * N + gi);
+                        } else {
+                            cp_async16(buf0 + i * S::pitch + lane, ringf + (size_t)(2 * slot) * N + gi);
+                            cp_async16(buf1 + i * S::pitch + lane, ringf + (size_t)(2 * slot + 1) * N + gi);
+                        }
+                    }
+                }
+                if (k + 1 < sp.n_tau) {
+                    // hint the next frame's box into L2 while this one lands and is summed
+                    const int nslot = (sp.t - k - 1) % sp.T;
+                    const int lines = (bw * S::rec + 127) >> 7;
+                    for (int j = lane; j < bh * lines; j += 32) {
+                        const int i = j / lines, l = j - i * lines;
+                        const size_t gi = (size_t)(by0 + i) * W + bx0;
+                        const char* row = kMixed
+                            ? reinterpret_cast<const char*>(ringm + (size_t)nslot * N + gi)
+                            : reinterpret_cast<const char*>(ringf + (size_t)(2 * nslot) * N + gi);
+                        prefetch_l2(row + l * 128);
+                        if (!kMixed) prefetch_l2(row + (size_t)N * 16 + l * 128);
+                    }
+                }
+                cp_async_wait_all();
+                __syncwarp();   // the box is visible to every lane of the warp
+                if (active) {
+                    const int cb = (cy - by0) * S::pitch + (cx - bx0);
+                    auto at = [&](int si, float u1, float u2, float en0) {
+                        if (kMixed)
+                            accumulate(acc, bufm[si], u1, u2, en0, sf, cf);
+                        else
+                            accumulate(acc, buf0[si], buf1[si], u1, u2, en0, sf, cf);
+                    };
+                    if (interior) {
+#pragma unroll 1
+                        for (int q = sub; q < nq; q += gl) {
+                            const float4 e = table[q];
+                            at(cb + __float_as_int(e.x), e.y, e.z, e.w);
+                        }
+                    } else {
+                        const int nvalid = nx * ny;
+                        int ox = dxlo + sub % nx;
+                        int oy = dylo + sub / nx;
+#pragma unroll 1
+                        for (int q = sub; q < nvalid; q += gl) {
+                            const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+                            at(cb + oy * S::pitch + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
+                            ox += gl;
+                            while (ox > dxhi) {
+                                ox -= nx;
+                                ++oy;
+                            }
+                        }
+                    }
+                }
+            } else if (active) {
+                // box too large for the buffer: read the windows through L1
                 const float4* __restrict__ R0 = ringf + (size_t)(2 * slot) * N + pix;
                 const float4* __restrict__ R1 = ringf + (size_t)(2 * slot + 1) * N + pix;
                 const uint4* __restrict__ RM = ringm + (size_t)slot * N + pix;
@@ -167,32 +271,23 @@ __global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, c
                     else
                         accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, en0, sf, cf);
                 };
-                if (nx == side && ny == side) {
-#pragma unroll 2
-                    for (int q = sub; q < nq; q += kLanes) {
-                        const float4 t4 = table[q];
-                        const int packed = __float_as_int(t4.x);
-                        const int ox = (int)(short)(packed & 0xffff), oy = packed >> 16;
-                        at(oy * W + ox, t4.y, t4.z, t4.w);
-                    }
-                } else {
-                    const int nvalid = nx * ny;
-                    int ox = dxlo + sub % nx;
-                    int oy = dylo + sub / nx;
-                    for (int q = sub; q < nvalid; q += kLanes) {
-                        const float u1 = (float)ox * g.s_px, u2 = (float)oy * g.s_px;
-                        at(oy * W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
-                        ox += kLanes;
-                        while (ox > dxhi) {
-                            ox -= nx;
-                            ++oy;
-                        }
+                const int nvalid = nx * ny;
+                int ox = dxlo + sub % nx;
+                int oy = dylo + sub / nx;
+#pragma unroll 1
+                for (int q = sub; q < nvalid; q += gl) {
+                    const float u1 = (float)ox * spx, u2 = (float)oy * spx;
+                    at(oy * W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
+                    ox += gl;
+                    while (ox > dxhi) {
+                        ox -= nx;
+                        ++oy;
                     }
                 }
             }
         }
 #pragma unroll
-        for (int off = kLanes >> 1; off >= 1; off >>= 1) {
+        for (int off = gl >> 1; off >= 1; off >>= 1) {
 #pragma unroll
             for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
 #pragma unroll
@@ -201,7 +296,7 @@ __global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, c
         if (active && sub == 0) {
             atomicAdd(&s_pairs, (unsigned long long)(nx * ny * sp.n_tau));
             atomicAdd(&s_pix, 1ull);
-            solve_and_emit<kMixed>(sp, acc, cx, cy, &s_fp64);
+            solve_and_emit<kMixed, true>(sp, acc, cx, cy, &s_fp64);
         }
     }
     __syncthreads();
@@ -254,16 +349,17 @@ __global__ void __launch_bounds__(kTilePix) batch_event_write_kernel(BatchGlobal
 
 typedef void (*WlrKernel)(BatchGlobal, const WlrParams);
 
+// lanes per pixel 8, 16, 32 <-> items of 4, 2, 1 queue entries
 WlrKernel pick_kernel(int lanes, bool mixed)
 {
     if (mixed) {
-        if (lanes == 8) return batch_wlr_kernel<8, true>;
-        if (lanes == 32) return batch_wlr_kernel<32, true>;
-        return batch_wlr_kernel<16, true>;
+        if (lanes == 8) return batch_wlr_kernel<4, true>;
+        if (lanes == 32) return batch_wlr_kernel<1, true>;
+        return batch_wlr_kernel<2, true>;
     }
-    if (lanes == 8) return batch_wlr_kernel<8, false>;
-    if (lanes == 32) return batch_wlr_kernel<32, false>;
-    return batch_wlr_kernel<16, false>;
+    if (lanes == 8) return batch_wlr_kernel<4, false>;
+    if (lanes == 32) return batch_wlr_kernel<1, false>;
+    return batch_wlr_kernel<2, false>;
 }
 
 const double kExp2Scale = 0.84932180028801904272;
@@ -305,6 +401,7 @@ struct esim_ad_batch {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_lanes = 0;
     int grid = 0;
+    int smem = 0;        // dynamic shared memory of the regression launch
     int lanes = 16;
     bool tuned = false;
     int tune_stage = 0;                         // candidates measured so far
@@ -499,7 +596,7 @@ cudaError_t enqueue_step_body(esim_ad_batch* b, int lanes, cudaStream_t s, bool 
     batch_ingest_kernel<<<b->total_tiles, kTilePix, 0, s>>>(g);
     rec(0, false);
     rec(1, true);
-    pick_kernel(lanes, b->mixed)<<<b->grid, kTilePix, 0, s>>>(g, global_wlr(b));
+    pick_kernel(lanes, b->mixed)<<<b->grid, kTilePix, b->smem, s>>>(g, global_wlr(b));
     rec(1, false);
     rec(2, true);
     batch_event_write_kernel<<<b->total_chunks, kTilePix, 0, s>>>(g);
@@ -637,7 +734,7 @@ esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, voi
     }
     if (cudaMalloc((void**)&b->tile_seq, tseq.size() * 2) != cudaSuccess ||
         cudaMalloc((void**)&b->chunk_seq, cseq.size() * 2) != cudaSuccess ||
-        cudaMalloc((void**)&b->flag_list, b->total_pix * 4) != cudaSuccess ||
+        cudaMalloc((void**)&b->flag_list, (b->total_pix + 4 * (size_t)b->total_tiles) * 4) != cudaSuccess ||
         cudaMalloc((void**)&b->chunk_cnt, (size_t)b->total_chunks * 4) != cudaSuccess ||
         cudaMalloc((void**)&b->chunk_off, (size_t)b->total_chunks * 8) != cudaSuccess ||
         cudaMalloc((void**)&b->events, (size_t)c0.event_capacity * sizeof(esim_ad_batch_event)) != cudaSuccess ||
@@ -657,8 +754,14 @@ esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, voi
         cudaMemcpy(b->chunk_seq, cseq.data(), cseq.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->ctrl, 0, sizeof(Ctrl)) != cudaSuccess)
         return fail(ESIM_AD_ECUDA);
+    // the regression kernels' dynamic shared memory: window table and per-warp boxes
+    b->smem = sparse_layout(b->cfg[0].radius, b->mixed).total;
+    for (int lanes : {8, 16, 32})
+        if (cudaFuncSetAttribute(pick_kernel(lanes, b->mixed), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 b->smem) != cudaSuccess)
+            return fail(ESIM_AD_ECUDA);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(16, b->mixed), kTilePix, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(16, b->mixed), kTilePix, b->smem) !=
             cudaSuccess ||
         per_sm < 1)
         per_sm = 1;

@@ -29,6 +29,7 @@
 #include "internal.h"
 #include "ptx.cuh"
 #include "wlr_math.cuh"
+#include "sparse_stage.cuh"
 
 namespace esim {
 
@@ -369,38 +370,6 @@ __global__ void __launch_bounds__(kTilePix, 2)
 // window's offsets and accumulate from shared memory; boxes too large for the
 // buffer are read through L1 instead.  Warps fetch work independently; there
 // is no block barrier inside the loop.
-template <bool kMixed>
-struct SparseStage;
-template <>
-struct SparseStage<true> {   // one 16-byte record per pixel
-    static constexpr int pitch = 32, rows = 24, rec = 16;
-};
-template <>
-struct SparseStage<false> {  // two float4 half-planes per pixel
-    static constexpr int pitch = 20, rows = 19, rec = 32;
-};
-constexpr int kSparsePerWarp = 4;                  // list entries per work item (one warp)
-constexpr uint32_t kListPad = 0xffffffffu;          // padding entry of the flagged list
-
-struct SparseLayout {
-    int buf_off, buf_bytes, total;
-};
-
-// window table [(2r+1)^2] float4 (buffer offset, u_dx, u_dy, -(u_dx^2 + u_dy^2)) | 8 warp buffers
-__host__ __device__ inline SparseLayout sparse_layout(int r, bool mixed)
-{
-    const int side = 2 * r + 1, nq = side * side;
-    const int pitch = mixed ? SparseStage<true>::pitch : SparseStage<false>::pitch;
-    const int rows = mixed ? SparseStage<true>::rows : SparseStage<false>::rows;
-    const int rec = mixed ? SparseStage<true>::rec : SparseStage<false>::rec;
-    const bool stage = side <= pitch && side <= rows;
-    SparseLayout L;
-    L.buf_bytes = stage ? pitch * rows * rec : 0;
-    L.buf_off = nq * 16;
-    L.total = L.buf_off + (kTilePix / 32) * L.buf_bytes;
-    return L;
-}
-
 template <bool kMixed>
 __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams p)
 {
