@@ -111,3 +111,31 @@ def test_mixed_form_1080p_band():
     import paper_2303_02608_gb300 as m
     rep = _run(preset("rects1080p"), 7, 5, 0.1, ADAPTIVE, 6, m.ESIM_AD_MIXED, "bf16", rows=(536, 544))
     assert rep["regressed"] > 0
+
+
+def test_storage_rounding_deviation_reported():
+    """How far storage rounding alone moves alpha: the precision form (FP16
+    log brightness, BF16 features) against the FP64 oracle on the original
+    FP32 frames (not the dequantised ones), on a dense frame of the 1080p
+    workload's band.  This is a report of the format's effect, not parity;
+    the bound only guards against gross errors."""
+    import paper_2303_02608_gb300 as m
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    sc = preset("rects1080p")
+    fr = Scene(sc).frame(0)
+    W, H = sc.width, sc.height
+    st = storage_frame(fr)
+    sim = Simulator(SimConfig(width=W, height=H, radius=7, frames=5, contrast=0.1, mode=EXHAUSTIVE,
+                              radiance_fmt=m.ESIM_AD_LOGLUMA_F16, feature_fmt=m.ESIM_AD_FEAT_BF16,
+                              precision=m.ESIM_AD_MIXED, feature_scale=FSCALE))
+    sim.push({k: v.cuda() for k, v in st["gpu"].items()})
+    a_gpu = sim.denoised()[0].cpu().numpy().astype(np.float64)
+    sim.close()
+    rows = (536, 544)
+    orc = Oracle(OracleConfig(W, H, radius=7, frames=5, channels=3, mode=EXHAUSTIVE, contrast=0.1))
+    orc.push(fr, rows)
+    a_ref = orc.outputs()["alpha"][rows[0]:rows[1]]
+    dev = np.abs(a_gpu[rows[0]:rows[1]] - a_ref)
+    print(f"storage-rounding deviation of alpha on rows {rows}: max {dev.max():.3e} "
+          f"p99 {np.percentile(dev, 99):.3e} mean {dev.mean():.3e}")
+    assert dev.mean() < 1e-2 and np.isfinite(dev).all()
