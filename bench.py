@@ -46,6 +46,14 @@ WORKLOADS = {
 FLOP_PER_NEIGHBOUR = 162
 FLOP_PER_SOLVE = 700
 FP32_LANES_PER_SM = 128
+# Second-order regression (55 unknowns + the log brightness column): per
+# (pixel, neighbour) pair the scaled offsets and weight (33), the 45 products
+# and the sqrt(w) scaling of 56 entries (101), and the 56 x 57 / 2 = 1596
+# entries of the augmented Gram (3192) -> 3326 flop; per pixel the ridge and
+# equilibration (3300) and the Cholesky of the augmented 56 x 56 system
+# (2 x 55 x 56 x 57 / 6 trailing-update flop + column scaling) -> 63300 flop.
+FLOP_PER_NEIGHBOUR_2 = 3326
+FLOP_PER_SOLVE_2 = 63300
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the sparse
 # regression kernel from one ncu capture, valid only while that kernel's
@@ -62,6 +70,13 @@ def _sparse_kernel_hash() -> str:
     a = src.index("__global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel")
     b = src.index("int wlr_sparse_smem(", a)
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
+def _fp32_peak(dev) -> float:
+    """FP32 FMA peak in TFLOP/s: SMs x 128 lanes x 2 flop x the maximum SM clock."""
+    import torch
+    sm_mhz = float(_peaks()[0].get("sm_max_mhz", 2070.0))
+    return torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def _peaks():
@@ -335,7 +350,7 @@ def run_ours(args):
     peaks, peak_src = _peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
+    fp32_peak = _fp32_peak(dev)
 
     def roofline(prof):
         n_launch = prof["launches"]["wlr_emit"]
@@ -394,6 +409,8 @@ def run_ours(args):
         line["e2e"] = _e2e(args, scene, wl, N, stream)
     if rank == 0 and not args.no_diff:
         line["differentiation_form"] = _differentiation(dev)
+    if rank == 0 and not args.no_second_order:
+        line["second_order_form"] = _second_order(dev, fp32_peak)
     if rank == 0 and not args.no_quality:
         line["quality"] = _quality(dev)
     if rank == 0 and not args.no_render:
@@ -691,6 +708,84 @@ def _differentiation(dev, reps=5):
             "grad_bandwidth_finite": bool(torch.isfinite(b.grad).all())}
 
 
+def _window_pairs(W, H, F, r, T):
+    """(pixel, neighbour) pairs of a dense sequence with clipped windows."""
+    sx = sum(min(W, x + r + 1) - max(0, x - r) for x in range(W))
+    sy = sum(min(H, y + r + 1) - max(0, y - r) for y in range(H))
+    return sum(min(T, f + 1) for f in range(F)) * sx * sy
+
+
+def _second_order(dev, fp32_peak, reps=5, warmup=3, r=3, T=3):
+    """Second-order dense regression on the differentiation workload (512x512
+    RGB, 16 frames, 2 spp, 7x7x3 window): throughput, FP32 roofline, a sampled
+    check against the FP64 oracle, the oracle's CPU rate on that sample, and
+    the denoising error of first- and second-order regression against the clean
+    log luminance."""
+    import torch
+    from paper_2303_02608_gb300 import esim_ad_wlr2_workspace_size, make_wlr_desc, wlr, wlr2
+    from scenes import Scene, preset
+    sc = Scene(preset("rects512"))
+    fr = [sc.frame(t, dev) for t in range(sc.cfg.frames)]
+    rad = torch.stack([f["radiance"] for f in fr]).contiguous()
+    feat = torch.stack([torch.cat([f["normal"], f["depth"][None], f["albedo"]]) for f in fr]).contiguous()
+    F, _, H, W = rad.shape
+    ws = torch.empty(esim_ad_wlr2_workspace_size(make_wlr_desc(W, H, F, r, T)), dtype=torch.uint8, device=dev)
+    ones = torch.ones(7, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times = []
+    for it in range(reps + warmup):
+        torch.cuda.synchronize()
+        ev[0].record()
+        alpha2 = wlr2(rad, feat, ones, radius=r, frames=T, workspace=ws)
+        ev[1].record()
+        torch.cuda.synchronize()
+        if it >= warmup:
+            times.append(ev[0].elapsed_time(ev[1]))
+    ms = statistics.median(times)
+    n_pf = F * H * W
+    pairs = _window_pairs(W, H, F, r, T)
+    flops = pairs * FLOP_PER_NEIGHBOUR_2 + n_pf * FLOP_PER_SOLVE_2
+    ach = flops / (ms * 1e-3) / 1e12
+    out = {"workload": "rects512: 512x512 RGB, 16 frames, 2 spp, 7x7x3 window, dense (every pixel-frame)",
+           "value": round(n_pf / (ms * 1e-3), 1), "unit": "pixel-frames/s", "ms_per_call": round(ms, 3),
+           "gpu_launches_per_call": 2,
+           "roofline": {"kernel": "wlr2_kernel (+ the 32 B/pixel-frame pack it reads)", "bound": "alu",
+                        "unit": "TFLOP/s", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
+                        "frac": round(ach / fp32_peak, 4), "flops_per_call": flops,
+                        "neighbour_pairs": pairs}}
+    # FP64 oracle on a bounded sample of centres (frames 2..15), timed on the host
+    import numpy as np
+    from oracle import wlr2 as O2
+    rng = np.random.default_rng(0)
+    pts = [(int(rng.integers(2, F)), int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(2000)]
+    rad_c, feat_c = rad.cpu().numpy(), feat.cpu().numpy()
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter, cores = threadpool_limits(1), 1
+    except ImportError:                      # LAPACK keeps its default threading
+        limiter, cores = None, os.cpu_count()
+    t0 = time.perf_counter()
+    ref = O2.wlr2(rad_c, feat_c, radius=r, frames=T, centres=pts)
+    dt = time.perf_counter() - t0
+    if limiter is not None:
+        limiter.unregister()
+    a_c = alpha2.cpu().double().numpy()
+    got = np.array([a_c[t, y, x] for t, y, x in pts])
+    out["max_abs_err_vs_oracle_sample"] = float(np.abs(got - ref).max())
+    out["cpu_baseline"] = {"value": round(len(pts) / dt, 1), "unit": "pixel-frames/s", "cores": cores,
+                           "kind": "oracle", "sample": f"{len(pts)} random centres of frames 2-15 "
+                                                       "(numpy/LAPACK QR per centre)"}
+    Yc = sum(w * torch.stack([f["clean"][i] for f in fr]) for i, w in enumerate(REC709))
+    target = torch.log(Yc + 1e-3)
+    alpha1 = wlr(rad, feat, ones, radius=r, frames=T)
+    y_noisy = torch.log(sum(w * rad[:, i] for i, w in enumerate(REC709)) + 1e-3)
+    out["mse_vs_clean_log_luminance"] = {
+        "noisy_input": float(((y_noisy - target) ** 2).mean()),
+        "first_order": float(((alpha1 - target) ** 2).mean()),
+        "second_order": float(((alpha2 - target) ** 2).mean())}
+    return out
+
+
 def _dequantised_cpu(sf):
     """Storage-format frame widened to float32 on the host (what the oracle reads)."""
     import torch
@@ -839,11 +934,19 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-render", action="store_true")
+    ap.add_argument("--no-second-order", action="store_true")
+    ap.add_argument("--form", choices=["second-order"], default=None,
+                    help="run only that form's measurement and print its JSON object")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "second-order":
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps(_second_order(dev, _fp32_peak(dev), warmup=args.warmup)), flush=True)
     else:
         run_ours(args)
 

@@ -355,6 +355,33 @@ esim_ad_status esim_ad_wlr_backward(const esim_ad_wlr_desc* d, const float* radi
                                     float* g_bandwidth, void* workspace, void* cuda_stream);
 
 /*
+ * Second-order form: the dense regression of Eqs. 4-5 with the Taylor
+ * expansion of Eq. 3 carried to second order, the non-linear regression that
+ * the paper's conclusion (Section 5) names as its extension.  Per frame t and
+ * pixel c, over the same window and weights as esim_ad_wlr_forward, it fits
+ *     y ~ alpha + beta^T d + sum_{a<=b} gamma_ab d_a d_b,   d = x^i - x^c
+ * (55 unknowns over the 9-D feature: coordinate offset (q - c)/r, normal,
+ * depth, albedo), minimising sum_i w^i (y^i - theta^T z^i)^2 +
+ * lambda W sum_{k>=1} theta_k^2 (ridge on every coefficient but alpha, in
+ * these natural units), and returns alpha.  Stateless and dense: every pixel of
+ * every frame.  FP32 accumulation and Cholesky; the window's neighbours are
+ * summed in up to eight interleaved partial sums, so results are deterministic.
+ *
+ * radiance  [F][C][H][W] float32, C = 1 or 3 (device, input)
+ * features  [F][7][H][W] float32: normal xyz, depth, albedo rgb (device, input)
+ * bandwidth [7] float32 b_j > 0 (device, input)
+ * alpha     [F][H][W] float32 (device, output)
+ * workspace esim_ad_wlr2_workspace_size bytes (device, caller-owned scratch:
+ *           the packed log brightness and features, 32 bytes per pixel-frame)
+ * Asynchronous on cuda_stream.  EINVAL on a bad desc, a NULL pointer or more
+ * than 65535 frames; ECUDA if a launch fails.
+ */
+size_t esim_ad_wlr2_workspace_size(const esim_ad_wlr_desc* d);
+esim_ad_status esim_ad_wlr2_forward(const esim_ad_wlr_desc* d, const float* radiance,
+                                    const float* features, const float* bandwidth, float* alpha,
+                                    void* workspace, void* cuda_stream);
+
+/*
  * Write the events of one frame from a map of signed per-pixel event counts
  * (p*n, as Eq. 1 emission produces), in canonical order (row, column, repeat),
  * without allocating anything.  The paper has no counterpart: this is a

@@ -47,7 +47,7 @@ EXPORTS = (
     "esim_ad_batch_reset_sequence", "esim_ad_batch_denoised", "esim_ad_batch_get_state",
     "esim_ad_batch_stats", "esim_ad_batch_profile_enable", "esim_ad_batch_profile_get",
     "esim_ad_batch_destroy", "esim_ad_esim_frame", "esim_ad_quality_workspace_size", "esim_ad_quality",
-    "esim_ad_render",
+    "esim_ad_render", "esim_ad_wlr2_workspace_size", "esim_ad_wlr2_forward",
 )
 
 
@@ -146,6 +146,10 @@ def load_library():
     lib.esim_ad_wlr_workspace_size.argtypes = [ctypes.POINTER(esim_ad_wlr_desc)]
     lib.esim_ad_wlr_forward.restype = st
     lib.esim_ad_wlr_forward.argtypes = [ctypes.POINTER(esim_ad_wlr_desc), P, P, P, P, P, P, P]
+    lib.esim_ad_wlr2_workspace_size.restype = ctypes.c_size_t
+    lib.esim_ad_wlr2_workspace_size.argtypes = [ctypes.POINTER(esim_ad_wlr_desc)]
+    lib.esim_ad_wlr2_forward.restype = st
+    lib.esim_ad_wlr2_forward.argtypes = [ctypes.POINTER(esim_ad_wlr_desc), P, P, P, P, P, P]
     lib.esim_ad_wlr_backward.restype = st
     lib.esim_ad_wlr_backward.argtypes = [ctypes.POINTER(esim_ad_wlr_desc), P, P, P, P, P, P, P, P, P]
     lib.esim_ad_batch_init.restype = st
@@ -427,6 +431,42 @@ def esim_ad_wlr_backward(desc, radiance: int, features: int, bandwidth: int, sav
     _check(load_library().esim_ad_wlr_backward(ctypes.byref(desc), *(ctypes.c_void_p(x) for x in (
         radiance, features, bandwidth, saved, g_alpha, g_radiance, g_bandwidth, workspace,
         cuda_stream or None))), "esim_ad_wlr_backward")
+
+
+def esim_ad_wlr2_workspace_size(desc: esim_ad_wlr_desc) -> int:
+    return int(load_library().esim_ad_wlr2_workspace_size(ctypes.byref(desc)))
+
+
+def esim_ad_wlr2_forward(desc, radiance: int, features: int, bandwidth: int, alpha: int, workspace: int,
+                         cuda_stream: int = 0) -> None:
+    _check(load_library().esim_ad_wlr2_forward(ctypes.byref(desc), *(ctypes.c_void_p(x) for x in (
+        radiance, features, bandwidth, alpha, workspace, cuda_stream or None))), "esim_ad_wlr2_forward")
+
+
+def wlr2(radiance, features, bandwidth=None, radius: int = 3, frames: int = 3, h: float = 1.0,
+         log_eps: float = 1e-3, ridge: float = 1e-4, workspace=None):
+    """Second-order dense regression: radiance [F][C][H][W], features [F][7][H][W]
+    (normal xyz, depth, albedo rgb), bandwidth [7] (default all 1) -> alpha
+    [F][H][W], all float32 device tensors.  `workspace` (uint8, at least
+    esim_ad_wlr2_workspace_size bytes) may be passed to reuse one across calls."""
+    import torch
+    F_, C, H, W = radiance.shape
+    if C not in (1, 3) or features.shape != (F_, 7, H, W):
+        raise ValueError("wlr2: radiance [F][1|3][H][W] and features [F][7][H][W]")
+    dev = radiance.device
+    if bandwidth is None:
+        bandwidth = torch.ones(7, dtype=torch.float32, device=dev)
+    radiance, features, bandwidth = (t.contiguous().float() for t in (radiance, features, bandwidth))
+    desc = make_wlr_desc(W, H, F_, radius, frames, C == 3, h, log_eps, ridge)
+    need = esim_ad_wlr2_workspace_size(desc)
+    if need == 0:
+        raise ValueError("wlr2: invalid sizes or parameters")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    alpha = torch.empty(F_, H, W, dtype=torch.float32, device=dev)
+    esim_ad_wlr2_forward(desc, radiance.data_ptr(), features.data_ptr(), bandwidth.data_ptr(), alpha.data_ptr(),
+                         workspace.data_ptr(), torch.cuda.current_stream(dev).cuda_stream)
+    return alpha
 
 
 def _wlr_function():

@@ -1,0 +1,383 @@
+// Second-order form: the dense weighted local regression of Eqs. 4-5 with the
+// Taylor expansion of Eq. 3 carried one order further (the non-linear
+// regression that Section 5 names as the extension).  Per frame t and centre c
+// the design row of neighbour i is built from the scaled offset u = s d
+// (s_j = k / (h b_j), k = sqrt(log2(e) / 2), so w = 2^-|u|^2 is the product
+// Gaussian of Eq. 5):
+//
+//     z = (u_a u_b for a <= b [45], u [9], 1),   55 unknowns,
+//
+// and the log brightness y rides along as a 56th entry, so one symmetric
+// 56 x 56 Gram G = sum_i w_i [z;y][z;y]^T holds the normal matrix and the
+// right-hand side.  The ridge lambda W |theta_k|^2 on every coefficient but the
+// intercept is added in natural units (lambda W s_a^2 s_b^2 on the diagonal of
+// a quadratic unknown, lambda W s_a^2 on a linear one).  With the intercept
+// ordered last among the unknowns, the Cholesky factor of the augmented
+// (equilibrated) Gram gives alpha = L[55][54] / L[54][54] directly: no back
+// substitution.
+//
+// Layout of the work: a CTA of 288 threads holds 8 slots of 36 threads.  The
+// 56 x 56 Gram is cut into 8 x 8 blocks of 7; the 36 blocks on and above the
+// block diagonal go one per thread, a 7 x 7 register tile (49 FP32
+// accumulators) fed by two 7-vectors from shared memory per neighbour.  A round
+// builds sqrt(w) z for 32 neighbours per slot in shared memory, then every
+// thread runs its tile over them.  G slots share one pixel, each summing an
+// interleaved G-th of the window's neighbour batches (G grows with the window,
+// so no accumulator sums more than a few hundred terms in FP32); their partial
+// Grams are added in slot order, so results do not depend on scheduling.  One
+// warp per pixel then equilibrates (Jacobi) and factors the packed Gram in
+// shared memory, spreading each step's trailing update over the lanes.
+#include <stdlib.h>
+
+#include "esim_ad.h"
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace esim {
+namespace {
+
+constexpr int kNQ = 55;                    // unknowns
+constexpr int kNA = 56;                    // unknowns + log brightness
+constexpr int kNB = 36;                    // 7 x 7 tiles on and above the block diagonal
+constexpr int kSlots = 8;                  // 36-thread slots per CTA
+constexpr int kThreads = kSlots * kNB;     // 288
+constexpr int kBatch = 32;                 // neighbours per slot per round
+constexpr int kRow4 = 17;                  // float4 per neighbour: [2 halves][8 blocks] + 1 pad
+constexpr int kTri = kNA * (kNA + 1) / 2;  // 1596 entries of the packed lower triangle
+constexpr size_t kSmemZ = (size_t)kSlots * kBatch * kRow4 * sizeof(float4);  // 69,632 B
+static_assert((size_t)kSlots * kTri * sizeof(float) <= kSmemZ, "Grams must fit in the neighbour buffer");
+
+constexpr float kExp2Scale = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
+
+// Packed lower triangle, column-major: column c holds rows c..55.
+__host__ __device__ constexpr int tri_off(int c) { return c * kNA - c * (c - 1) / 2; }
+
+// Quadratic unknown q (0..44) -> feature pair (a, b), a <= b, a-major order.
+__host__ __device__ constexpr int pair_a(int q)
+{
+    int a = 0;
+    while (q >= 9 - a) { q -= 9 - a; ++a; }
+    return a;
+}
+__host__ __device__ constexpr int pair_b(int q)
+{
+    int a = 0;
+    while (q >= 9 - a) { q -= 9 - a; ++a; }
+    return a + q;
+}
+
+// Entry Z of the augmented row [z; y] (before the sqrt(w) factor).
+template <int Z>
+__device__ __forceinline__ float zval(const float (&u)[9], float y)
+{
+    if constexpr (Z < 45) return u[pair_a(Z)] * u[pair_b(Z)];
+    else if constexpr (Z < 54) return u[Z - 45];
+    else if constexpr (Z == 54) return 1.0f;
+    else return y;
+}
+
+// Element m (0..7, 7 = pad) of block b sits in float4 slot (m / 4) * 8 + b,
+// lane m % 4: the 8 blocks of one half fill a 128-byte row of banks.
+template <int S>
+__device__ __forceinline__ void store_row(float4* row, const float (&u)[9], float y, float sw)
+{
+    constexpr int h = S / 8, b = S % 8, z0 = 7 * b + 4 * h;
+    float4 v;
+    v.x = zval<z0>(u, y) * sw;
+    v.y = zval<z0 + 1>(u, y) * sw;
+    v.z = zval<z0 + 2>(u, y) * sw;
+    if constexpr (h == 0) v.w = zval<z0 + 3>(u, y) * sw;
+    else v.w = 0.0f;
+    row[S] = v;
+    if constexpr (S + 1 < 16) store_row<S + 1>(row, u, y, sw);
+}
+
+struct W2Params {
+    int W, H, F, r, T, rgb, tiles_x;
+    float h, log_eps, ridge;
+    const float* radiance;   // [F][C][H][W]
+    const float* features;   // [F][7][H][W]
+    const float* bandwidth;  // [7]
+    float4* packed;          // [F][2][H][W]: (y, normal xyz), (depth, albedo rgb)
+    float* alpha;            // [F][H][W]
+};
+
+__global__ void __launch_bounds__(kTilePix) wlr2_pack_kernel(W2Params p)
+{
+    const size_t N = (size_t)p.W * p.H;
+    const int f = blockIdx.y;
+    const int x = (blockIdx.x % p.tiles_x) * kTileX + (threadIdx.x & 31);
+    const int y = (blockIdx.x / p.tiles_x) * kTileY + (threadIdx.x >> 5);
+    if (x >= p.W || y >= p.H) return;
+    const size_t i = (size_t)y * p.W + x;
+    const float* rad = p.radiance + (size_t)f * (p.rgb ? 3 : 1) * N;
+    const float Y = p.rgb ? 0.2126f * rad[i] + 0.7152f * rad[N + i] + 0.0722f * rad[2 * N + i] : rad[i];
+    const float* ft = p.features + (size_t)f * 7 * N;
+    float4* out = p.packed + (size_t)f * 2 * N;
+    out[i] = make_float4(logf(Y + p.log_eps), ft[i], ft[N + i], ft[2 * N + i]);
+    out[N + i] = make_float4(ft[3 * N + i], ft[4 * N + i], ft[5 * N + i], ft[6 * N + i]);
+}
+
+// G slots per pixel, 8 / G pixels per CTA along one image row.
+template <int G>
+__global__ void __launch_bounds__(kThreads, 2) wlr2_kernel(W2Params p)
+{
+    constexpr int P = kSlots / G;
+    extern __shared__ float4 zbuf[];           // [kSlots][kBatch][kRow4]; then [kSlots][kTri] floats
+    __shared__ uint16_t s_tab[kTri];           // packed index -> row | col << 8
+    __shared__ float s_s2[kNQ];                // squared natural-unit scale of each unknown
+    __shared__ float s_sf[7];
+    __shared__ float s_dsc[P][kNA];
+
+    const int tid = threadIdx.x;
+    const size_t N = (size_t)p.W * p.H;
+    const int nxc = (p.W + P - 1) / P;
+    const int xc = (int)(blockIdx.x % (unsigned)nxc);
+    const int cy = (int)((blockIdx.x / (unsigned)nxc) % (unsigned)p.H);
+    const int f = (int)(blockIdx.x / ((unsigned)nxc * (unsigned)p.H));
+    const int x0 = xc * P;
+
+    if (tid < kNA)
+        for (int R = tid; R < kNA; ++R) s_tab[tri_off(tid) + R - tid] = (uint16_t)(R | (tid << 8));
+    if (tid < 7) s_sf[tid] = kExp2Scale / (p.h * p.bandwidth[tid]);
+    __syncthreads();
+    if (tid < kNQ) {
+        const float sc = kExp2Scale / p.h;
+        auto sdim = [&](int a) { return a < 2 ? sc : s_sf[a - 2]; };
+        float s2 = 0.0f;
+        if (tid < 45) {
+            const float v = sdim(pair_a(tid)) * sdim(pair_b(tid));
+            s2 = v * v;
+        } else if (tid < 54) {
+            const float v = sdim(tid - 45);
+            s2 = v * v;
+        }
+        s_s2[tid] = s2;
+    }
+
+    // builder role: slot cs, neighbour j of each round
+    const int cs = tid >> 5, j = tid & 31;
+    const int b_pix = x0 + cs / G, b_sub = cs % G;
+    const bool builder = tid < kSlots * kBatch;
+    const bool b_ok = builder && b_pix < p.W;
+    float cf[7], sf[7];
+    const float s_px = kExp2Scale / (p.h * (float)p.r);
+    if (b_ok) {
+        const size_t ci = (size_t)cy * p.W + b_pix;
+        const float4 c0 = p.packed[(size_t)f * 2 * N + ci];
+        const float4 c1 = p.packed[((size_t)f * 2 + 1) * N + ci];
+        const float xcv[7] = {c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            sf[k] = s_sf[k];
+            cf[k] = xcv[k] * sf[k];
+        }
+    }
+
+    // accumulator role: slot, 7 x 7 tile (bi, bj) of the block grid
+    const int slot = tid / kNB;
+    int bi = 0, bj = tid - slot * kNB;
+    while (bj >= 8 - bi) { bj -= 8 - bi; ++bi; }
+    bj += bi;
+    float acc[7][7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc[i][k] = 0.0f;
+
+    const int S = 2 * p.r + 1;
+    const int t_eff = min(p.T, f + 1);
+    const int M = S * S * t_eff;
+    const int n_batch = (M + kBatch - 1) / kBatch;
+    const int rounds = (n_batch + G - 1) / G;
+    for (int q = 0; q < rounds; ++q) {
+        if (builder) {
+            float4* row = zbuf + ((size_t)cs * kBatch + j) * kRow4;
+            const int n = (q * G + b_sub) * kBatch + j;
+            bool ok = b_ok && n < M;
+            int qx = 0, qy = 0, tau = 0;
+            if (ok) {
+                const int ti = n / (S * S), rem = n - ti * S * S;
+                const int oy = rem / S - p.r, ox = rem - (rem / S) * S - p.r;
+                tau = f - t_eff + 1 + ti;
+                qx = b_pix + ox;
+                qy = cy + oy;
+                ok = qx >= 0 && qx < p.W && qy >= 0 && qy < p.H;
+                if (ok) {
+                    const size_t qi = (size_t)qy * p.W + qx;
+                    const float4 h0 = __ldg(p.packed + (size_t)tau * 2 * N + qi);
+                    const float4 h1 = __ldg(p.packed + ((size_t)tau * 2 + 1) * N + qi);
+                    const float xv[7] = {h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                    float u[9];
+                    u[0] = (float)ox * s_px;
+                    u[1] = (float)oy * s_px;
+                    float e = fmaf(u[0], u[0], u[1] * u[1]);
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) {
+                        u[2 + k] = fmaf(xv[k], sf[k], -cf[k]);
+                        e = fmaf(u[2 + k], u[2 + k], e);
+                    }
+                    store_row<0>(row, u, h0.x, ex2_approx(-0.5f * e));   // sqrt(w) = 2^(-|u|^2 / 2)
+                }
+            }
+            if (!ok) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) row[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        }
+        __syncthreads();
+        const float4* base = zbuf + (size_t)slot * kBatch * kRow4;
+#pragma unroll 2
+        for (int n = 0; n < kBatch; ++n) {
+            const float4* row = base + n * kRow4;
+            const float4 r0 = row[bi], r1 = row[8 + bi], c0 = row[bj], c1 = row[8 + bj];
+            const float rv[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
+            const float cv[7] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z};
+#pragma unroll
+            for (int i = 0; i < 7; ++i)
+#pragma unroll
+                for (int k = 0; k < 7; ++k) acc[i][k] = fmaf(rv[i], cv[k], acc[i][k]);
+        }
+        __syncthreads();
+    }
+
+    // partial Gram of each slot, packed lower triangle (entry (7bj+k, 7bi+i))
+    float* grams = reinterpret_cast<float*>(zbuf);
+    {
+        float* g = grams + (size_t)slot * kTri;
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const int R = 7 * bj + k, C = 7 * bi + i;
+                if (R >= C) g[tri_off(C) + R - C] = acc[i][k];
+            }
+    }
+    __syncthreads();
+    if constexpr (G > 1) {
+        for (int e = tid; e < P * kTri; e += kThreads) {
+            const int pp = e / kTri, k = e - pp * kTri;
+            float* g0 = grams + (size_t)pp * G * kTri + k;
+            float v = g0[0];
+#pragma unroll
+            for (int s = 1; s < G; ++s) v += g0[(size_t)s * kTri];
+            g0[0] = v;
+        }
+        __syncthreads();
+    }
+
+    // one warp per pixel: ridge, Jacobi equilibration, Cholesky of the augmented Gram
+    const int w = tid >> 5, lane = tid & 31;
+    if (w >= P || x0 + w >= p.W) return;
+    float* A = grams + (size_t)w * G * kTri;
+    float* dsc = s_dsc[w];
+    const float lw = p.ridge * A[tri_off(54)];   // lambda W
+    for (int a = lane; a < 54; a += 32) A[tri_off(a)] = fmaf(lw, s_s2[a], A[tri_off(a)]);
+    __syncwarp();
+    for (int a = lane; a < kNA; a += 32) dsc[a] = a < kNQ ? rsqrtf(A[tri_off(a)]) : 1.0f;
+    __syncwarp();
+    for (int e = lane; e < kTri; e += 32) {
+        const uint32_t rc = s_tab[e];
+        A[e] *= dsc[rc & 0xffu] * dsc[rc >> 8];
+    }
+    __syncwarp();
+    for (int jc = 0; jc < kNQ; ++jc) {
+        const int oj = tri_off(jc);
+        const float piv = sqrtf(fmaxf(A[oj], 1e-30f));
+        const float inv = 1.0f / piv;
+        __syncwarp();
+        for (int i = jc + 1 + lane; i < kNA; i += 32) A[oj + i - jc] *= inv;
+        if (lane == 0) A[oj] = piv;
+        __syncwarp();
+#pragma unroll 4
+        for (int e = tri_off(jc + 1) + lane; e < kTri; e += 32) {
+            const uint32_t rc = s_tab[e];
+            A[e] = fmaf(-A[oj + (int)(rc & 0xffu) - jc], A[oj + (int)(rc >> 8) - jc], A[e]);
+        }
+        __syncwarp();
+    }
+    if (lane == 0)
+        p.alpha[(size_t)f * N + (size_t)cy * p.W + x0 + w] = A[tri_off(54) + 1] / A[tri_off(54)] * dsc[54];
+}
+
+bool desc_ok(const esim_ad_wlr_desc* d)
+{
+    return d && d->struct_size == sizeof(esim_ad_wlr_desc) && d->width >= 1 && d->height >= 1 &&
+           d->sequence >= 1 && d->radius >= 1 && d->radius <= kMaxRadius && d->frames >= 1 &&
+           d->frames <= kMaxFrames && (d->radiance_fmt == ESIM_AD_LUMA_F32 || d->radiance_fmt == ESIM_AD_RGB_F32) &&
+           d->h > 0.0f && d->ridge > 0.0f && d->log_eps >= 0.0f;
+}
+
+// Slots per pixel: the largest of 1, 2, 4, 8 that leaves each slot at least
+// 128 of the window's neighbours.  ESIM_AD_WLR2_GROUPS overrides it.
+int groups_for(const esim_ad_wlr_desc* d)
+{
+    if (const char* e = getenv("ESIM_AD_WLR2_GROUPS")) {
+        const int g = atoi(e);
+        if (g == 1 || g == 2 || g == 4 || g == 8) return g;
+    }
+    const int S = 2 * d->radius + 1, M = S * S * d->frames;
+    int g = 1;
+    while (g < 8 && M >= 2 * g * 128) g *= 2;
+    return g;
+}
+
+template <int G>
+cudaError_t launch(const W2Params& p, cudaStream_t s)
+{
+    constexpr int P = kSlots / G;
+    cudaError_t e = cudaFuncSetAttribute(wlr2_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemZ);
+    if (e != cudaSuccess) return e;
+    const unsigned long long n = (unsigned long long)p.F * p.H * ((p.W + P - 1) / P);
+    if (n == 0 || n > 0x7fffffffull) return cudaErrorInvalidValue;
+    wlr2_kernel<G><<<(unsigned)n, kThreads, kSmemZ, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace esim
+
+using namespace esim;
+
+extern "C" size_t esim_ad_wlr2_workspace_size(const esim_ad_wlr_desc* d)
+{
+    if (!desc_ok(d)) return 0;
+    return (size_t)d->sequence * 2 * (size_t)d->width * d->height * sizeof(float4);
+}
+
+extern "C" esim_ad_status esim_ad_wlr2_forward(const esim_ad_wlr_desc* d, const float* radiance,
+                                               const float* features, const float* bandwidth, float* alpha,
+                                               void* workspace, void* cuda_stream)
+{
+    if (!desc_ok(d) || !radiance || !features || !bandwidth || !alpha || !workspace) return ESIM_AD_EINVAL;
+    W2Params p;
+    p.W = d->width;
+    p.H = d->height;
+    p.F = d->sequence;
+    p.r = d->radius;
+    p.T = d->frames;
+    p.rgb = d->radiance_fmt == ESIM_AD_RGB_F32 ? 1 : 0;
+    p.tiles_x = (d->width + kTileX - 1) / kTileX;
+    p.h = d->h;
+    p.log_eps = d->log_eps;
+    p.ridge = d->ridge;
+    p.radiance = radiance;
+    p.features = features;
+    p.bandwidth = bandwidth;
+    p.packed = static_cast<float4*>(workspace);
+    p.alpha = alpha;
+    if (d->sequence > 65535) return ESIM_AD_EINVAL;   // frames index the pack grid's y dimension
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const dim3 pack_grid(p.tiles_x * ((d->height + kTileY - 1) / kTileY), d->sequence);
+    wlr2_pack_kernel<<<pack_grid, kTilePix, 0, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return ESIM_AD_ECUDA;
+    cudaError_t e;
+    switch (groups_for(d)) {
+        case 1: e = launch<1>(p, s); break;
+        case 2: e = launch<2>(p, s); break;
+        case 4: e = launch<4>(p, s); break;
+        default: e = launch<8>(p, s); break;
+    }
+    if (e == cudaErrorInvalidValue) return ESIM_AD_EINVAL;
+    return e == cudaSuccess ? ESIM_AD_OK : ESIM_AD_ECUDA;
+}
