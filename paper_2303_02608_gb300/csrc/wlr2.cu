@@ -43,14 +43,10 @@ constexpr int kSlots = 8;                  // 36-thread slots per CTA
 constexpr int kThreads = kSlots * kNB;     // 288
 constexpr int kBatch = 32;                 // neighbours per slot per round
 constexpr int kRow4 = 17;                  // float4 per neighbour: [2 halves][8 blocks] + 1 pad
-constexpr int kTri = kNA * (kNA + 1) / 2;  // 1596 entries of the packed lower triangle
 constexpr size_t kSmemZ = (size_t)kSlots * kBatch * kRow4 * sizeof(float4);  // 69,632 B
-static_assert((size_t)kSlots * kTri * sizeof(float) <= kSmemZ, "Grams must fit in the neighbour buffer");
+static_assert((size_t)kSlots * kNB * 49 * sizeof(float) <= kSmemZ, "partial tiles must fit in the neighbour buffer");
 
 constexpr float kExp2Scale = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
-
-// Packed lower triangle, column-major: column c holds rows c..55.
-__host__ __device__ constexpr int tri_off(int c) { return c * kNA - c * (c - 1) / 2; }
 
 // Quadratic unknown q (0..44) -> feature pair (a, b), a <= b, a-major order.
 __host__ __device__ constexpr int pair_a(int q)
@@ -120,14 +116,16 @@ __global__ void __launch_bounds__(kTilePix) wlr2_pack_kernel(W2Params p)
 
 // G slots per pixel, 8 / G pixels per CTA along one image row.
 template <int G>
-__global__ void __launch_bounds__(kThreads, 2) wlr2_kernel(W2Params p)
+__global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
 {
-    constexpr int P = kSlots / G;
-    extern __shared__ float4 zbuf[];           // [kSlots][kBatch][kRow4]; then [kSlots][kTri] floats
-    __shared__ uint16_t s_tab[kTri];           // packed index -> row | col << 8
+    constexpr int P = kSlots / G;              // pixels per CTA
+    extern __shared__ float4 zbuf[];           // [kSlots][kBatch][kRow4]; then [kSlots][kNB][49] partial tiles
     __shared__ float s_s2[kNQ];                // squared natural-unit scale of each unknown
     __shared__ float s_sf[7];
-    __shared__ float s_dsc[P][kNA];
+    __shared__ float s_diag[kSlots][kNA];      // Gram diagonal, for the equilibration
+    __shared__ float s_lw[kSlots];             // lambda W
+    __shared__ __align__(16) float s_u[kSlots][8][7][8];   // panel U_J,K of the current block column
+    __shared__ float s_inv[kSlots][7];         // 1 / diagonal of U_JJ
 
     const int tid = threadIdx.x;
     const size_t N = (size_t)p.W * p.H;
@@ -137,8 +135,6 @@ __global__ void __launch_bounds__(kThreads, 2) wlr2_kernel(W2Params p)
     const int f = (int)(blockIdx.x / ((unsigned)nxc * (unsigned)p.H));
     const int x0 = xc * P;
 
-    if (tid < kNA)
-        for (int R = tid; R < kNA; ++R) s_tab[tri_off(tid) + R - tid] = (uint16_t)(R | (tid << 8));
     if (tid < 7) s_sf[tid] = kExp2Scale / (p.h * p.bandwidth[tid]);
     __syncthreads();
     if (tid < kNQ) {
@@ -241,63 +237,123 @@ __global__ void __launch_bounds__(kThreads, 2) wlr2_kernel(W2Params p)
         __syncthreads();
     }
 
-    // partial Gram of each slot, packed lower triangle (entry (7bj+k, 7bi+i))
-    float* grams = reinterpret_cast<float*>(zbuf);
-    {
-        float* g = grams + (size_t)slot * kTri;
+    // The G slots of a pixel add their tiles into the first slot's, in slot order.
+    const int tk = tid - slot * kNB;
+    if constexpr (G > 1) {
+        float* part = reinterpret_cast<float*>(zbuf) + ((size_t)slot * kNB + tk) * 49;
 #pragma unroll
         for (int i = 0; i < 7; ++i)
 #pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                const int R = 7 * bj + k, C = 7 * bi + i;
-                if (R >= C) g[tri_off(C) + R - C] = acc[i][k];
+            for (int k = 0; k < 7; ++k) part[i * 7 + k] = acc[i][k];
+        __syncthreads();
+        if (slot % G == 0) {
+#pragma unroll
+            for (int s = 1; s < G; ++s) {
+                const float* o = part + (size_t)s * kNB * 49;
+#pragma unroll
+                for (int i = 0; i < 7; ++i)
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) acc[i][k] += o[i * 7 + k];
             }
+        }
+    }
+    const bool lead = slot % G == 0 && x0 + slot / G < p.W;
+
+    // Ridge and Jacobi equilibration, tile by tile: A_ab <- A_ab / sqrt(A_aa A_bb)
+    // (the log-brightness row keeps scale 1).
+    if (lead && bi == bj) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) s_diag[slot][7 * bi + i] = acc[i][i];
+        if (bi == 7) s_lw[slot] = p.ridge * acc[5][5];   // lambda W; W = sum w = A[54][54]
     }
     __syncthreads();
-    if constexpr (G > 1) {
-        for (int e = tid; e < P * kTri; e += kThreads) {
-            const int pp = e / kTri, k = e - pp * kTri;
-            float* g0 = grams + (size_t)pp * G * kTri + k;
-            float v = g0[0];
+    float dr[7];
+    if (lead) {
+        const float lw = s_lw[slot];
+        float dc[7];
 #pragma unroll
-            for (int s = 1; s < G; ++s) v += g0[(size_t)s * kTri];
-            g0[0] = v;
+        for (int i = 0; i < 7; ++i) {
+            const int a = 7 * bi + i, c = 7 * bj + i;
+            const float da = a < 54 ? fmaf(lw, s_s2[a], s_diag[slot][a]) : s_diag[slot][a];
+            const float dcv = c < 54 ? fmaf(lw, s_s2[c], s_diag[slot][c]) : s_diag[slot][c];
+            dr[i] = a < kNQ ? rsqrtf(da) : 1.0f;
+            dc[i] = c < kNQ ? rsqrtf(dcv) : 1.0f;
+            if (bi == bj && a < 54) acc[i][i] = fmaf(lw, s_s2[a], acc[i][i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+#pragma unroll
+            for (int k = 0; k < 7; ++k) acc[i][k] *= dr[i] * dc[k];
+    }
+
+    // Right-looking blocked Cholesky A = U^T U over the 8 block columns, each
+    // tile staying in its owner's registers: factor the diagonal tile, solve
+    // the panel U_JK = U_JJ^-T A_JK, update the trailing tiles
+    // A_KL -= U_JK^T U_JL.  Panels pass through shared memory.
+    float* uf = reinterpret_cast<float*>(&s_u[slot][0][0][0]);   // [8 blocks][7 rows][8]
+    for (int J = 0; J < 8; ++J) {
+        if (lead && bi == J && bj == J) {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                float sd = acc[i][i];
+#pragma unroll
+                for (int m = 0; m < i; ++m) sd = fmaf(-acc[m][i], acc[m][i], sd);
+                const float piv = sqrtf(fmaxf(sd, 1e-30f));
+                const float inv = 1.0f / piv;
+                acc[i][i] = piv;
+#pragma unroll
+                for (int k = i + 1; k < 7; ++k) {
+                    float x = acc[i][k];
+#pragma unroll
+                    for (int m = 0; m < i; ++m) x = fmaf(-acc[m][i], acc[m][k], x);
+                    acc[i][k] = x * inv;
+                }
+                s_inv[slot][i] = inv;
+            }
+#pragma unroll
+            for (int i = 0; i < 7; ++i)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) uf[(J * 7 + i) * 8 + k] = (k < 7 && k >= i) ? acc[i][k] : 0.0f;
+        }
+        __syncthreads();
+        if (lead && bi == J && bj > J) {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                const float inv = s_inv[slot][i];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    float x = acc[i][k];
+#pragma unroll
+                    for (int m = 0; m < i; ++m) x = fmaf(-uf[(J * 7 + m) * 8 + i], acc[m][k], x);
+                    acc[i][k] = x * inv;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 7; ++i)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) uf[(bj * 7 + i) * 8 + k] = k < 7 ? acc[i][k] : 0.0f;
+        }
+        __syncthreads();
+        if (lead && bi > J) {
+            const float4* u4 = reinterpret_cast<const float4*>(uf);
+#pragma unroll
+            for (int m = 0; m < 7; ++m) {
+                const float4 a0 = u4[(bi * 7 + m) * 2], a1 = u4[(bi * 7 + m) * 2 + 1];
+                const float4 b0 = u4[(bj * 7 + m) * 2], b1 = u4[(bj * 7 + m) * 2 + 1];
+                const float av[7] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z};
+                const float bv[7] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z};
+#pragma unroll
+                for (int i = 0; i < 7; ++i)
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) acc[i][k] = fmaf(-av[i], bv[k], acc[i][k]);
+            }
         }
         __syncthreads();
     }
-
-    // one warp per pixel: ridge, Jacobi equilibration, Cholesky of the augmented Gram
-    const int w = tid >> 5, lane = tid & 31;
-    if (w >= P || x0 + w >= p.W) return;
-    float* A = grams + (size_t)w * G * kTri;
-    float* dsc = s_dsc[w];
-    const float lw = p.ridge * A[tri_off(54)];   // lambda W
-    for (int a = lane; a < 54; a += 32) A[tri_off(a)] = fmaf(lw, s_s2[a], A[tri_off(a)]);
-    __syncwarp();
-    for (int a = lane; a < kNA; a += 32) dsc[a] = a < kNQ ? rsqrtf(A[tri_off(a)]) : 1.0f;
-    __syncwarp();
-    for (int e = lane; e < kTri; e += 32) {
-        const uint32_t rc = s_tab[e];
-        A[e] *= dsc[rc & 0xffu] * dsc[rc >> 8];
-    }
-    __syncwarp();
-    for (int jc = 0; jc < kNQ; ++jc) {
-        const int oj = tri_off(jc);
-        const float piv = sqrtf(fmaxf(A[oj], 1e-30f));
-        const float inv = 1.0f / piv;
-        __syncwarp();
-        for (int i = jc + 1 + lane; i < kNA; i += 32) A[oj + i - jc] *= inv;
-        if (lane == 0) A[oj] = piv;
-        __syncwarp();
-#pragma unroll 4
-        for (int e = tri_off(jc + 1) + lane; e < kTri; e += 32) {
-            const uint32_t rc = s_tab[e];
-            A[e] = fmaf(-A[oj + (int)(rc & 0xffu) - jc], A[oj + (int)(rc >> 8) - jc], A[e]);
-        }
-        __syncwarp();
-    }
-    if (lane == 0)
-        p.alpha[(size_t)f * N + (size_t)cy * p.W + x0 + w] = A[tri_off(54) + 1] / A[tri_off(54)] * dsc[54];
+    // With the intercept last and y appended, U[54][55] = (U^-T b)_54 and
+    // theta_54 = U[54][55] / U[54][54] in the equilibrated basis.
+    if (lead && bi == 7 && bj == 7)
+        p.alpha[(size_t)f * N + (size_t)cy * p.W + x0 + slot / G] = acc[5][6] / acc[5][5] * dr[5];
 }
 
 bool desc_ok(const esim_ad_wlr_desc* d)
