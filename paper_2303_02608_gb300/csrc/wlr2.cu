@@ -114,9 +114,11 @@ __global__ void __launch_bounds__(kTilePix) wlr2_pack_kernel(W2Params p)
     out[N + i] = make_float4(ft[3 * N + i], ft[4 * N + i], ft[5 * N + i], ft[6 * N + i]);
 }
 
-// G slots per pixel, 8 / G pixels per CTA along one image row.
+// G slots per pixel, 8 / G pixels per CTA along one image row.  96 registers
+// keep two 9-warp CTAs per SM (the register file is split over four
+// sub-partitions); the few values that do not fit spill only in the panel solve.
 template <int G>
-__global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
+__global__ void __maxnreg__(96) wlr2_kernel(W2Params p)
 {
     constexpr int P = kSlots / G;              // pixels per CTA
     extern __shared__ float4 zbuf[];           // [kSlots][kBatch][kRow4]; then [kSlots][kNB][49] partial tiles
@@ -126,6 +128,7 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
     __shared__ float s_lw[kSlots];             // lambda W
     __shared__ __align__(16) float s_u[kSlots][8][7][8];   // panel U_J,K of the current block column
     __shared__ float s_inv[kSlots][7];         // 1 / diagonal of U_JJ
+    __shared__ float s_cf[kSlots][7];          // scaled centre features of each slot's pixel
 
     const int tid = threadIdx.x;
     const size_t N = (size_t)p.W * p.H;
@@ -156,18 +159,17 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
     const int b_pix = x0 + cs / G, b_sub = cs % G;
     const bool builder = tid < kSlots * kBatch;
     const bool b_ok = builder && b_pix < p.W;
-    float cf[7], sf[7];
     const float s_px = kExp2Scale / (p.h * (float)p.r);
-    if (b_ok) {
+    if (b_ok && j < 7) {   // scaled centre features of the slot's pixel
         const size_t ci = (size_t)cy * p.W + b_pix;
         const float4 c0 = p.packed[(size_t)f * 2 * N + ci];
         const float4 c1 = p.packed[((size_t)f * 2 + 1) * N + ci];
         const float xcv[7] = {c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        float v = xcv[0];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            sf[k] = s_sf[k];
-            cf[k] = xcv[k] * sf[k];
-        }
+        for (int k = 1; k < 7; ++k)
+            if (j == k) v = xcv[k];
+        s_cf[cs][j] = v * s_sf[j];
     }
 
     // accumulator role: slot, 7 x 7 tile (bi, bj) of the block grid
@@ -181,6 +183,7 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
 #pragma unroll
         for (int k = 0; k < 7; ++k) acc[i][k] = 0.0f;
 
+    __syncthreads();   // s_cf, s_s2 ready
     const int S = 2 * p.r + 1;
     const int t_eff = min(p.T, f + 1);
     const int M = S * S * t_eff;
@@ -210,7 +213,7 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
                     float e = fmaf(u[0], u[0], u[1] * u[1]);
 #pragma unroll
                     for (int k = 0; k < 7; ++k) {
-                        u[2 + k] = fmaf(xv[k], sf[k], -cf[k]);
+                        u[2 + k] = fmaf(xv[k], s_sf[k], -s_cf[cs][k]);
                         e = fmaf(u[2 + k], u[2 + k], e);
                     }
                     store_row<0>(row, u, h0.x, ex2_approx(-0.5f * e));   // sqrt(w) = 2^(-|u|^2 / 2)
@@ -267,10 +270,10 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
         if (bi == 7) s_lw[slot] = p.ridge * acc[5][5];   // lambda W; W = sum w = A[54][54]
     }
     __syncthreads();
-    float dr[7];
+    float d54 = 1.0f;   // equilibration scale of the intercept (tile (7,7), row 5)
     if (lead) {
         const float lw = s_lw[slot];
-        float dc[7];
+        float dr[7], dc[7];
 #pragma unroll
         for (int i = 0; i < 7; ++i) {
             const int a = 7 * bi + i, c = 7 * bj + i;
@@ -284,6 +287,7 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
         for (int i = 0; i < 7; ++i)
 #pragma unroll
             for (int k = 0; k < 7; ++k) acc[i][k] *= dr[i] * dc[k];
+        d54 = dr[5];
     }
 
     // Right-looking blocked Cholesky A = U^T U over the 8 block columns, each
@@ -336,7 +340,7 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
         __syncthreads();
         if (lead && bi > J) {
             const float4* u4 = reinterpret_cast<const float4*>(uf);
-#pragma unroll
+#pragma unroll 1
             for (int m = 0; m < 7; ++m) {
                 const float4 a0 = u4[(bi * 7 + m) * 2], a1 = u4[(bi * 7 + m) * 2 + 1];
                 const float4 b0 = u4[(bj * 7 + m) * 2], b1 = u4[(bj * 7 + m) * 2 + 1];
@@ -353,7 +357,7 @@ __global__ void __maxnreg__(112) wlr2_kernel(W2Params p)
     // With the intercept last and y appended, U[54][55] = (U^-T b)_54 and
     // theta_54 = U[54][55] / U[54][54] in the equilibrated basis.
     if (lead && bi == 7 && bj == 7)
-        p.alpha[(size_t)f * N + (size_t)cy * p.W + x0 + slot / G] = acc[5][6] / acc[5][5] * dr[5];
+        p.alpha[(size_t)f * N + (size_t)cy * p.W + x0 + slot / G] = acc[5][6] / acc[5][5] * d54;
 }
 
 bool desc_ok(const esim_ad_wlr_desc* d)
@@ -383,6 +387,9 @@ cudaError_t launch(const W2Params& p, cudaStream_t s)
 {
     constexpr int P = kSlots / G;
     cudaError_t e = cudaFuncSetAttribute(wlr2_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemZ);
+    if (e != cudaSuccess) return e;
+    // two CTAs per SM: about 175 KB of shared memory (the rest of the unified array stays L1)
+    e = cudaFuncSetAttribute(wlr2_kernel<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 80);
     if (e != cudaSuccess) return e;
     const unsigned long long n = (unsigned long long)p.F * p.H * ((p.W + P - 1) / P);
     if (n == 0 || n > 0x7fffffffull) return cudaErrorInvalidValue;
