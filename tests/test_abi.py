@@ -108,6 +108,27 @@ def test_null_context_calls(lib):
         assert lib.status_string(code) not in ("unknown status", "")
 
 
+def test_dense_form_descriptors_checked_on_the_host(lib):
+    """Workspace sizes of the differentiation and second-order forms, and their
+    rejection of bad descriptors and NULL buffers, need no GPU."""
+    so = lib.load_library()
+    d = lib.make_wlr_desc(40, 24, 5, radius=3, frames=3)
+    assert lib.esim_ad_wlr2_workspace_size(d) == 5 * 2 * 40 * 24 * 16
+    assert lib.esim_ad_wlr_workspace_size(d) > 0
+    for k, v in (("radius", 0), ("radius", 16), ("frames", 0), ("frames", 17), ("width", 0), ("ridge", 0.0),
+                 ("h", -1.0), ("log_eps", -1e-3), ("radiance_fmt", 7), ("struct_size", 4)):
+        bad = lib.make_wlr_desc(40, 24, 5)
+        setattr(bad, k, v)
+        assert lib.esim_ad_wlr2_workspace_size(bad) == 0, k
+        assert lib.esim_ad_wlr_workspace_size(bad) == 0, k
+    P = ctypes.c_void_p
+    assert so.esim_ad_wlr2_forward(ctypes.byref(d), None, P(16), P(16), P(16), P(16), None) == lib.ESIM_AD_EINVAL
+    assert so.esim_ad_wlr2_forward(None, P(16), P(16), P(16), P(16), P(16), None) == lib.ESIM_AD_EINVAL
+    many = lib.make_wlr_desc(8, 8, 70000)
+    assert so.esim_ad_wlr2_forward(ctypes.byref(many), P(16), P(16), P(16), P(16), P(16), None) == \
+        lib.ESIM_AD_EINVAL
+
+
 def test_init_without_gpu_reports_cuda_error(lib):
     import torch
     if torch.cuda.is_available():
