@@ -43,7 +43,9 @@ constexpr int kSlots = 8;                  // 36-thread slots per CTA
 constexpr int kThreads = kSlots * kNB;     // 288
 constexpr int kBatch = 32;                 // neighbours per slot per round
 constexpr int kRow4 = 17;                  // float4 per neighbour: [2 halves][8 blocks] + 1 pad
-constexpr size_t kSmemZ = (size_t)kSlots * kBatch * kRow4 * sizeof(float4);  // 69,632 B
+constexpr int kSlot4 = kBatch * kRow4 + 1; // float4 per slot: the +1 puts the 8 slots in 8 bank groups
+constexpr int kUStride = 8 * 7 * 8 + 4;    // floats per slot of panel storage, same bank spread
+constexpr size_t kSmemZ = (size_t)kSlots * kSlot4 * sizeof(float4);  // 69,760 B
 static_assert((size_t)kSlots * kNB * 49 * sizeof(float) <= kSmemZ, "partial tiles must fit in the neighbour buffer");
 
 constexpr float kExp2Scale = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
@@ -121,12 +123,12 @@ template <int G>
 __global__ void __maxnreg__(96) wlr2_kernel(W2Params p)
 {
     constexpr int P = kSlots / G;              // pixels per CTA
-    extern __shared__ float4 zbuf[];           // [kSlots][kBatch][kRow4]; then [kSlots][kNB][49] partial tiles
+    extern __shared__ float4 zbuf[];           // [kSlots][kSlot4]; then [kSlots][kNB][49] partial tiles
     __shared__ float s_s2[kNQ];                // squared natural-unit scale of each unknown
     __shared__ float s_sf[7];
-    __shared__ float s_diag[kSlots][kNA];      // Gram diagonal, for the equilibration
+    __shared__ float s_diag[kSlots][kNA + 1];  // Gram diagonal, for the equilibration
     __shared__ float s_lw[kSlots];             // lambda W
-    __shared__ __align__(16) float s_u[kSlots][8][7][8];   // panel U_J,K of the current block column
+    __shared__ __align__(16) float s_u[kSlots * kUStride];  // panel U_J,K of the current block column
     __shared__ float s_inv[kSlots][7];         // 1 / diagonal of U_JJ
     __shared__ float s_cf[kSlots][7];          // scaled centre features of each slot's pixel
 
@@ -172,9 +174,11 @@ __global__ void __maxnreg__(96) wlr2_kernel(W2Params p)
         s_cf[cs][j] = v * s_sf[j];
     }
 
-    // accumulator role: slot, 7 x 7 tile (bi, bj) of the block grid
-    const int slot = tid / kNB;
-    int bi = 0, bj = tid - slot * kNB;
+    // accumulator role: 7 x 7 tile (bi, bj) of the block grid for one slot.  The
+    // 8 slots' copies of a tile sit in adjacent lanes, so that each step of the
+    // factorisation below runs in the few warps that hold its tiles.
+    const int slot = tid % kSlots, tk = tid / kSlots;
+    int bi = 0, bj = tk;
     while (bj >= 8 - bi) { bj -= 8 - bi; ++bi; }
     bj += bi;
     float acc[7][7];
@@ -191,7 +195,7 @@ __global__ void __maxnreg__(96) wlr2_kernel(W2Params p)
     const int rounds = (n_batch + G - 1) / G;
     for (int q = 0; q < rounds; ++q) {
         if (builder) {
-            float4* row = zbuf + ((size_t)cs * kBatch + j) * kRow4;
+            float4* row = zbuf + (size_t)cs * kSlot4 + j * kRow4;
             const int n = (q * G + b_sub) * kBatch + j;
             bool ok = b_ok && n < M;
             int qx = 0, qy = 0, tau = 0;
@@ -225,7 +229,7 @@ __global__ void __maxnreg__(96) wlr2_kernel(W2Params p)
             }
         }
         __syncthreads();
-        const float4* base = zbuf + (size_t)slot * kBatch * kRow4;
+        const float4* base = zbuf + (size_t)slot * kSlot4;
 #pragma unroll 2
         for (int n = 0; n < kBatch; ++n) {
             const float4* row = base + n * kRow4;
@@ -241,7 +245,6 @@ __global__ void __maxnreg__(96) wlr2_kernel(W2Params p)
     }
 
     // The G slots of a pixel add their tiles into the first slot's, in slot order.
-    const int tk = tid - slot * kNB;
     if constexpr (G > 1) {
         float* part = reinterpret_cast<float*>(zbuf) + ((size_t)slot * kNB + tk) * 49;
 #pragma unroll
@@ -294,7 +297,7 @@ __global__ void __maxnreg__(96) wlr2_kernel(W2Params p)
     // tile staying in its owner's registers: factor the diagonal tile, solve
     // the panel U_JK = U_JJ^-T A_JK, update the trailing tiles
     // A_KL -= U_JK^T U_JL.  Panels pass through shared memory.
-    float* uf = reinterpret_cast<float*>(&s_u[slot][0][0][0]);   // [8 blocks][7 rows][8]
+    float* uf = s_u + slot * kUStride;         // [8 blocks][7 rows][8]
     for (int J = 0; J < 8; ++J) {
         if (lead && bi == J && bj == J) {
 #pragma unroll
