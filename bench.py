@@ -783,6 +783,29 @@ def _second_order(dev, fp32_peak, reps=5, warmup=3, r=3, T=3):
         "noisy_input": float(((y_noisy - target) ** 2).mean()),
         "first_order": float(((alpha1 - target) ** 2).mean()),
         "second_order": float(((alpha2 - target) ** 2).mean())}
+    # events: plain ESIM on each log-brightness series, against ESIM on the clean frames
+    from paper_2303_02608_gb300 import esim_frame, quality
+    taus = [5e-4, 1e-3, 2e-3, 5e-3, 1e-2]
+
+    def esim_counts(series, C):
+        l_last = torch.empty(H, W, dtype=torch.float32, device=dev)
+        counts = torch.zeros(F, H, W, dtype=torch.int32, device=dev)
+        for t in range(F):
+            esim_frame(series(t), l_last, counts[t], C, t == 0)
+        return counts
+
+    as_radiance = lambda a: (lambda t: (torch.exp(a[t]) - 1e-3)[None].contiguous())   # ln(Y + eps) = a
+    ev = {}
+    for C in (0.25, 0.5):
+        ref = esim_counts(lambda t: Yc[t][None].contiguous(), C)
+        res = {}
+        for name, series in (("ESIM", lambda t: rad[t]), ("WLR+ESIM", as_radiance(alpha1)),
+                             ("WLR2+ESIM", as_radiance(alpha2))):
+            q = quality(esim_counts(series, C), ref, taus)
+            res[name] = {"F": [round(v, 5) for v in q["fscore"]], "CD": q["chamfer"], "events": q["n_gen"]}
+        res["reference_events"] = q["n_ref"]
+        ev[str(C)] = res
+    out["event_quality"] = {"taus": taus, "reference": "ESIM on the clean frames", "by_C": ev}
     return out
 
 
