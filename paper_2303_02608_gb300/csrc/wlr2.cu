@@ -12,21 +12,22 @@
 // right-hand side.  The ridge lambda W |theta_k|^2 on every coefficient but the
 // intercept is added in natural units (lambda W s_a^2 s_b^2 on the diagonal of
 // a quadratic unknown, lambda W s_a^2 on a linear one).  With the intercept
-// ordered last among the unknowns, the Cholesky factor of the augmented
-// (equilibrated) Gram gives alpha = L[55][54] / L[54][54] directly: no back
+// ordered last among the unknowns, the upper Cholesky factor U of the augmented
+// (equilibrated) Gram gives alpha = U[54][55] / U[54][54] directly: no back
 // substitution.
 //
-// Layout of the work: a CTA of 288 threads holds 8 slots of 36 threads.  The
-// 56 x 56 Gram is cut into 8 x 8 blocks of 7; the 36 blocks on and above the
-// block diagonal go one per thread, a 7 x 7 register tile (49 FP32
-// accumulators) fed by two 7-vectors from shared memory per neighbour.  A round
-// builds sqrt(w) z for 32 neighbours per slot in shared memory, then every
-// thread runs its tile over them.  G slots share one pixel, each summing an
-// interleaved G-th of the window's neighbour batches (G grows with the window,
-// so no accumulator sums more than a few hundred terms in FP32); their partial
-// Grams are added in slot order, so results do not depend on scheduling.  One
-// warp per pixel then equilibrates (Jacobi) and factors the packed Gram in
-// shared memory, spreading each step's trailing update over the lanes.
+// Layout of the work: a CTA of 288 threads covers 8 slots.  The 56 x 56 Gram is
+// cut into 8 x 8 blocks of 7; the 36 blocks on and above the block diagonal of
+// each slot go one per thread, a 7 x 7 register tile (49 FP32 accumulators) fed
+// by two 7-vectors from shared memory per neighbour.  A round builds sqrt(w) z
+// for 32 neighbours per slot in shared memory, then every thread runs its tile
+// over them.  G slots share one pixel, each summing an interleaved G-th of the
+// window's neighbour batches (G grows with the window, so no accumulator sums
+// more than a few hundred terms in FP32); their partial tiles are added in slot
+// order, so results do not depend on scheduling.  The solve never leaves the
+// tiles: ridge and Jacobi equilibration tile by tile, then a right-looking
+// blocked Cholesky over the 8 block columns, panels passing through shared
+// memory.
 #include <stdlib.h>
 
 #include "esim_ad.h"
