@@ -49,11 +49,12 @@ FP32_LANES_PER_SM = 128
 # Second-order regression (55 unknowns + the log brightness column): per
 # (pixel, neighbour) pair the scaled offsets and weight (33), the 45 products
 # and the sqrt(w) scaling of 56 entries (101), and the 56 x 57 / 2 = 1596
-# entries of the augmented Gram (3192) -> 3326 flop; per pixel the ridge and
-# equilibration (3300) and the Cholesky of the augmented 56 x 56 system
-# (2 x 55 x 56 x 57 / 6 trailing-update flop + column scaling) -> 63300 flop.
+# entries of the augmented Gram (3192) -> 3326 flop; per pixel the ridge (108),
+# the equilibration of the 1596 Gram entries (3192 + 55 rsqrt) and the
+# Cholesky of the augmented 56 x 56 system (2 x 55 x 56 x 57 / 6 = 58520
+# trailing-update flop, 1540 column scalings, 55 sqrt, 2 for alpha) -> 63472.
 FLOP_PER_NEIGHBOUR_2 = 3326
-FLOP_PER_SOLVE_2 = 63300
+FLOP_PER_SOLVE_2 = 63472
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the sparse
 # regression kernel from one ncu capture, valid only while that kernel's
