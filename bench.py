@@ -411,7 +411,10 @@ def run_ours(args):
     if rank == 0 and not args.no_diff:
         line["differentiation_form"] = _differentiation(dev)
     if rank == 0 and not args.no_second_order:
-        line["second_order_form"] = _second_order(dev, fp32_peak)
+        try:   # a side measurement: its failure is reported in the line, not fatal to it
+            line["second_order_form"] = _second_order(dev, fp32_peak)
+        except Exception as exc:   # noqa: BLE001
+            line["second_order_form"] = {"error": repr(exc)}
     if rank == 0 and not args.no_quality:
         line["quality"] = _quality(dev)
     if rank == 0 and not args.no_render:
