@@ -158,3 +158,40 @@ def test_normal_equations_on_clipped_windows():
                     Wsum += w
         A[np.arange(1, 55), np.arange(1, 55)] += lam * Wsum
         assert alpha[t, cy, cx] == pytest.approx(np.linalg.solve(A, rhs)[0], abs=1e-9)
+
+
+def test_agrees_with_the_first_order_oracle_where_both_are_exact():
+    """Two independent oracles, one window and weight convention: on a field
+    linear in the 9-D feature both fits are exact (same alpha as y at the
+    centre), and as the ridge grows both become the same weighted mean.  This
+    ties the second-order oracle's windows (clipping, causal frames), coordinate
+    units and weights to the first-order C oracle."""
+    from oracle import EXHAUSTIVE, Oracle, OracleConfig
+    rng = np.random.default_rng(13)
+    F, H, W, r, T = 3, 8, 9, 2, 2
+    feat = rng.uniform(0.0, 1.0, size=(F, 7, H, W)).astype(np.float32).astype(np.float64)
+    rad_w = rng.uniform(0.2, 2.0, size=(F, 1, H, W)).astype(np.float32).astype(np.float64)
+    b = [0.7, 1.3, 0.9, 1.6, 0.8, 1.2, 1.0]
+
+    def first_order(rad, ridge):
+        o = Oracle(OracleConfig(W, H, radius=r, frames=T, channels=1, mode=EXHAUSTIVE, bandwidth=b, ridge=ridge))
+        out = []
+        for t in range(F):
+            o.push({"radiance": rad[t, 0].astype(np.float32), "normal": feat[t, 0:3].astype(np.float32),
+                    "depth": feat[t, 3].astype(np.float32), "albedo": feat[t, 4:7].astype(np.float32)})
+            out.append(o.outputs()["alpha"])
+        return np.stack(out)
+
+    a1 = first_order(rad_w, 1e14)
+    a2 = O.wlr2(rad_w, feat, bandwidth=b, radius=r, frames=T, ridge=1e14)
+    np.testing.assert_allclose(a2, a1, rtol=0, atol=1e-9)
+    # a field linear in the feature: both reproduce it (to the float32 rounding of the radiance)
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    g = rng.normal(size=9)
+    lin = (0.3 + g[0] * xx / r + g[1] * yy / r)[None] + np.einsum("j,fjhw->fhw", g[2:], feat)
+    rad_l = (np.exp(lin) - 1e-3)[:, None].astype(np.float32).astype(np.float64)
+    y_l = O.log_brightness(rad_l, 1e-3)
+    a1 = first_order(rad_l, 1e-12)
+    a2 = O.wlr2(rad_l, feat, bandwidth=b, radius=r, frames=T, ridge=1e-12)
+    np.testing.assert_allclose(a1, y_l, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(a2, y_l, rtol=0, atol=2e-6)
