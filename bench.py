@@ -262,9 +262,29 @@ def _cpu_baseline(frames_cpu, wl, budget_s=15.0, rows=None):
             break
     dt = time.perf_counter() - t0
     px = (r1 - r0) * Wd
-    return {"value": px * n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"rows {r0}-{r1 - 1} ({px} px) of the {Wd}x{H} workload, frames 0-{n - 1}, "
-                      f"adaptive, FP64 C oracle with OpenMP", "seconds": round(dt, 2)}
+    out = {"value": px * n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"rows {r0}-{r1 - 1} ({px} px) of the {Wd}x{H} workload, frames 0-{n - 1}, "
+                     f"adaptive, FP64 C oracle with OpenMP", "seconds": round(dt, 2)}
+    # the same oracle on one core, on a 16-row band of the same frames
+    all_cores = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        q0, q1 = H // 2 - 8, H // 2 + 8
+        orc1 = Oracle(OracleConfig(Wd, H, radius=wl["r"], frames=wl["T"], channels=channels,
+                                   mode=ADAPTIVE, contrast=wl["C"]))
+        t0, m = time.perf_counter(), 0
+        for fr in frames_cpu:
+            orc1.push(fr, (q0, q1))
+            m += 1
+            if time.perf_counter() - t0 > budget_s / 2 and m >= 2:
+                break
+        dt1 = time.perf_counter() - t0
+        out["one_core"] = {"value": (q1 - q0) * Wd * m / dt1, "unit": UNIT, "cores": 1,
+                           "sample": f"rows {q0}-{q1 - 1} ({(q1 - q0) * Wd} px), frames 0-{m - 1}",
+                           "seconds": round(dt1, 2)}
+    finally:
+        oracle.set_threads(all_cores)
+    return out
 
 
 FSCALE = [1.0, 1.0, 1.0, 8.0, 1.0, 1.0, 1.0]   # BF16 feature scales: depth stored as depth / 8

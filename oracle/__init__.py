@@ -71,12 +71,18 @@ def _load():
         lib.or_wlr_at.restype = ctypes.c_int
         lib.or_wlr_at.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P]
         lib.or_threads.restype = ctypes.c_int32
+        lib.or_set_threads.argtypes = [ctypes.c_int32]
         _lib = lib
     return _lib
 
 
 def threads() -> int:
     return int(_load().or_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's later calls (timing only)."""
+    _load().or_set_threads(int(n))
 
 
 @dataclass

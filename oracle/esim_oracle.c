@@ -72,6 +72,15 @@ int32_t or_threads(void)
 #endif
 }
 
+void or_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 or_sim* or_create(const or_config* cfg)
 {
     if (!cfg || cfg->width <= 0 || cfg->height <= 0 || cfg->radius < 1 || cfg->frames < 1 ||

@@ -83,6 +83,8 @@ int     or_wlr_at(const or_sim* s, int32_t cx, int32_t cy, double* theta10, doub
                   double* W);
 
 int32_t or_threads(void);
+/* OpenMP threads for the calls that follow (n > 0); timing only. */
+void    or_set_threads(int32_t n);
 
 #ifdef __cplusplus
 }
