@@ -64,6 +64,7 @@ struct esim_ad_ctx {
     int nbuf = 2;
     int wlr_grid = 0;
     int sparse_grid = 0;
+    int solve_grid = 0;
     int sparse_stage = 1;        // sparse kernel stages window boxes (ESIM_AD_SPARSE_STAGE=0: L1 only)
     bool mixed = false;
     uint32_t sparse_max = 0;     // adaptive frames with at most this many flagged pixels use the sparse kernel
@@ -76,6 +77,8 @@ struct esim_ad_ctx {
     int32_t* tile_nflag = nullptr;
     uint8_t* tile_pix = nullptr;
     uint32_t* flag_list = nullptr;
+    uint32_t* tile_base = nullptr;
+    float* gram = nullptr;       // Gram records of the frame's regressed pixels
     uint32_t* chunk_cnt = nullptr;
     unsigned long long* chunk_off = nullptr;
     esim_ad_event* events = nullptr;
@@ -137,7 +140,7 @@ esim_ad_status check_config(const esim_ad_config* c)
 void release(esim_ad_ctx* c)
 {
     void* ptrs[] = {c->ring, c->state, c->alpha, c->flag, c->nev, c->tile_queue, c->tile_nflag,
-                    c->tile_pix, c->flag_list, c->chunk_cnt, c->chunk_off, c->events, c->ctrl,
+                    c->tile_pix, c->flag_list, c->tile_base, c->gram, c->chunk_cnt, c->chunk_off, c->events, c->ctrl,
                     c->staging[0], c->staging[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -276,6 +279,8 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         {(void**)&c->tile_nflag, (size_t)c->n_tiles * sizeof(int32_t)},
         {(void**)&c->tile_pix, (size_t)c->n_tiles * kTilePix},
         {(void**)&c->flag_list, (N + 4 * (size_t)c->n_tiles) * sizeof(uint32_t)},   // + tile padding
+        {(void**)&c->tile_base, (size_t)c->n_tiles * sizeof(uint32_t)},
+        {(void**)&c->gram, (N + 4 * (size_t)c->n_tiles) * kGramRecordBytes},       // one per list entry or pixel
         {(void**)&c->chunk_cnt, (size_t)c->n_chunks * sizeof(uint32_t)},
         {(void**)&c->chunk_off, (size_t)c->n_chunks * sizeof(unsigned long long)},
         {(void**)&c->events, (size_t)cfg->event_capacity * sizeof(esim_ad_event)},
@@ -306,6 +311,7 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     }
     c->wlr_grid = wlr_grid(c->smem_bytes, num_sms, c->mixed);
     c->sparse_grid = wlr_sparse_grid(num_sms, c->mixed, cfg->radius);
+    c->solve_grid = wlr_solve_grid(num_sms);
     // default: frames with up to 1/8 of the pixels flagged take the sparse kernel
     // (measured faster than tile staging at the 1-2% densities of edge-like
     // flag patterns); ESIM_AD_SPARSE_MAX overrides it (0: always the tile-staged
@@ -440,6 +446,7 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     ip.chunk_cnt = c->chunk_cnt;
     ip.n_chunks = c->n_chunks;
     ip.flag_list = c->flag_list;
+    ip.tile_base = c->tile_base;
     ip.ctrl = c->ctrl;
     {
         ProfScope ps(c, 0);
@@ -487,6 +494,10 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     wp.sparse_max = c->sparse_max;
     wp.flag_list = c->flag_list;
     wp.sparse_stage = c->sparse_stage;
+    wp.tile_base = c->tile_base;
+    wp.gram = c->gram;
+    wp.poll_limit = kPollLimit;
+    wp.withhold_copy = 0;
     wp.ctrl = c->ctrl;
     {
         ProfScope ps(c, 1);
@@ -497,7 +508,9 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
         // flagged; each of the two launches returns at once on the other's frames
         if (!wp.dense && launch_wlr_sparse(wp, c->mixed, c->sparse_grid, c->stream) != cudaSuccess)
             return ESIM_AD_ECUDA;
-        c->prof_kernels += wp.dense ? 1 : 2;
+        // solve every accumulated system, emit, and scan the event counts
+        if (launch_wlr_solve(wp, c->mixed, c->solve_grid, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        c->prof_kernels += wp.dense ? 2 : 3;
     }
 
     if (c->t > 0) {

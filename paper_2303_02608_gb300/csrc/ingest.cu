@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kTilePix) ingest_test_kernel(IngestParams p)
             p.tile_queue[slot] = (uint32_t)tile;
             atomicAdd(&p.ctrl->flag_total, (uint32_t)total);
             s_list_base = atomicAdd(&p.ctrl->list_len, (uint32_t)((total + 3) & ~3));
+            p.tile_base[tile] = s_list_base;
         }
     }
     __syncthreads();

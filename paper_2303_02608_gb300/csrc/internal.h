@@ -43,6 +43,8 @@ struct Ctrl {
     uint32_t pad2;
 };
 constexpr size_t kCtrlPerFrameBytes = 24;
+constexpr size_t kGramRecordBytes = 272;   // one Gram record: 66 sums padded to 68 floats
+constexpr uint32_t kPollLimit = 1u << 24;   // default bound on an mbarrier wait (polls)
 
 // Ring of the last T frames.  FP32 form: float4 planes [2T][H][W]; plane
 // 2*slot holds (y, normal xyz), plane 2*slot+1 holds (depth, albedo rgb).
@@ -119,6 +121,7 @@ struct IngestParams {
     int n_chunks;
     uint32_t* flag_list;   // frame-wide list of flagged pixel indices: each tile's run, in raster
                            // order, padded with 0xffffffff to a multiple of 4 entries
+    uint32_t* tile_base;   // position of each queued tile's run in flag_list
     Ctrl* ctrl;
 };
 
@@ -150,6 +153,11 @@ struct WlrParams {
     uint32_t sparse_max;             // queue mode: at most this many flagged pixels -> sparse kernel
     const uint32_t* flag_list;       // flagged pixel indices per tile, each run padded to 4 entries
     int sparse_stage;                // sparse kernel: 1 stage window boxes in shared memory, 0 read via L1
+    const uint32_t* tile_base;       // position of each queued tile's run in flag_list
+    float* gram;                     // Gram records [entries][68]: entry = pixel index (dense) or
+                                     // position in flag_list (adaptive frames)
+    uint32_t poll_limit;             // bound on each mbarrier wait of the sparse kernel (polls)
+    int withhold_copy;               // test only: the sparse kernel never issues its first box copy
     Ctrl* ctrl;
 };
 
@@ -180,6 +188,8 @@ int wlr_sparse_grid(int num_sms, bool mixed, int r);
 cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, bool mixed, int grid,
                        int smem_bytes, cudaStream_t s);
 cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s);
+cudaError_t launch_wlr_solve(const WlrParams& p, bool mixed, int grid, cudaStream_t s);
+int wlr_solve_grid(int num_sms);
 cudaError_t launch_events(const EventParams& p, cudaStream_t s);
 cudaError_t launch_event_write(const EventParams& p, cudaStream_t s);
 

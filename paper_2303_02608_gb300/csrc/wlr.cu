@@ -1,30 +1,36 @@
-// Weighted local regression (Eqs. 3-5) with fused event emission (Eq. 1).
+// Weighted local regression (Eqs. 3-5) with event emission (Eq. 1), in two
+// passes per frame.
 //
-// Work unit: a 32x8 pixel tile.  For each frame tau of the temporal window
-// t-T+1..t the tile plus an r-pixel halo of that frame's ring slot
-// ((32+2r) x (8+2r) pixels x 2 float4 half-planes) is staged in shared memory
-// by one 4-D TMA load.  CTAs are persistent: they pull work items (tiles, or
-// chunks of a tile's flagged pixels) from a counter and keep up to three staged
-// frames in flight, so the copy of the next frame or item overlaps the
-// arithmetic on the current one.  Pixels outside the image arrive zero-filled and are never
-// read: each centre's offset range is clipped to the image instead.
+// Pass 1 accumulates.  For every regressed pixel the kernel-weighted sums of
+// the normal equations over the spatio-temporal window (the Gram matrix of
+// z = (1, u) and the right-hand side, 65 numbers) are summed in registers and
+// stored as one 272-byte Gram record.  Two kernels share this pass and pick
+// frames by flag density:
+//   wlr_kernel         - tile-staged: a 32x8 pixel tile plus an r-pixel halo of
+//                        one ring frame per stage, landed by one 4-D TMA load,
+//                        up to three stages in flight per persistent CTA; every
+//                        pixel of a tile (dense frames) or the tile's flagged
+//                        pixels (adaptive frames with many flags);
+//   wlr_sparse_kernel  - per-warp window boxes of four flagged pixels, landed by
+//                        bulk asynchronous copies (adaptive frames with few flags).
+// Each regressed pixel is owned by g lanes (g = 1 when a tile is densely
+// flagged, up to 32); the lanes split the window's offsets, accumulate in
+// packed FP32 pairs, and are reduced with warp shuffles.  Regressors are the
+// feature differences scaled by k / (h b_j), k = sqrt(log2(e) / 2), so the
+// product Gaussian of Eq. 5 is one exp2:  w = 2^(-|u|^2).
 //
-// Each regressed pixel is owned by g lanes (g = 1 when its tile is densely
-// flagged, up to 32 when it holds few flagged pixels); the lanes split the
-// window's offsets, accumulate the weighted Gram matrix of z = (1, u) and the
-// right-hand side in registers, and are reduced with warp shuffles.  Regressors
-// are the feature differences scaled by k / (h b_j), k = sqrt(log2(e) / 2), so
-// the product Gaussian of Eq. 5 is one exp2:  w = 2^(-|u|^2).  The slopes are
-// mapped back to natural units afterwards; the ridge lambda * W * |beta|^2 is
-// added on the scaled diagonal as lambda * W * s_j^2.  The 10x10 system is
-// Jacobi-equilibrated and solved by Cholesky in fp32.
-//
-// Epilogue (Eq. 1, fixed frame times): Delta L = alpha - L_last,
+// Pass 2 (wlr_solve_kernel) solves each record: the ridge lambda * W * |beta|^2
+// added on the scaled diagonal as lambda * W * s_j^2, Jacobi equilibration and
+// an FP32 Cholesky (the mixed form adds one refinement step and sends systems
+// with condition estimate above 1e6 to a compensated re-accumulation and an
+// FP64 solve); the slopes are mapped back to natural units.  It then applies
+// Eq. 1 at a fixed frame time: Delta L = alpha - L_last,
 // n = floor(|Delta L| / C); if n >= 1 the pixel emits n events of polarity
 // sign(Delta L) (recorded in the per-pixel count map for the ordered event
 // writer), L_last moves by p n C and the model (beta, x^c) is replaced by the
 // new fit (Fig. 1: the model is kept until a new event).  Frame 0 only
-// initialises L_last = alpha and the model.
+// initialises L_last = alpha and the model.  Its last CTA scans the per-chunk
+// event counts for the writer.
 #include "block_scan.cuh"
 #include "internal.h"
 #include "ptx.cuh"
@@ -95,11 +101,11 @@ __global__ void __launch_bounds__(kTilePix, 2)
     const float spx = p.s_coord_px;
 
     // window walk table for lanes that split one interior pixel's window:
-    // (smem offset, u_dx, u_dy, -(u_dx^2 + u_dy^2)) per offset
+    // (u_dx, u_dy, -(u_dx^2 + u_dy^2), smem offset) per offset
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
         const int ox = q % side - p.r, oy = q / side - p.r;
         const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-        table[q] = make_float4(__int_as_float(oy * p.sw + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
+        table[q] = make_float4(u1, u2, -fmaf(u1, u1, u2 * u2), __int_as_float(oy * p.sw + ox));
     }
     if (threadIdx.x == 0) {
         for (int b = 0; b < L.nbuf; ++b) {
@@ -196,12 +202,17 @@ __global__ void __launch_bounds__(kTilePix, 2)
         pr->issued = S + 1;
     };
     // ---- consumer state
-    Acc acc;
+    AccP acc;
     const float* sf = kMixed ? p.q_scale : p.s_feat;   // regressor scale of a stored value
-    float cf[7];
+    PairConst kc;
+    {
+        float cf0[7];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) cf[j] = 0.0f;
+        for (int j = 0; j < 7; ++j) cf0[j] = 0.0f;
+        kc = pair_const(sf, cf0);
+    }
     int g = 1, lg = 0, sub = 0, npix = 0, cx = 0, cy = 0, sx = 0, sy = 0;
+    uint32_t entry = 0;
     int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0;
     bool active = false;
     bool timed_out = false;
@@ -214,10 +225,15 @@ __global__ void __launch_bounds__(kTilePix, 2)
     __syncthreads();
     if (threadIdx.x == 0)
         for (int i = 0; i < L.nbuf; ++i) produce(i);
+    // the first stages are issued before any warp waits on them: a warp whose
+    // other lanes spun on stage 0 while its lane 0 was still issuing it could
+    // starve that lane until the bounded wait gave up
+    __syncthreads();
 
     int s_fail = 0;
     for (int s = 0;; ++s) {
         const int b = s % L.nbuf;
+        __syncwarp();   // lane 0 may still be issuing a stage: no lane polls while it does
         if (!mbar_wait_bounded(&full[b], (uint32_t)((s / L.nbuf) & 1))) {
             timed_out = true;
             s_fail = s;
@@ -231,9 +247,9 @@ __global__ void __launch_bounds__(kTilePix, 2)
         // accumulate the neighbour at staged index si (either ring form)
         auto at = [&](int si, float u1, float u2, float en0) {
             if (kMixed)
-                accumulate(acc, PM[si], u1, u2, en0, sf, cf);
+                accp(acc, PM[si], make_float2(u1, u2), en0, kc);
             else
-                accumulate(acc, P0[si], P1[si], u1, u2, en0, sf, cf);
+                accp(acc, P0[si], P1[si], make_float2(u1, u2), en0, kc);
         };
         if (in.k == 0) {
             // new tile: assign lanes to its regressed pixels
@@ -247,6 +263,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
             active = item < npix;
             const int lidx = kDense ? (int)threadIdx.x
                                     : (active ? (int)p.tile_pix[(size_t)in.tile * kTilePix + in.first + item] : 0);
+            if (!kDense && active) entry = p.tile_base[in.tile] + (uint32_t)(in.first + item);
             const int lx = lidx & (kTileX - 1), ly = lidx / kTileX;
             cx = tx0 + lx;
             cy = ty0 + ly;
@@ -257,10 +274,8 @@ __global__ void __launch_bounds__(kTilePix, 2)
             dyhi = min(p.r, p.H - 1 - cy);
             sx = lx + p.r;
             sy = ly + p.r;
-#pragma unroll
-            for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
+            if (kDense) entry = (uint32_t)cy * (uint32_t)p.W + (uint32_t)cx;
+            accp_zero(acc);
             if (active) {
                 float c[7];
                 if (kMixed) {
@@ -271,8 +286,10 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     const float4 c1 = P1[sy * p.sw + sx];
                     c[0] = c0.y; c[1] = c0.z; c[2] = c0.w; c[3] = c1.x; c[4] = c1.y; c[5] = c1.z; c[6] = c1.w;
                 }
+                float cf[7];
 #pragma unroll
                 for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
+                kc = pair_const(sf, cf);
             }
         }
         if (active) {
@@ -296,7 +313,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
                 const int cbase = sy * p.sw + sx;
                 for (int q = sub; q < nq; q += g) {
                     const float4 e = table[q];
-                    at(cbase + __float_as_int(e.x), e.y, e.z, e.w);
+                    at(cbase + __float_as_int(e.w), e.x, e.y, e.z);
                 }
             } else {
                 // window clipped by the image border
@@ -328,19 +345,14 @@ __global__ void __launch_bounds__(kTilePix, 2)
         }
 
         if (in.k == p.n_tau - 1) {
-            // last frame of the window for this tile: reduce, solve, emit
-            if (!kDense && g > 1) {
-                for (int off = g >> 1; off >= 1; off >>= 1) {
-#pragma unroll
-                    for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
-#pragma unroll
-                    for (int i = 0; i < NZ; ++i) acc.B[i] += __shfl_xor_sync(0xffffffffu, acc.B[i], off);
+            // last frame of the window for this tile: reduce and store the sums
+            if (!kDense && g > 1) accp_reduce(acc, g);
+            if (active) {
+                accp_store(acc, p.gram + (size_t)entry * kGramStride, sub, g);
+                if (sub == 0) {
+                    atomicAdd(&s_pairs, (unsigned long long)((dxhi - dxlo + 1) * (dyhi - dylo + 1) * p.n_tau));
+                    atomicAdd(&s_pix, 1ull);
                 }
-            }
-            if (active && sub == 0) {
-                atomicAdd(&s_pairs, (unsigned long long)((dxhi - dxlo + 1) * (dyhi - dylo + 1) * p.n_tau));
-                atomicAdd(&s_pix, 1ull);
-                solve_and_emit<kMixed>(p, acc, cx, cy, &s_fp64);
             }
         }
     }
@@ -354,45 +366,59 @@ __global__ void __launch_bounds__(kTilePix, 2)
         }
     }
     __syncthreads();   // every thread's counter updates are in before thread 0 reads them
-    finish(p, s_pairs, s_pix, s_fp64, timed_out || (threadIdx.x == 0 && !pr->ok));
+    finish(p, s_pairs, s_pix, 0ull, timed_out || (threadIdx.x == 0 && !pr->ok), false);
 }
 
-// Sparse-frame regression.  When few pixels are flagged they lie on thin
-// feature edges, a handful per tile, and staging a whole tile window per work
-// item would move far more data than it feeds.  Here each warp takes four
-// consecutive entries of the frame's flagged list (the test kernel pads every
-// tile's run to a multiple of four, so the four pixels share a tile and are
-// usually adjacent along an edge), 8 lanes per pixel (16 or 32 when the item
-// holds only two or one pixel, the tail of a tile's run).  For each frame of the
-// temporal window the warp copies the bounding box of its pixels' windows
-// from the ring into its own shared-memory buffer with 16-byte asynchronous
-// copies (and hints the next frame's box into L2), then the lanes split each
-// window's offsets and accumulate from shared memory; boxes too large for the
-// buffer are read through L1 instead.  Warps fetch work independently; there
-// is no block barrier inside the loop.
+// Sparse-frame regression (accumulation; wlr_solve_kernel solves and emits).
+// When few pixels are flagged they lie on thin feature edges, a handful per
+// tile, and staging a whole tile window per work item would move far more
+// data than it feeds.  Here each warp takes four consecutive entries of the
+// frame's flagged list (the test kernel pads every tile's run to a multiple
+// of four, so the four pixels share a tile and are usually adjacent along an
+// edge), 8 lanes per pixel (16 or 32 when the item holds only two or one
+// pixel, the tail of a tile's run).  For each frame of the temporal window the
+// bounding box of the four windows (clipped to the image) is copied from the
+// ring into the warp's shared memory by bulk asynchronous copies (the TMA
+// engine, one row per lane, completing on the warp's mbarrier).  Boxes of up
+// to 20 x 20 records are double-buffered: frame k+1's copy is issued before
+// frame k is summed.  Larger boxes take the whole buffer one frame at a time;
+// boxes too large for it are read through L1.  The lanes split each window's
+// offsets and accumulate the 65 sums in packed FP32 pairs; the g lanes of a
+// pixel are then reduced by shuffles and store one Gram record at the pixel's
+// position in the flagged list.  Warps fetch work independently; there is no
+// block barrier inside the loop, and every mbarrier wait is bounded.
 template <bool kMixed>
 __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams p)
 {
     if (p.sparse_max == 0 || *(volatile uint32_t*)&p.ctrl->flag_total > p.sparse_max)
         return;  // the tile-staged kernel's frame
-    using S = SparseStage<kMixed>;
-    extern __shared__ __align__(16) unsigned char sm[];
-    const SparseLayout L = sparse_layout(p.r, kMixed);
-    float4* table = reinterpret_cast<float4*>(sm);
-    const bool can_stage = L.buf_bytes > 0 && p.sparse_stage;
-    __shared__ unsigned long long s_pairs, s_pix, s_fp64;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const BoxLayout L = box_layout(p.r);
+    __shared__ unsigned long long s_pairs, s_pix;
     const int side = 2 * p.r + 1, nq = side * side;
     const float spx = p.s_coord_px;
     const size_t N = (size_t)p.W * p.H;
+    // window tables (u_dx, u_dy, -(u_dx^2 + u_dy^2), box offset) for the two row pitches
+    float4* tab_s = reinterpret_cast<float4*>(sm + L.tab_small);
+    float4* tab_l = reinterpret_cast<float4*>(sm + L.tab_large);
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
         const int ox = q % side - p.r, oy = q / side - p.r;
         const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-        table[q] = make_float4(__int_as_float(oy * S::pitch + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
+        const float en0 = -fmaf(u1, u1, u2 * u2);
+        tab_s[q] = make_float4(u1, u2, en0, __int_as_float(oy * kPitchSmall + ox));
+        tab_l[q] = make_float4(u1, u2, en0, __int_as_float(oy * kPitchLarge + ox));
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar_off) + 2 * warp;
+    unsigned char* wbuf = sm + L.buf_off + warp * kBoxBytes;
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
         s_pix = 0ull;
-        s_fp64 = 0ull;
+    }
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
     const uint32_t n_list = *(volatile uint32_t*)&p.ctrl->list_len;
@@ -401,14 +427,12 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
     const float* sf = kMixed ? p.q_scale : p.s_feat;
     const float4* ringf = reinterpret_cast<const float4*>(p.ring);
     const uint4* ringm = reinterpret_cast<const uint4*>(p.ring);
-    const int lane = threadIdx.x & 31;
     const int slot_t = p.t % p.T;
-    unsigned char* wbuf = sm + L.buf_off + (threadIdx.x >> 5) * L.buf_bytes;
-    uint4* bufm = reinterpret_cast<uint4*>(wbuf);
-    float4* buf0 = reinterpret_cast<float4*>(wbuf);
-    float4* buf1 = buf0 + S::pitch * S::rows;
-    Acc acc;
-    float cf[7];
+    const uint32_t poll = p.poll_limit;
+    uint32_t phase = 0u;        // bit b: parity of bar[b]'s next phase completion
+    bool timed_out = false;
+    bool first_item = true;
+    AccP acc;
     for (;;) {
         // Four-entry items until the last stretch of the list; that stretch
         // (half an item per warp of the grid) goes out one pixel at a time, so
@@ -432,14 +456,11 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         const int lg = m >= 3 ? 3 : 6 - m;
         const int g = 1 << lg;
         const int grp = lane >> lg, sub = lane & (g - 1);
-        const uint32_t entry = __shfl_sync(0xffffffffu, e4, grp);
+        const uint32_t pix_e = __shfl_sync(0xffffffffu, e4, grp);
         const bool active = grp < m;
-        const uint32_t pix = active ? entry : 0u;
+        const uint32_t pix = active ? pix_e : 0u;
+        const uint32_t entry = base + (uint32_t)grp;
         const int cx = (int)(pix % (uint32_t)p.W), cy = (int)(pix / (uint32_t)p.W);
-#pragma unroll
-        for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
-#pragma unroll
-        for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
         const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
         const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
         const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
@@ -449,67 +470,86 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         const int bx1 = __reduce_max_sync(0xffffffffu, active ? cx + dxhi : -1);
         const int by1 = __reduce_max_sync(0xffffffffu, active ? cy + dyhi : -1);
         const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
-        const bool staged = can_stage && bw > 0 && bw <= S::pitch && bh <= S::rows;   // warp-uniform
-        if (active) {
-            float c[7];
-            if (kMixed) {
-                float yc;
-                unpack_mixed(__ldg(ringm + (size_t)slot_t * N + pix), yc, c);
-            } else {
-                const float4 c0 = __ldg(ringf + (size_t)(2 * slot_t) * N + pix);
-                const float4 c1 = __ldg(ringf + (size_t)(2 * slot_t + 1) * N + pix);
-                c[0] = c0.y; c[1] = c0.z; c[2] = c0.w; c[3] = c1.x; c[4] = c1.y; c[5] = c1.z; c[6] = c1.w;
+        // 2: double-buffered halves, 1: whole buffer, 0: windows read through L1 (warp-uniform)
+        int mode = 0;
+        if (p.sparse_stage) {
+            if (kMixed && bw <= kPitchSmall && bh <= kRowsSmall) mode = 2;
+            else if (kMixed && bw <= kPitchLarge && bh <= kRowsLarge) mode = 1;
+            else if (!kMixed && bw <= kPitchSmall && bh <= kRowsSmall) mode = 1;
+        }
+        const int P = (mode == 2 || !kMixed) ? kPitchSmall : kPitchLarge;
+        const float4* tab = P == kPitchSmall ? tab_s : tab_l;
+        PairConst kc;
+        {
+            float c[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (active) {
+                if (kMixed) {
+                    float yc;
+                    unpack_mixed(__ldg(ringm + (size_t)slot_t * N + pix), yc, c);
+                } else {
+                    const float4 c0 = __ldg(ringf + (size_t)(2 * slot_t) * N + pix);
+                    const float4 c1 = __ldg(ringf + (size_t)(2 * slot_t + 1) * N + pix);
+                    c[0] = c0.y; c[1] = c0.z; c[2] = c0.w; c[3] = c1.x; c[4] = c1.y; c[5] = c1.z; c[6] = c1.w;
+                }
             }
+            float cf[7];
 #pragma unroll
             for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
+            kc = pair_const(sf, cf);
         }
-        const bool interior = nx == side && ny == side;
-        for (int k = 0; k < p.n_tau; ++k) {
+        accp_zero(acc);
+        // Copy frame k of the box into half b (mode 2) or the whole buffer
+        // (mode 1).  Every lane is past its reads of that region first.
+        auto issue = [&](int b, int k) {
+            __syncwarp();
+            fence_proxy_async_smem();
+            if (p.withhold_copy && first_item && k == 0) return;   // test: this phase never completes
             const int slot = (p.t - k) % p.T;
-            if (staged) {
-                // box of this frame -> the warp's buffer (bw <= 32: one record per lane per row)
-                __syncwarp();   // every lane is done with the previous frame's box
-                const size_t row0 = (size_t)by0 * p.W + bx0 + lane;
-                if (lane < bw) {
-                    for (int i = 0; i < bh; ++i) {
-                        const size_t g = row0 + (size_t)i * p.W;
-                        if (kMixed) {
-                            cp_async16(bufm + i * S::pitch + lane, ringm + (size_t)slot * N + g);
-                        } else {
-                            cp_async16(buf0 + i * S::pitch + lane, ringf + (size_t)(2 * slot) * N + g);
-                            cp_async16(buf1 + i * S::pitch + lane, ringf + (size_t)(2 * slot + 1) * N + g);
-                        }
-                    }
+            const uint32_t rowb = (uint32_t)bw * 16u;
+            if (lane == 0) mbar_arrive_expect_tx(&bar[b], (uint32_t)bh * rowb * (kMixed ? 1u : 2u));
+            __syncwarp();
+            if (lane < bh) {
+                const size_t gi = (size_t)(by0 + lane) * p.W + bx0;
+                unsigned char* dst = wbuf + (mode == 2 ? b * (kBoxBytes / 2) : 0) + lane * P * 16;
+                if (kMixed) {
+                    bulk_load(dst, ringm + (size_t)slot * N + gi, rowb, &bar[b]);
+                } else {
+                    bulk_load(dst, ringf + (size_t)(2 * slot) * N + gi, rowb, &bar[b]);
+                    bulk_load(dst + kBoxBytes / 2, ringf + (size_t)(2 * slot + 1) * N + gi, rowb, &bar[b]);
                 }
-                if (k + 1 < p.n_tau) {
-                    // hint the next frame's box into L2 while this one lands and is summed
-                    const int nslot = (p.t - k - 1) % p.T;
-                    const int lines = (bw * S::rec + 127) >> 7;
-                    for (int j = lane; j < bh * lines; j += 32) {
-                        const int i = j / lines, l = j - i * lines;
-                        const size_t g = (size_t)(by0 + i) * p.W + bx0;
-                        const char* row = kMixed
-                            ? reinterpret_cast<const char*>(ringm + (size_t)nslot * N + g)
-                            : reinterpret_cast<const char*>(ringf + (size_t)(2 * nslot) * N + g);
-                        prefetch_l2(row + l * 128);
-                        if (!kMixed) prefetch_l2(row + (size_t)N * 16 + l * 128);
-                    }
+            }
+        };
+        const bool interior = nx == side && ny == side;
+        if (mode) issue(0, 0);
+        for (int k = 0; k < p.n_tau; ++k) {
+            if (mode) {
+                const int b = mode == 2 ? (k & 1) : 0;
+                const bool ahead = mode == 2 && k + 1 < p.n_tau;
+                if (ahead) issue(b ^ 1, k + 1);
+                const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[b], (phase >> b) & 1u, poll));
+                phase ^= 1u << b;
+                if (!ok) {
+                    // give the copies still in flight a bounded chance to land, then stop
+                    mbar_wait_bounded(&bar[b], ((phase >> b) & 1u) ^ 1u, poll);
+                    if (ahead) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u, poll);
+                    timed_out = true;
+                    break;
                 }
-                cp_async_wait_all();
-                __syncwarp();   // the box is visible to every lane of the warp
+                const unsigned char* buf = wbuf + (mode == 2 ? b * (kBoxBytes / 2) : 0);
+                auto at = [&](int si, float u1, float u2, float en0) {
+                    if (kMixed)
+                        accp(acc, reinterpret_cast<const uint4*>(buf)[si], make_float2(u1, u2), en0, kc);
+                    else
+                        accp(acc, reinterpret_cast<const float4*>(buf)[si],
+                             reinterpret_cast<const float4*>(buf + kBoxBytes / 2)[si], make_float2(u1, u2), en0, kc);
+                };
                 if (active) {
-                    const int cb = (cy - by0) * S::pitch + (cx - bx0);
-                    auto at = [&](int si, float u1, float u2, float en0) {
-                        if (kMixed)
-                            accumulate(acc, bufm[si], u1, u2, en0, sf, cf);
-                        else
-                            accumulate(acc, buf0[si], buf1[si], u1, u2, en0, sf, cf);
-                    };
+                    const int cb = (cy - by0) * P + (cx - bx0);
                     if (interior) {
 #pragma unroll 1
                         for (int q = sub; q < nq; q += g) {
-                            const float4 e = table[q];
-                            at(cb + __float_as_int(e.x), e.y, e.z, e.w);
+                            const float4 e = tab[q];
+                            at(cb + __float_as_int(e.w), e.x, e.y, e.z);
                         }
                     } else {
                         const int nvalid = nx * ny;
@@ -518,7 +558,7 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
 #pragma unroll 1
                         for (int q = sub; q < nvalid; q += g) {
                             const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-                            at(cb + oy * S::pitch + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
+                            at(cb + oy * P + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
                             ox += g;
                             while (ox > dxhi) {
                                 ox -= nx;
@@ -527,25 +567,24 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
                         }
                     }
                 }
+                if (mode == 1 && k + 1 < p.n_tau) issue(0, k + 1);
             } else if (active) {
                 // box too large for the buffer: read the windows through L1
+                const int slot = (p.t - k) % p.T;
                 const float4* __restrict__ R0 = ringf + (size_t)(2 * slot) * N + pix;
                 const float4* __restrict__ R1 = ringf + (size_t)(2 * slot + 1) * N + pix;
                 const uint4* __restrict__ RM = ringm + (size_t)slot * N + pix;
-                auto at = [&](int d, float u1, float u2, float en0) {
-                    if (kMixed)
-                        accumulate(acc, __ldg(RM + d), u1, u2, en0, sf, cf);
-                    else
-                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, en0, sf, cf);
-                };
-                // (rare: the window walked offset by offset, clipped or not)
                 const int nvalid = nx * ny;
                 int ox = dxlo + sub % nx;
                 int oy = dylo + sub / nx;
 #pragma unroll 1
                 for (int q = sub; q < nvalid; q += g) {
                     const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-                    at(oy * p.W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
+                    const int d = oy * p.W + ox;
+                    if (kMixed)
+                        accp(acc, __ldg(RM + d), make_float2(u1, u2), -fmaf(u1, u1, u2 * u2), kc);
+                    else
+                        accp(acc, __ldg(R0 + d), __ldg(R1 + d), make_float2(u1, u2), -fmaf(u1, u1, u2 * u2), kc);
                     ox += g;
                     while (ox > dxhi) {
                         ox -= nx;
@@ -554,24 +593,217 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
                 }
             }
         }
-#pragma unroll
-        for (int off = g >> 1; off >= 1; off >>= 1) {
-#pragma unroll
-            for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
-#pragma unroll
-            for (int i = 0; i < NZ; ++i) acc.B[i] += __shfl_xor_sync(0xffffffffu, acc.B[i], off);
-        }
-        if (active && sub == 0) {
-            atomicAdd(&s_pairs, (unsigned long long)(nx * ny * p.n_tau));
-            atomicAdd(&s_pix, 1ull);
-            solve_and_emit<kMixed, true>(p, acc, cx, cy, &s_fp64);
+        first_item = false;
+        if (timed_out) break;
+        accp_reduce(acc, g);
+        if (active) {
+            accp_store(acc, p.gram + (size_t)entry * kGramStride, sub, g);
+            if (sub == 0) {
+                atomicAdd(&s_pairs, (unsigned long long)(nx * ny * p.n_tau));
+                atomicAdd(&s_pix, 1ull);
+            }
         }
     }
     __syncthreads();
-    finish(p, s_pairs, s_pix, s_fp64, false);
+    finish(p, s_pairs, s_pix, 0ull, timed_out, false);
 }
 
-int wlr_sparse_smem(int r, bool mixed) { return sparse_layout(r, mixed).total; }
+constexpr int kSolveThreads = 256;
+
+// Error-free sum of two floats (Knuth's TwoSum): s + err == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    err = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+}
+
+// Ill-conditioned system of pixel pix, one warp: the 65 sums are accumulated
+// again from the ring with compensated FP32 arithmetic (each product term
+// rounded once, each running sum carried as an unevaluated pair hi + lo by
+// TwoSum; feature differences taken before scaling, which is exact for the
+// stored BF16 values), lane l owning sums l, l + 32 and l + 64 (sums 0-54 are
+// the Gram triangle in tri() order, 55-64 the right-hand side).  Lane 0 then
+// adds the ridge and solves the equilibrated system by Cholesky in FP64 and
+// emits.  sys: 66 doubles of this warp's shared memory.
+template <bool kMixed>
+__device__ __noinline__ void refine_fp64(const WlrParams& p, uint32_t pix, const float (&s2)[NZ], double* sys)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t N = (size_t)p.W * p.H;
+    const int cx = (int)(pix % (uint32_t)p.W), cy = (int)(pix / (uint32_t)p.W);
+    const float* sf = kMixed ? p.q_scale : p.s_feat;
+    const float4* ringf = reinterpret_cast<const float4*>(p.ring);
+    const uint4* ringm = reinterpret_cast<const uint4*>(p.ring);
+    auto load = [&](int slot, size_t i, float& y, float (&f)[7]) {
+        if (kMixed) {
+            unpack_mixed(__ldg(ringm + (size_t)slot * N + i), y, f);
+        } else {
+            const float4 a = __ldg(ringf + (size_t)(2 * slot) * N + i);
+            const float4 b = __ldg(ringf + (size_t)(2 * slot + 1) * N + i);
+            y = a.x; f[0] = a.y; f[1] = a.z; f[2] = a.w; f[3] = b.x; f[4] = b.y; f[5] = b.z; f[6] = b.w;
+        }
+    };
+    float yc, c[7];
+    load(p.t % p.T, pix, yc, c);
+    // the (row, column) of each owned sum; column 10 is the log brightness
+    int oi[3], oj[3];
+    float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        const int idx = lane + 32 * o;
+        int i = 0, j = 0;
+        if (idx < NG) {
+            while (tri(i + 1, 0) <= idx) ++i;
+            j = idx - tri(i, 0);
+        } else if (idx < NG + NZ) {
+            i = 10;
+            j = idx - NG;
+        } else {
+            i = -1;
+        }
+        oi[o] = i;
+        oj[o] = j;
+    }
+    const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
+    const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
+    for (int k = 0; k < p.n_tau; ++k) {
+        const int slot = (p.t - k) % p.T;
+        for (int oy = dylo; oy <= dyhi; ++oy) {
+            for (int ox = dxlo; ox <= dxhi; ++ox) {
+                float y, f[7];
+                load(slot, (size_t)(cy + oy) * p.W + cx + ox, y, f);
+                float z[NZ + 1];
+                z[0] = 1.0f;
+                z[1] = __fmul_rn((float)ox, p.s_coord_px);
+                z[2] = __fmul_rn((float)oy, p.s_coord_px);
+#pragma unroll
+                for (int j = 0; j < 7; ++j) z[3 + j] = __fmul_rn(__fadd_rn(f[j], -c[j]), sf[j]);
+                z[NZ] = y;
+                float en = 0.0f;
+#pragma unroll
+                for (int j = 1; j < NZ; ++j) en = fmaf(-z[j], z[j], en);
+                const float w = exp2f(en);
+#pragma unroll
+                for (int o = 0; o < 3; ++o) {
+                    if (oi[o] < 0) continue;
+                    const float t = __fmul_rn(__fmul_rn(w, z[oi[o]]), z[oj[o]]);
+                    float sum, err;
+                    two_sum(hi[o], t, sum, err);
+                    hi[o] = sum;
+                    lo[o] = __fadd_rn(lo[o], err);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+        if (oi[o] >= 0) sys[lane + 32 * o] = (double)hi[o] + (double)lo[o];
+    __syncwarp();
+    if (lane == 0) {
+        double A[NG], b[NZ], dsc[NZ];
+        for (int i = 0; i < NG; ++i) A[i] = sys[i];
+        for (int i = 0; i < NZ; ++i) b[i] = sys[NG + i];
+        const double Wsum = A[0];
+        for (int j = 1; j < NZ; ++j) A[tri(j, j)] += (double)p.ridge * Wsum * (double)s2[j];
+        for (int i = 0; i < NZ; ++i) dsc[i] = 1.0 / sqrt(A[tri(i, i)]);
+        for (int i = 0; i < NZ; ++i) {
+            for (int j = 0; j <= i; ++j) A[tri(i, j)] *= dsc[i] * dsc[j];
+            b[i] *= dsc[i];
+        }
+        double dinv[NZ], zz[NZ], x[NZ];
+        for (int j = 0; j < NZ; ++j) {
+            double sj = A[tri(j, j)];
+            for (int k = 0; k < j; ++k) sj -= A[tri(j, k)] * A[tri(j, k)];
+            sj = sj > 1e-300 ? sj : 1e-300;
+            const double l = sqrt(sj);
+            A[tri(j, j)] = l;
+            dinv[j] = 1.0 / l;
+            for (int i = j + 1; i < NZ; ++i) {
+                double v = A[tri(i, j)];
+                for (int k = 0; k < j; ++k) v -= A[tri(i, k)] * A[tri(j, k)];
+                A[tri(i, j)] = v * dinv[j];
+            }
+        }
+        for (int i = 0; i < NZ; ++i) {
+            double v = b[i];
+            for (int k = 0; k < i; ++k) v -= A[tri(i, k)] * zz[k];
+            zz[i] = v * dinv[i];
+        }
+        for (int i = NZ - 1; i >= 0; --i) {
+            double v = zz[i];
+            for (int k = i + 1; k < NZ; ++k) v -= A[tri(k, i)] * x[k];
+            x[i] = v * dinv[i];
+        }
+        float theta[NZ];
+        for (int i = 0; i < NZ; ++i) theta[i] = (float)(x[i] * dsc[i]);
+        emit<kMixed>(p, cx, cy, theta);
+    }
+    __syncwarp();
+}
+
+// Solve and emit (Eqs. 4-5 and Eq. 1) for every Gram record of the frame:
+// one thread per record (pixel index in dense frames, flagged-list position
+// otherwise; list padding is skipped).  FP32 form: equilibrated FP32
+// Cholesky.  Mixed form: FP32 Cholesky plus one refinement step; systems
+// whose condition estimate exceeds 1e6 are set aside and, after each pass of
+// the block, re-accumulated by one warp each with compensated FP32 sums and
+// solved by FP64 Cholesky (refine_fp64).  The last CTA scans the per-chunk
+// event counts for the ordered writer.
+template <bool kMixed>
+__global__ void __launch_bounds__(kSolveThreads) wlr_solve_kernel(const WlrParams p)
+{
+    __shared__ uint32_t s_ill[kSolveThreads];
+    __shared__ int s_nill;
+    __shared__ unsigned long long s_fp64;
+    __shared__ double s_sys[kSolveThreads / 32][66];
+    if (threadIdx.x == 0) {
+        s_nill = 0;
+        s_fp64 = 0ull;
+    }
+    __syncthreads();
+    const uint32_t n = p.dense ? (uint32_t)((size_t)p.W * p.H) : *(volatile uint32_t*)&p.ctrl->list_len;
+    float s2[NZ];
+    s2[0] = 0.0f;
+    s2[1] = p.s_coord * p.s_coord;
+    s2[2] = s2[1];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) s2[3 + j] = p.s_feat[j] * p.s_feat[j];
+    const uint32_t stride = gridDim.x * kSolveThreads;
+    for (uint32_t b0 = blockIdx.x * kSolveThreads; b0 < n; b0 += stride) {   // same trip count in the block
+        const uint32_t e = b0 + threadIdx.x;
+        uint32_t pix = kListPad;
+        if (e < n) pix = p.dense ? e : p.flag_list[e];
+        if (pix != kListPad) {
+            Acc acc;
+            gram_load(p.gram + (size_t)e * kGramStride, acc);
+            float theta[NZ];
+            bool ok = true;
+            if (kMixed) ok = solve_refined(acc, s2, p.ridge, theta);
+            else solve(acc, s2, p.ridge, theta);
+            if (ok) emit<kMixed>(p, (int)(pix % (uint32_t)p.W), (int)(pix / (uint32_t)p.W), theta);
+            else s_ill[atomicAdd(&s_nill, 1)] = pix;
+        }
+        if (kMixed) {
+            __syncthreads();
+            const int nill = s_nill;
+            if (nill > 0) {
+                for (int i = (int)(threadIdx.x >> 5); i < nill; i += kSolveThreads / 32)
+                    refine_fp64<kMixed>(p, s_ill[i], s2, s_sys[threadIdx.x >> 5]);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    s_fp64 += (unsigned long long)nill;
+                    s_nill = 0;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    finish(p, 0ull, 0ull, s_fp64, false, true);
+}
+
+int wlr_sparse_smem(int r, bool /*mixed*/) { return box_layout(r).total; }
 
 cudaError_t wlr_sparse_prepare(int r, bool mixed)
 {
@@ -601,6 +833,17 @@ cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStre
         wlr_sparse_kernel<true><<<grid, kTilePix, bytes, s>>>(p);
     else
         wlr_sparse_kernel<false><<<grid, kTilePix, bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+int wlr_solve_grid(int num_sms) { return 8 * num_sms; }
+
+cudaError_t launch_wlr_solve(const WlrParams& p, bool mixed, int grid, cudaStream_t s)
+{
+    if (mixed)
+        wlr_solve_kernel<true><<<grid, kSolveThreads, 0, s>>>(p);
+    else
+        wlr_solve_kernel<false><<<grid, kSolveThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
