@@ -54,8 +54,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_v else []
 
+    headers = [d for d in _deps() if not d.endswith(".cu")]
+    newest_header = max(os.path.getmtime(h) for h in headers)
+
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        if not force and not ptxas_v and os.path.exists(obj) and \
+                os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header):
+            return obj   # object newer than its source and every header
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

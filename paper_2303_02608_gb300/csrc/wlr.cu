@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     const int row = (sy + oy) * p.sw + sx;
                     float u1 = (float)dxlo * spx;
                     // the mixed form's larger loop body runs faster without unrolling
-                    constexpr int kRowUnroll = kMixed ? 1 : 3;
+                    constexpr int kRowUnroll = 1;
 #pragma unroll kRowUnroll
                     for (int ox = dxlo; ox <= dxhi; ++ox) {
                         at(row + ox, u1, u2, fmaf(-u1, u1, en_row));
@@ -453,30 +453,52 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
         // 8 lanes per pixel for m = 3, 4, 16 for m = 2, 32 for m = 1
         const int m = __popc(__ballot_sync(0xffffffffu, e4 != kListPad) & 0xfu);
         if (m == 0) continue;   // a padding entry of the tail
-        const int lg = m >= 3 ? 3 : 6 - m;
+        // The m pixels go together when the bounding box of their windows fits
+        // the buffer; otherwise (pixels spread across their tile) one at a
+        // time with all 32 lanes, each pass staging its own window.
+        auto box_mode = [&](int bw, int bh) {   // 2: double-buffered halves, 1: whole buffer, 0: none
+            if (!p.sparse_stage) return 0;
+            if (kMixed && bw <= kPitchSmall && bh <= kRowsSmall) return 2;
+            if (kMixed && bw <= kPitchLarge && bh <= kRowsLarge) return 1;
+            if (!kMixed && bw <= kPitchSmall && bh <= kRowsSmall) return 1;
+            return 0;
+        };
+        int passes = 1;
+        bool split = false;
+        if (m > 1 && p.sparse_stage && side <= kPitchSmall) {
+            const int lg0 = m >= 3 ? 3 : 6 - m;
+            const int grp0 = lane >> lg0;
+            const bool act0 = grp0 < m;
+            const uint32_t px0 = __shfl_sync(0xffffffffu, e4, grp0);
+            const int x0 = (int)(px0 % (uint32_t)p.W), y0 = (int)(px0 / (uint32_t)p.W);
+            const int ux0 = __reduce_min_sync(0xffffffffu, act0 ? max(x0 - p.r, 0) : 0x7fffffff);
+            const int uy0 = __reduce_min_sync(0xffffffffu, act0 ? max(y0 - p.r, 0) : 0x7fffffff);
+            const int ux1 = __reduce_max_sync(0xffffffffu, act0 ? min(x0 + p.r, p.W - 1) : -1);
+            const int uy1 = __reduce_max_sync(0xffffffffu, act0 ? min(y0 + p.r, p.H - 1) : -1);
+            if (box_mode(ux1 - ux0 + 1, uy1 - uy0 + 1) == 0) {
+                split = true;
+                passes = m;
+            }
+        }
+        for (int part = 0; part < passes; ++part) {
+        const int lg = split ? 5 : (m >= 3 ? 3 : 6 - m);
         const int g = 1 << lg;
-        const int grp = lane >> lg, sub = lane & (g - 1);
-        const uint32_t pix_e = __shfl_sync(0xffffffffu, e4, grp);
+        const int grp = split ? 0 : lane >> lg, sub = lane & (g - 1);
+        const uint32_t pix_e = __shfl_sync(0xffffffffu, e4, split ? part : grp);
         const bool active = grp < m;
         const uint32_t pix = active ? pix_e : 0u;
-        const uint32_t entry = base + (uint32_t)grp;
+        const uint32_t entry = base + (uint32_t)(split ? part : grp);
         const int cx = (int)(pix % (uint32_t)p.W), cy = (int)(pix / (uint32_t)p.W);
         const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
         const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
         const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
-        // bounding box of the warp's windows (clipped to the image)
+        // bounding box of the pass's windows (clipped to the image)
         const int bx0 = __reduce_min_sync(0xffffffffu, active ? cx + dxlo : 0x7fffffff);
         const int by0 = __reduce_min_sync(0xffffffffu, active ? cy + dylo : 0x7fffffff);
         const int bx1 = __reduce_max_sync(0xffffffffu, active ? cx + dxhi : -1);
         const int by1 = __reduce_max_sync(0xffffffffu, active ? cy + dyhi : -1);
         const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
-        // 2: double-buffered halves, 1: whole buffer, 0: windows read through L1 (warp-uniform)
-        int mode = 0;
-        if (p.sparse_stage) {
-            if (kMixed && bw <= kPitchSmall && bh <= kRowsSmall) mode = 2;
-            else if (kMixed && bw <= kPitchLarge && bh <= kRowsLarge) mode = 1;
-            else if (!kMixed && bw <= kPitchSmall && bh <= kRowsSmall) mode = 1;
-        }
+        const int mode = box_mode(bw, bh);   // warp-uniform; 0: windows read through L1
         const int P = (mode == 2 || !kMixed) ? kPitchSmall : kPitchLarge;
         const float4* tab = P == kPitchSmall ? tab_s : tab_l;
         PairConst kc;
@@ -603,12 +625,14 @@ __global__ void __launch_bounds__(kTilePix, 2) wlr_sparse_kernel(const WlrParams
                 atomicAdd(&s_pix, 1ull);
             }
         }
+        }   // passes
+        if (timed_out) break;
     }
     __syncthreads();
     finish(p, s_pairs, s_pix, 0ull, timed_out, false);
 }
 
-constexpr int kSolveThreads = 256;
+constexpr int kSolveThreads = 128;
 
 // Error-free sum of two floats (Knuth's TwoSum): s + err == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err)
@@ -751,7 +775,7 @@ __device__ __noinline__ void refine_fp64(const WlrParams& p, uint32_t pix, const
 // solved by FP64 Cholesky (refine_fp64).  The last CTA scans the per-chunk
 // event counts for the ordered writer.
 template <bool kMixed>
-__global__ void __launch_bounds__(kSolveThreads) wlr_solve_kernel(const WlrParams p)
+__global__ void __launch_bounds__(kSolveThreads, 4) wlr_solve_kernel(const WlrParams p)
 {
     __shared__ uint32_t s_ill[kSolveThreads];
     __shared__ int s_nill;
@@ -774,29 +798,30 @@ __global__ void __launch_bounds__(kSolveThreads) wlr_solve_kernel(const WlrParam
         const uint32_t e = b0 + threadIdx.x;
         uint32_t pix = kListPad;
         if (e < n) pix = p.dense ? e : p.flag_list[e];
+        bool ill = false;
         if (pix != kListPad) {
-            Acc acc;
-            gram_load(p.gram + (size_t)e * kGramStride, acc);
+            const float* rec = p.gram + (size_t)e * kGramStride;
             float theta[NZ];
-            bool ok = true;
-            if (kMixed) ok = solve_refined(acc, s2, p.ridge, theta);
-            else solve(acc, s2, p.ridge, theta);
-            if (ok) emit<kMixed>(p, (int)(pix % (uint32_t)p.W), (int)(pix / (uint32_t)p.W), theta);
+            if (kMixed) {
+                ill = !solve_refined_rec(rec, s2, p.ridge, theta);
+            } else {
+                Acc acc;
+                gram_load(rec, acc);
+                solve(acc, s2, p.ridge, theta);
+            }
+            if (!ill) emit<kMixed>(p, (int)(pix % (uint32_t)p.W), (int)(pix / (uint32_t)p.W), theta);
             else s_ill[atomicAdd(&s_nill, 1)] = pix;
         }
-        if (kMixed) {
-            __syncthreads();
+        if (kMixed && __syncthreads_or(ill)) {
             const int nill = s_nill;
-            if (nill > 0) {
-                for (int i = (int)(threadIdx.x >> 5); i < nill; i += kSolveThreads / 32)
-                    refine_fp64<kMixed>(p, s_ill[i], s2, s_sys[threadIdx.x >> 5]);
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    s_fp64 += (unsigned long long)nill;
-                    s_nill = 0;
-                }
-                __syncthreads();
+            for (int i = (int)(threadIdx.x >> 5); i < nill; i += kSolveThreads / 32)
+                refine_fp64<kMixed>(p, s_ill[i], s2, s_sys[threadIdx.x >> 5]);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_fp64 += (unsigned long long)nill;
+                s_nill = 0;
             }
+            __syncthreads();
         }
     }
     __syncthreads();
@@ -836,7 +861,7 @@ cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStre
     return cudaGetLastError();
 }
 
-int wlr_solve_grid(int num_sms) { return 8 * num_sms; }
+int wlr_solve_grid(int num_sms) { return 4 * num_sms; }   // one wave at 4 CTAs per SM
 
 cudaError_t launch_wlr_solve(const WlrParams& p, bool mixed, int grid, cudaStream_t s)
 {

@@ -74,14 +74,16 @@ __device__ __forceinline__ void accum_core(Acc& a, float y, float f0, float f1, 
 // With wQ_k = w Q_k the sums are
 //     g0 = sum w,  r_k = sum wQ_k,  s_k = sum wQ_k * Q_k,  x_k = sum wQ_k.x Q_k.y
 //     d_b = sum wQ_k * Q_m,  c_b = sum wQ_k * swap(Q_m)      (k > m, b = k(k-1)/2 + m)
-// (s_4.x = sum w y^2 is not needed and is ignored).  A Gram record stores them
-// in that order: g0, r[5], d[10], c[10], s[5], x[5] = 66 floats, padded to 68.
+// (s_4.x = sum w y^2 is not needed: only s_4.y = sum w u_nx^2 is kept, as s4).
+// A Gram record stores them in that order: g0, r[5], d[10], c[10], s[5] (with
+// s_4.x = 0), x[5] = 66 floats, padded to 68.
 struct AccP {
     float g0;
     float2 r[5];
     float2 d[10];
     float2 c[10];
-    float2 s[5];
+    float2 s[4];
+    float s4;
     float x[5];
 };
 constexpr int kGramFloats = 66;
@@ -98,10 +100,11 @@ struct PairConst {
 __device__ __forceinline__ void accp_zero(AccP& a)
 {
     a.g0 = 0.0f;
+    a.s4 = 0.0f;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         a.r[k] = make_float2(0.0f, 0.0f);
-        a.s[k] = make_float2(0.0f, 0.0f);
+        if (k < 4) a.s[k] = make_float2(0.0f, 0.0f);
         a.x[k] = 0.0f;
     }
 #pragma unroll
@@ -161,10 +164,10 @@ __device__ __forceinline__ void accp_core(AccP& a, float2 q0, float en0, float y
         }
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        a.s[i] = __ffma2_rn(wQ[i], Q[i], a.s[i]);
-        a.x[i] = fmaf(wQ[i].x, Q[i].y, a.x[i]);
-    }
+    for (int i = 0; i < 4; ++i) a.s[i] = __ffma2_rn(wQ[i], Q[i], a.s[i]);
+    a.s4 = fmaf(wQ[4].y, unx, a.s4);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a.x[i] = fmaf(wQ[i].x, Q[i].y, a.x[i]);
 }
 
 // FP32 ring: h0 = (y, n_x, n_y, n_z), h1 = (d, a_r, a_g, a_b).
@@ -190,12 +193,15 @@ __device__ __forceinline__ void accp_reduce(AccP& a, int g)
 {
     for (int off = g >> 1; off >= 1; off >>= 1) {
         a.g0 += __shfl_xor_sync(0xffffffffu, a.g0, off);
+        a.s4 += __shfl_xor_sync(0xffffffffu, a.s4, off);
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             a.r[i].x += __shfl_xor_sync(0xffffffffu, a.r[i].x, off);
             a.r[i].y += __shfl_xor_sync(0xffffffffu, a.r[i].y, off);
-            a.s[i].x += __shfl_xor_sync(0xffffffffu, a.s[i].x, off);
-            a.s[i].y += __shfl_xor_sync(0xffffffffu, a.s[i].y, off);
+            if (i < 4) {
+                a.s[i].x += __shfl_xor_sync(0xffffffffu, a.s[i].x, off);
+                a.s[i].y += __shfl_xor_sync(0xffffffffu, a.s[i].y, off);
+            }
             a.x[i] += __shfl_xor_sync(0xffffffffu, a.x[i], off);
         }
 #pragma unroll
@@ -219,8 +225,8 @@ __device__ __forceinline__ void accp_store(const AccP& a, float* __restrict__ re
     for (int i = 0; i < 5; ++i) {
         v[1 + 2 * i] = a.r[i].x;
         v[2 + 2 * i] = a.r[i].y;
-        v[51 + 2 * i] = a.s[i].x;
-        v[52 + 2 * i] = a.s[i].y;
+        v[51 + 2 * i] = i < 4 ? a.s[i].x : 0.0f;
+        v[52 + 2 * i] = i < 4 ? a.s[i].y : a.s4;
         v[61 + i] = a.x[i];
     }
 #pragma unroll
@@ -559,6 +565,102 @@ __device__ __forceinline__ bool solve_refined(Acc& a, const float (&s2)[NZ], flo
     return true;
 }
 
+// Mixed-form solve of one Gram record: FP32 Cholesky of the ridged,
+// Jacobi-equilibrated system plus one step of iterative refinement, whose
+// residual is taken against the unfactored system re-read from the record,
+// 16 bytes at a time (so that the factor can overwrite the matrix in
+// registers).  Returns false,
+// leaving theta unset, when the condition number estimated from the factor's
+// diagonal, (max L_ii / min L_ii)^2, exceeds 1e6: such systems are
+// accumulated again with compensated sums and solved in FP64.
+__device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec, const float (&s2)[NZ], float ridge,
+                                                  float (&theta)[NZ])
+{
+    Acc a;
+    gram_load(rec, a);
+    const float rW = ridge * a.G[0];
+#pragma unroll
+    for (int j = 1; j < NZ; ++j) a.G[tri(j, j)] = fmaf(rW, s2[j], a.G[tri(j, j)]);
+    float dsc[NZ], b[NZ];
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) dsc[i] = rsqrtf(a.G[tri(i, i)]);
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) a.G[tri(i, j)] *= dsc[i] * dsc[j];
+        b[i] = a.B[i] * dsc[i];
+    }
+    float inv[NZ];
+    float lmin = 3.4e38f, lmax = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+        float sj = a.G[tri(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) sj = fmaf(-a.G[tri(j, k)], a.G[tri(j, k)], sj);
+        sj = fmaxf(sj, 1e-20f);
+        const float l = sqrtf(sj);
+        lmin = fminf(lmin, l);
+        lmax = fmaxf(lmax, l);
+        a.G[tri(j, j)] = l;
+        inv[j] = 1.0f / l;
+#pragma unroll
+        for (int i = j + 1; i < NZ; ++i) {
+            float v = a.G[tri(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v = fmaf(-a.G[tri(i, k)], a.G[tri(j, k)], v);
+            a.G[tri(i, j)] = v * inv[j];
+        }
+    }
+    const float ratio = lmax / lmin;
+    if (!(ratio * ratio <= 1e6f)) return false;
+    auto llt_solve = [&](const float (&rhs)[NZ], float (&x)[NZ]) {
+        float z[NZ];
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            float v = rhs[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) v = fmaf(-a.G[tri(i, k)], z[k], v);
+            z[i] = v * inv[i];
+        }
+#pragma unroll
+        for (int i = NZ - 1; i >= 0; --i) {
+            float v = z[i];
+#pragma unroll
+            for (int k = i + 1; k < NZ; ++k) v = fmaf(-a.G[tri(k, i)], x[k], v);
+            x[i] = v * inv[i];
+        }
+    };
+    float th[NZ];
+    llt_solve(b, th);
+    // r = b - A th with A the ridged, equilibrated matrix, entries re-read from the record
+    float r[NZ];
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) r[i] = b[i];
+    const float4* r4 = reinterpret_cast<const float4*>(rec);
+#pragma unroll
+    for (int q = 0; q < kGramStride / 4; ++q) {
+        const float4 v4 = __ldg(r4 + q);
+        const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int sl = 4 * q + k;
+            if (sl >= kGramFloats) continue;
+            const int i = slot_i(sl), j = slot_j(sl);
+            if (i == 10 || j == 10) continue;   // right-hand side (already in b)
+            float g = vv[k];
+            if (i == j && i > 0) g = fmaf(rW, s2[i], g);
+            const float aij = g * (dsc[i] * dsc[j]);
+            r[i] = fmaf(-aij, th[j], r[i]);
+            if (i != j) r[j] = fmaf(-aij, th[i], r[j]);
+        }
+    }
+    float dth[NZ];
+    llt_solve(r, dth);
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) theta[i] = (th[i] + dth[i]) * dsc[i];
+    return true;
+}
+
 // Out-of-line copy for callers whose accumulation loop already holds the
 // register budget (the solve then runs on the call's own frame).
 __device__ __noinline__ int solve_mixed_call(Acc& a, const float (&s2)[NZ], float ridge, float (&theta)[NZ])
@@ -644,7 +746,6 @@ __device__ __forceinline__ void finish(const WlrParams& p, unsigned long long pa
                                        bool scan = true)
 {
     __shared__ int s_timeout, s_last;
-    __shared__ int s_warp[8];
     if (threadIdx.x == 0) {
         s_timeout = 0;
         s_last = 0;
@@ -666,19 +767,24 @@ __device__ __forceinline__ void finish(const WlrParams& p, unsigned long long pa
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    unsigned long long running = *(volatile unsigned long long*)&p.ctrl->ev_total;
-    const unsigned long long start = running;
-    for (int base = 0; base < p.n_chunks; base += blockDim.x) {
-        const int j = base + (int)threadIdx.x;
-        const int v = (j < p.n_chunks) ? (int)*(volatile uint32_t*)&p.chunk_cnt[j] : 0;
-        int seg;
-        const int off = block_exclusive_scan(v, s_warp, seg);
-        if (j < p.n_chunks) p.chunk_off[j] = running + (unsigned long long)off;
-        running += (unsigned long long)seg;
+    // last CTA: exclusive scan of the per-chunk event counts, in chunk order;
+    // each thread takes a run of consecutive chunks (all its loads in flight at once)
+    __shared__ unsigned long long s_warp64[8];
+    const int per = (p.n_chunks + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = (int)threadIdx.x * per;
+    const int j1 = min(j0 + per, p.n_chunks);
+    unsigned long long mine = 0;
+    for (int j = j0; j < j1; ++j) mine += *(volatile uint32_t*)&p.chunk_cnt[j];
+    unsigned long long seg;
+    const unsigned long long start = *(volatile unsigned long long*)&p.ctrl->ev_total;
+    unsigned long long off = start + block_exclusive_scan64(mine, s_warp64, seg);
+    for (int j = j0; j < j1; ++j) {
+        p.chunk_off[j] = off;
+        off += *(volatile uint32_t*)&p.chunk_cnt[j];
     }
     if (threadIdx.x == 0) {
-        p.ctrl->ev_total = running;
-        p.ctrl->ev_cum += running - start;
+        p.ctrl->ev_total = start + seg;
+        p.ctrl->ev_cum += seg;
     }
 }
 
