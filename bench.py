@@ -36,6 +36,9 @@ WORKLOADS = {
                        desc="1920x1080 RGB, 240 frames, 1 spp Gamma noise, 15x15x5 window, C=0.1"),
     "rects720p": dict(scene="rects720p", r=7, T=5, C=0.15, rgb=True,
                       desc="1280x720 RGB, 120 frames, 4 spp Gamma noise, 15x15x5 window, C=0.15"),
+    "pan1080p": dict(scene="pan1080p", r=7, T=5, C=0.1, rgb=True,
+                     desc="1920x1080 RGB, 240 frames, 1 spp Gamma noise, 15x15x5 window, C=0.1, the rectangles "
+                          "over a textured background (6-px cells) panning 1.7 x 0.7 px/frame"),
 }
 
 # Algorithmic FP32 work of the regression (counted from the method, see DESIGN):
@@ -428,6 +431,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_e2e:
         line["e2e"] = _e2e(args, scene, wl, N, stream)
+    if rank == 0 and not args.no_paper_density:
+        line["paper_density"] = _paper_density(args, dev, stream, fp32_peak, sink)
     if rank == 0 and not args.no_diff:
         line["differentiation_form"] = _differentiation(dev)
     if rank == 0 and not args.no_second_order:
@@ -445,10 +450,67 @@ def run_ours(args):
         nb = min(len(frames), 48)
         frames_cpu = [_dequantised_cpu(f) for f in sframes[:nb]]
         line["cpu_baseline"] = _cpu_baseline(frames_cpu, dict(wl, rgb=None))
+        try:   # a side report: its failure is recorded in the line, not fatal to it
+            line["precision_error"] = _precision_error(dev, sframes, wl)
+        except Exception as exc:   # noqa: BLE001
+            line["precision_error"] = {"error": repr(exc)}
     if dist:
         dist.barrier()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _paper_density(args, dev, stream, fp32_peak, sink):
+    """The adaptive path at the flag density the paper reports (about 28% of
+    pixels regressed): the 1080p rectangles over a textured background seen by
+    a panning camera, so that 14-27% of the pixels are flagged per frame.
+    Precision and FP32 forms, adaptive and exhaustive, timed like the headline
+    (frames generated on the device before timing, each step a distinct
+    frame)."""
+    import torch
+    import paper_2303_02608_gb300 as lib
+    from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, ESIM_AD_EXHAUSTIVE, SimConfig, Simulator
+    from scenes import Scene, preset
+    wl = WORKLOADS["pan1080p"]
+    sc = preset("pan1080p")
+    N = sc.width * sc.height
+    K, Wm = args.steps, args.warmup
+    frames = _gen_frames(Scene(sc), min(sc.frames, Wm + K), dev)
+    sframes = _storage_frames(frames)
+    torch.cuda.synchronize()
+    cap = sink.numel() // 12
+    out = {"workload": f"pan1080p: {wl['desc']}", "frames_timed": f"{Wm}-{Wm + K - 1}"}
+    for name, mode, mixed, fr in (("precision_adaptive", ESIM_AD_ADAPTIVE, True, sframes),
+                                  ("precision_exhaustive", ESIM_AD_EXHAUSTIVE, True, sframes),
+                                  ("fp32_adaptive", ESIM_AD_ADAPTIVE, False, frames)):
+        extra = dict(radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
+                     precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE) if mixed else {}
+        sim = Simulator(SimConfig(width=sc.width, height=sc.height, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
+                                  mode=mode, rgb=wl["rgb"], event_capacity=cap, **extra), stream)
+        ms, _, ev = _timed_run(sim, fr, Wm, K, stream, sink=sink, profile=False)
+        sim.reset()
+        _, prof, _ = _timed_run(sim, fr, Wm, K, stream, sink=sink, profile=True)
+        sim.close()
+        phi = prof["regressions_timed"] / (N * K)
+        n_launch = prof["launches"]["wlr_emit"]
+        wlr_ms = prof["ms"]["wlr_emit"]
+        pairs = prof["neighbours_timed"]
+        flops = pairs * FLOP_PER_NEIGHBOUR + prof["regressions_timed"] * FLOP_PER_SOLVE
+        ach = flops / (wlr_ms * 1e-3) / 1e12
+        out[name] = {"value": round(N * K / (ms * 1e-3), 1), "unit": UNIT, "ms_per_step": round(ms / K, 4),
+                     "flagged_fraction": round(phi, 4), "events_per_step": round(ev / K, 1),
+                     "kernel_ms_per_step": {k: round(v / K, 4) for k, v in prof["ms"].items()},
+                     "regression_kernel": ("dense tile-staged (every pixel)" if mode == ESIM_AD_EXHAUSTIVE else
+                                           "tile-staged over the flagged-tile queue when more than 1/8 of the "
+                                           "pixels are flagged, else per-warp window boxes"),
+                     "regression_roofline": {"achieved": round(ach, 3), "frac": round(ach / fp32_peak, 4),
+                                             "frac_at_145": round(ach / fp32_peak * 145 / FLOP_PER_NEIGHBOUR, 4),
+                                             "launch_ms": round(wlr_ms / n_launch, 4)}}
+    out["speedup_adaptive_vs_exhaustive"] = round(out["precision_adaptive"]["value"] /
+                                                  out["precision_exhaustive"]["value"], 3)
+    del frames, sframes
+    torch.cuda.empty_cache()
+    return out
 
 
 def _batching(dev, warmup=4, steps=12):
@@ -833,6 +895,56 @@ def _second_order(dev, fp32_peak, reps=5, warmup=3, r=3, T=3):
     return out
 
 
+def _precision_error(dev, sframes, wl, rows=(536, 544), n_frames=6):
+    """Per-result error of the precision form against the FP64 oracle (part of
+    the CPU-baseline leg, the one place the bench runs the oracle): alpha of
+    every pixel of a band of rows over the first frames of the workload in
+    exhaustive mode (the oracle reads the same FP16/BF16 values widened), and
+    a forced-fallback case: the 64x64 disc with grey albedo equal to its x
+    gradient and ridge 1e-9, whose collinear systems pass condition 1e6 and
+    are re-accumulated with compensated sums and solved in FP64."""
+    import numpy as np
+    import torch
+    import paper_2303_02608_gb300 as lib
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    from oracle import EXHAUSTIVE, Oracle, OracleConfig
+    from scenes import Scene, preset
+
+    def stats(err):
+        err = np.concatenate(err)
+        return {"results": int(err.size), "max": float(err.max()), "p99": float(np.percentile(err, 99)),
+                "mean": float(err.mean())}
+
+    def run(frames_dev, frames_cpu, W, H, r, T, C, ridge, band):
+        sim = Simulator(SimConfig(width=W, height=H, radius=r, frames=T, contrast=C, mode=lib.ESIM_AD_EXHAUSTIVE,
+                                  ridge=ridge, radiance_fmt=lib.ESIM_AD_LOGLUMA_F16,
+                                  feature_fmt=lib.ESIM_AD_FEAT_BF16, precision=lib.ESIM_AD_MIXED,
+                                  feature_scale=FSCALE))
+        orc = Oracle(OracleConfig(W, H, radius=r, frames=T, channels=0, mode=EXHAUSTIVE, contrast=C, ridge=ridge))
+        err = []
+        for fd, fc in zip(frames_dev, frames_cpu):
+            sim.push(fd)
+            orc.push(fc, band)
+            a = sim.denoised()[0].cpu().numpy().astype(np.float64)[band[0]:band[1]]
+            err.append(np.abs(a - orc.outputs()["alpha"][band[0]:band[1]]).ravel())
+        fp64 = sim.stats()["fp64_solves"]
+        sim.close()
+        return err, fp64
+
+    W, H = 1920, 1080
+    err, fp64 = run(sframes[:n_frames], [_dequantised_cpu(f) for f in sframes[:n_frames]], W, H, wl["r"], wl["T"],
+                    wl["C"], 1e-4, rows)
+    out = {"workload_band": dict(stats(err), rows=list(rows), frames=n_frames, mode="exhaustive",
+                                 fp64_solves=int(fp64))}
+    sc = preset("disc64", rgb=True)
+    raw = Scene(sc).sequence(4)
+    sd = _storage_frames([{k: f[k].to(dev) for k in ("radiance", "normal", "albedo", "depth")} for f in raw])
+    err, fp64 = run(sd, [_dequantised_cpu(f) for f in sd], sc.width, sc.height, 3, 3, 0.2, 1e-9, (0, sc.height))
+    out["forced_fallback"] = dict(stats(err), case="64x64 disc, grey albedo = x gradient, ridge 1e-9, 7x7x3, 4 frames",
+                                  fp64_solves=int(fp64))
+    return out
+
+
 def _dequantised_cpu(sf):
     """Storage-format frame widened to float32 on the host (what the oracle reads)."""
     import torch
@@ -981,6 +1093,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-render", action="store_true")
+    ap.add_argument("--no-paper-density", action="store_true")
     ap.add_argument("--no-second-order", action="store_true")
     ap.add_argument("--form", choices=["second-order"], default=None,
                     help="run only that form's measurement and print its JSON object")

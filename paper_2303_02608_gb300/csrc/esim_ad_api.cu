@@ -66,6 +66,7 @@ struct esim_ad_ctx {
     int sparse_grid = 0;
     int solve_grid = 0;
     int sparse_stage = 1;        // sparse kernel stages window boxes (ESIM_AD_SPARSE_STAGE=0: L1 only)
+    int test_withhold = 0;       // ESIM_AD_TEST_WITHHOLD_COPY=1: timeout injection for tests
     bool mixed = false;
     uint32_t sparse_max = 0;     // adaptive frames with at most this many flagged pixels use the sparse kernel
     float4* ring = nullptr;
@@ -323,6 +324,14 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     if (const char* e = getenv("ESIM_AD_SPARSE_STAGE")) {
         if (*e == '0') c->sparse_stage = 0;
     }
+    // Timeout injection for tests: ESIM_AD_TEST_WITHHOLD_COPY=1 makes every
+    // warp of the sparse regression kernel skip issuing its first window-box
+    // copy (nothing is in flight for that barrier) and bounds each mbarrier
+    // wait to 64 polls, so the wait gives up, the kernel records the timeout
+    // and returns; the normal bound is unchanged otherwise.
+    if (const char* e = getenv("ESIM_AD_TEST_WITHHOLD_COPY")) {
+        if (*e == '1') c->test_withhold = 1;
+    }
     *out = c;
     return ESIM_AD_OK;
 }
@@ -496,8 +505,8 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     wp.sparse_stage = c->sparse_stage;
     wp.tile_base = c->tile_base;
     wp.gram = c->gram;
-    wp.poll_limit = kPollLimit;
-    wp.withhold_copy = 0;
+    wp.poll_limit = c->test_withhold ? 64u : kPollLimit;
+    wp.withhold_copy = c->test_withhold;
     wp.ctrl = c->ctrl;
     {
         ProfScope ps(c, 1);

@@ -775,7 +775,7 @@ __device__ __noinline__ void refine_fp64(const WlrParams& p, uint32_t pix, const
 // solved by FP64 Cholesky (refine_fp64).  The last CTA scans the per-chunk
 // event counts for the ordered writer.
 template <bool kMixed>
-__global__ void __launch_bounds__(kSolveThreads, 4) wlr_solve_kernel(const WlrParams p)
+__global__ void __launch_bounds__(kSolveThreads, 3) wlr_solve_kernel(const WlrParams p)
 {
     __shared__ uint32_t s_ill[kSolveThreads];
     __shared__ int s_nill;
@@ -861,7 +861,7 @@ cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStre
     return cudaGetLastError();
 }
 
-int wlr_solve_grid(int num_sms) { return 4 * num_sms; }   // one wave at 4 CTAs per SM
+int wlr_solve_grid(int num_sms) { return 3 * num_sms; }   // one wave at 3 CTAs per SM
 
 cudaError_t launch_wlr_solve(const WlrParams& p, bool mixed, int grid, cudaStream_t s)
 {

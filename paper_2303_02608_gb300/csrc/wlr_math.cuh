@@ -566,13 +566,15 @@ __device__ __forceinline__ bool solve_refined(Acc& a, const float (&s2)[NZ], flo
 }
 
 // Mixed-form solve of one Gram record: FP32 Cholesky of the ridged,
-// Jacobi-equilibrated system plus one step of iterative refinement, whose
+// Jacobi-equilibrated system A plus one step of iterative refinement, whose
 // residual is taken against the unfactored system re-read from the record,
 // 16 bytes at a time (so that the factor can overwrite the matrix in
-// registers).  Returns false,
-// leaving theta unset, when the condition number estimated from the factor's
-// diagonal, (max L_ii / min L_ii)^2, exceeds 1e6: such systems are
-// accumulated again with compensated sums and solved in FP64.
+// registers).  The 2-norm condition number of A is estimated as
+// lambda_max / lambda_min with lambda_max bounded by the largest absolute row
+// sum (Gershgorin) and 1 / lambda_min by two steps of inverse iteration
+// through the factor from a fixed start vector.  Returns false, leaving theta
+// unset, when the estimate exceeds 1e6: such systems are accumulated again
+// with compensated sums and solved in FP64.
 __device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec, const float (&s2)[NZ], float ridge,
                                                   float (&theta)[NZ])
 {
@@ -591,7 +593,6 @@ __device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec,
         b[i] = a.B[i] * dsc[i];
     }
     float inv[NZ];
-    float lmin = 3.4e38f, lmax = 0.0f;
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
         float sj = a.G[tri(j, j)];
@@ -599,8 +600,6 @@ __device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec,
         for (int k = 0; k < j; ++k) sj = fmaf(-a.G[tri(j, k)], a.G[tri(j, k)], sj);
         sj = fmaxf(sj, 1e-20f);
         const float l = sqrtf(sj);
-        lmin = fminf(lmin, l);
-        lmax = fmaxf(lmax, l);
         a.G[tri(j, j)] = l;
         inv[j] = 1.0f / l;
 #pragma unroll
@@ -611,8 +610,6 @@ __device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec,
             a.G[tri(i, j)] = v * inv[j];
         }
     }
-    const float ratio = lmax / lmin;
-    if (!(ratio * ratio <= 1e6f)) return false;
     auto llt_solve = [&](const float (&rhs)[NZ], float (&x)[NZ]) {
         float z[NZ];
 #pragma unroll
@@ -630,12 +627,35 @@ __device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec,
             x[i] = v * inv[i];
         }
     };
+    // 1 / lambda_min: two steps of inverse iteration from a fixed unit vector
+    float x1[NZ], x2[NZ];
+    {
+        float v0[NZ];
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) v0[i] = (i & 1) ? -0.31622777f : 0.31622777f;   // (+-1) / sqrt(10)
+        llt_solve(v0, x1);
+        float n1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) n1 = fmaf(x1[i], x1[i], n1);
+        const float s1 = rsqrtf(fmaxf(n1, 1e-30f));
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) x1[i] *= s1;
+        llt_solve(x1, x2);
+    }
+    float inv_lmin = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) inv_lmin = fmaf(x2[i], x2[i], inv_lmin);
+    inv_lmin = sqrtf(inv_lmin);
     float th[NZ];
     llt_solve(b, th);
-    // r = b - A th with A the ridged, equilibrated matrix, entries re-read from the record
-    float r[NZ];
+    // r = b - A th with A re-read from the record; the same pass takes A's
+    // absolute row sums (Gershgorin bound on lambda_max)
+    float r[NZ], rowsum[NZ];
 #pragma unroll
-    for (int i = 0; i < NZ; ++i) r[i] = b[i];
+    for (int i = 0; i < NZ; ++i) {
+        r[i] = b[i];
+        rowsum[i] = 0.0f;
+    }
     const float4* r4 = reinterpret_cast<const float4*>(rec);
 #pragma unroll
     for (int q = 0; q < kGramStride / 4; ++q) {
@@ -651,9 +671,17 @@ __device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec,
             if (i == j && i > 0) g = fmaf(rW, s2[i], g);
             const float aij = g * (dsc[i] * dsc[j]);
             r[i] = fmaf(-aij, th[j], r[i]);
-            if (i != j) r[j] = fmaf(-aij, th[i], r[j]);
+            rowsum[i] += fabsf(aij);
+            if (i != j) {
+                r[j] = fmaf(-aij, th[i], r[j]);
+                rowsum[j] += fabsf(aij);
+            }
         }
     }
+    float lmax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) lmax = fmaxf(lmax, rowsum[i]);
+    if (!(lmax * inv_lmin <= 1e6f)) return false;
     float dth[NZ];
     llt_solve(r, dth);
 #pragma unroll

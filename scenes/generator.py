@@ -34,6 +34,7 @@ _LIGHT = (0.3, 0.5, 1.0)
 
 _KEY_NOISE = 0x5EED0001
 _KEY_LAYOUT = 0x1A70D002
+_KEY_BG = 0xB6C0D003
 
 
 @dataclass
@@ -55,10 +56,15 @@ class SceneConfig:
     disc_start: tuple = (16.0, 32.0)
     disc_velocity: tuple = (2.0, 0.0)
     bg_depth: float = 5.0
+    # textured, panning background (0 = the plain horizontal gradient): square
+    # cells of bg_cell pixels with their own RGB albedo, depth and tilted
+    # normal, translating by bg_pan pixels per frame (a camera pan)
+    bg_cell: int = 0
+    bg_pan: tuple = (0.0, 0.0)
     extra: dict = field(default_factory=dict)
 
 
-# Presets shaped like the five workloads (see the design doc for the recipe).
+# Presets shaped like the workloads the simulator is measured on.
 def preset(name: str, **over) -> SceneConfig:
     table = {
         "disc64": dict(kind="disc", width=64, height=64, frames=8, spp=4, seed=0, rgb=False),
@@ -68,6 +74,11 @@ def preset(name: str, **over) -> SceneConfig:
                            rgb=True, bg_depth=10.0),
         "rects512": dict(kind="rects", width=512, height=512, frames=16, spp=2, seed=0,
                          rgb=True, bg_depth=10.0),
+        # the same rectangles over a textured background seen by a panning
+        # camera: about a tenth to a third of the pixels change features per
+        # frame, the density at which the paper regresses (about 28%)
+        "pan1080p": dict(kind="rects", width=1920, height=1080, frames=240, spp=1, seed=0,
+                         rgb=True, bg_depth=10.0, bg_cell=6, bg_pan=(1.7, 0.7)),
     }
     d = dict(table[name])
     d.update(over)
@@ -150,6 +161,8 @@ class Scene:
         albedo = grad.unsqueeze(0).repeat(3, 1, 1)
         depth = torch.full((H, W), cfg.bg_depth, dtype=f64, device=device)
         rad = grad.unsqueeze(0).repeat(3, 1, 1)
+        if cfg.bg_cell > 0:
+            albedo, depth, normal, rad = self._textured_background(t, xs, ys, device)
         if cfg.kind == "disc":
             cx = cfg.disc_start[0] + cfg.disc_velocity[0] * t
             cy = cfg.disc_start[1] + cfg.disc_velocity[1] * t
@@ -185,6 +198,35 @@ class Scene:
         else:
             raise ValueError(cfg.kind)
         return {"radiance": rad, "normal": normal, "albedo": albedo, "depth": depth}
+
+    def _textured_background(self, t, xs, ys, device):
+        """Background of square cells in world coordinates, seen at an offset of
+        bg_pan * t pixels: per cell an RGB albedo U[0.1, 0.9], a depth
+        bg_depth * U[0.8, 1.2] and a unit normal tilted by up to ~25 degrees;
+        Lambertian shading as for the rectangles."""
+        cfg = self.cfg
+        f64 = torch.float64
+        wx = xs + cfg.bg_pan[0] * t
+        wy = ys + cfg.bg_pan[1] * t
+        cx = torch.floor(wx / cfg.bg_cell).to(torch.int64)
+        cy = torch.floor(wy / cfg.bg_cell).to(torch.int64)
+        # counters: cell x, cell y (offset to stay non-negative), sequence
+        z = torch.zeros_like(cx)
+        w = philox4x32((cx + (1 << 20)) & 0xFFFFFFFF, (cy + (1 << 20)) & 0xFFFFFFFF,
+                       z + (cfg.seq & 0xFFFFFFFF), z, cfg.seed, _KEY_BG)
+        w2 = philox4x32((cx + (1 << 20)) & 0xFFFFFFFF, (cy + (1 << 20)) & 0xFFFFFFFF,
+                        z + (cfg.seq & 0xFFFFFFFF), z + 1, cfg.seed, _KEY_BG)
+        u = [uniform_open01(v) for v in w] + [uniform_open01(v) for v in w2]
+        albedo = torch.stack([0.1 + 0.8 * u[0], 0.1 + 0.8 * u[1], 0.1 + 0.8 * u[2]], 0)
+        depth = cfg.bg_depth * (0.8 + 0.4 * u[3])
+        tx, ty = 0.45 * (u[4] - 0.5) * 2, 0.45 * (u[5] - 0.5) * 2
+        n = torch.stack([tx, ty, torch.ones_like(tx)], 0)
+        n = n / torch.sqrt((n * n).sum(0, keepdim=True))
+        lx, ly, lz = _LIGHT
+        ln = math.sqrt(lx * lx + ly * ly + lz * lz)
+        ndl = torch.clamp((n[0] * lx + n[1] * ly + n[2] * lz) / ln, min=0.0)
+        rad = albedo * (0.3 + 0.7 * ndl).unsqueeze(0)
+        return albedo.to(f64), depth.to(f64), n.to(f64), rad.to(f64)
 
     def gamma_factor(self, t: int, device="cpu") -> torch.Tensor:
         """Multiplicative Gamma(k, 1/k) noise, shape [C][H][W], float64."""

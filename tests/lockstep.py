@@ -184,3 +184,40 @@ def run(frames, sim, orc, C, rows=None, strict=True, adaptive=True, report=None,
         compare_frame(t, fr, g_alpha, g_flag, g_ev, g_st, orc, C, band, adaptive, rep, alpha_tol, strict,
                       gpu_state_after=sim.get_state)
     return rep
+
+
+def run_bands(frames, sim, orcs, C, bands, strict=False, adaptive=True, alpha_tol=ALPHA_TOL):
+    """As run(), with one oracle per band of rows (bands: list of (r0, r1),
+    orcs: one oracle per band); the CUDA path runs once over whole frames and
+    every band is compared each frame.  Returns one report per band."""
+    import torch
+
+    H, W = orcs[0].cfg.height, orcs[0].cfg.width
+    masks = []
+    for r0, r1 in bands:
+        m = np.zeros((H, W), bool)
+        m[r0:r1] = True
+        masks.append(m)
+    reps = [new_report() for _ in bands]
+    for t, fr in enumerate(frames):
+        g_st = sim.get_state() if t > 0 else None
+        if t > 0 and strict:
+            for orc in orcs:
+                adopt_gpu_state(orc, g_st)
+        if "gpu" in fr:
+            gpu_in = {k: v.cuda() for k, v in fr["gpu"].items()}
+        else:
+            gpu_in = {k: fr[k].cuda() for k in ("radiance", "normal", "albedo", "depth", "variance") if k in fr}
+        sim.push(gpu_in)
+        for orc, rows in zip(orcs, bands):
+            orc.push(fr, rows)
+        g_alpha, g_flag = sim.denoised()
+        g_alpha = g_alpha.cpu().numpy().astype(np.float64)
+        g_flag = g_flag.cpu().numpy().astype(bool)
+        g_ev = sim.events()
+        torch.cuda.synchronize()
+        for orc, band, rep in zip(orcs, masks, reps):
+            compare_frame(t, fr, g_alpha, g_flag, g_ev, g_st, orc, C, band, adaptive, rep, alpha_tol, strict,
+                          gpu_state_after=sim.get_state)
+    return reps
+

@@ -202,6 +202,50 @@ def test_overflow_is_sticky_and_drain_reports_counts(lib):
 
 
 @pytest.mark.gpu
+def test_bounded_wait_timeout_is_reported_and_sticky(lib):
+    """ESIM_AD_TEST_WITHHOLD_COPY=1 makes every warp of the sparse regression
+    kernel skip issuing its first window-box copy and bounds each mbarrier
+    wait to 64 polls: the wait on that box gives up with no copy in flight for
+    it, the kernel records the timeout and returns.  The host reports
+    ETIMEOUT at the next synchronising call, every later call ESTATE, and after
+    a reset the context works again (the GPU context was never lost)."""
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    import torch
+    W, H = 64, 48
+    keys = {"ESIM_AD_TEST_WITHHOLD_COPY": "1", "ESIM_AD_SPARSE_MAX": "4294967295"}
+    old = {k: os.environ.get(k) for k in keys}
+    os.environ.update(keys)
+    try:
+        sim = Simulator(SimConfig(width=W, height=H, radius=3, frames=2, contrast=0.05,
+                                  mode=lib.ESIM_AD_ADAPTIVE))
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    f0 = _frame(W, H)
+    f1 = {k: v.flip(-1).contiguous() for k, v in f0.items()}   # features move: pixels flag
+    sim.push(f0)                    # frame 0 regresses densely (tile-staged kernel)
+    sim.push(f1)                    # adaptive frame: the sparse kernel's first copies are withheld
+    with pytest.raises(lib.EsimError) as e:
+        sim.denoised()
+    assert e.value.status == lib.ESIM_AD_ETIMEOUT
+    with pytest.raises(lib.EsimError) as e:
+        sim.push(f0)
+    assert e.value.status == lib.ESIM_AD_ESTATE
+    with pytest.raises(lib.EsimError) as e:
+        sim.events()
+    assert e.value.status == lib.ESIM_AD_ESTATE
+    sim.reset()
+    sim.push(f0)
+    alpha, _ = sim.denoised()
+    assert torch.isfinite(alpha).all()
+    sim.close()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.gpu
 def test_drain_enospace_then_full_drain(lib):
     from paper_2303_02608_gb300 import EVENT_DTYPE, SimConfig, Simulator
     W, H = 40, 24

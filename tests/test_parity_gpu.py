@@ -123,6 +123,40 @@ def test_1080p_band():
     assert rep["regressed"] > 0
 
 
+def test_1080p_three_bands_20_frames_free_running():
+    """The benchmark's 1080p workload (FP32 form) over 20 frames, free-running:
+    the oracle keeps its own models except at threshold-ambiguous pixels;
+    bands at the top, middle and bottom of the image."""
+    from lockstep import run_bands
+    sc = preset("rects1080p")
+    frames = Scene(sc).sequence(20)
+    bands = [(0, 8), (536, 544), (1072, 1080)]
+    sim = _sim(sc.width, sc.height, 7, 5, 0.1, ADAPTIVE, True)
+    orcs = [_orc(sc.width, sc.height, 7, 5, 0.1, ADAPTIVE, True) for _ in bands]
+    reps = run_bands(frames, sim, orcs, 0.1, bands, strict=False)
+    sim.close()
+    assert all(r["frames"] == 20 and r["regressed"] > 0 for r in reps)
+    assert sum(r["events"] for r in reps) > 0
+
+
+@pytest.mark.parametrize("path", ["auto", "staged"])
+def test_pan1080p_band_paper_density(path):
+    """The paper-density workload: rectangles over a textured background seen
+    by a panning camera (14-27% of the pixels flagged per frame, where the
+    tile-staged kernel serves the flagged-tile queue); two bands."""
+    from lockstep import run_bands
+    sc = preset("pan1080p")
+    frames = Scene(sc).sequence(8)
+    bands = [(400, 408), (800, 808)]
+    sim = _sim(sc.width, sc.height, 7, 5, 0.1, ADAPTIVE, True, path=path)
+    orcs = [_orc(sc.width, sc.height, 7, 5, 0.1, ADAPTIVE, True) for _ in bands]
+    reps = run_bands(frames, sim, orcs, 0.1, bands, strict=True)
+    phi = sim.stats()["regressions"] / (8 * sc.width * sc.height)
+    sim.close()
+    assert all(r["frames"] == 8 for r in reps)
+    assert phi > 0.1, phi
+
+
 @pytest.mark.parametrize("mode,path", [(ADAPTIVE, "staged"), (ADAPTIVE, "sparse")])
 def test_variance_guard(mode, path):
     """Optional guard (kappa = 3, the frame's variance plane): flags also where
