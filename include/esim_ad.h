@@ -237,14 +237,17 @@ esim_ad_status esim_ad_profile_get(esim_ad_ctx* ctx, esim_ad_profile* out);
  * context of esim_ad_init would, up to floating-point summation order).
  *
  * Per step: one ingest/test launch over the tiles of all sequences, one
- * persistent regression launch over a single compacted queue of flagged
- * (sequence, pixel) entries of all sequences, one event-writer launch; the
- * whole step is a CUDA graph instantiated at init and replayed per step (the
- * per-step frame pointers travel in a small table copied by the graph).  The
- * regression's lanes per pixel are chosen by an autotuner that times the
- * candidates on the first adaptive steps and caches the choice per (radius,
- * frames, precision, SM count) in $ESIM_AD_CACHE (default
- * ~/.cache/esim_ad_autotune.txt); ESIM_AD_BATCH_LANES=8|16|32 forces one.
+ * persistent accumulation launch over a single compacted queue of flagged
+ * (sequence, pixel) entries of all sequences, one solve launch, one
+ * event-writer launch; the whole step is a CUDA graph instantiated at init
+ * and replayed per step (the per-step frame pointers travel in a small table
+ * copied by the graph).  The tile shape that groups flagged pixels into the
+ * queue (16x16, 32x8 or 64x4 pixels) and the regression's lanes per pixel
+ * (8, 16, 32) are chosen jointly by an autotuner that times the nine pairs on
+ * the first adaptive steps and caches the choice per (radius, frames,
+ * precision, SM count) in $ESIM_AD_CACHE (default
+ * ~/.cache/esim_ad_autotune.txt); ESIM_AD_BATCH_TILE=16|32|64 together with
+ * ESIM_AD_BATCH_LANES=8|16|32 forces a pair.
  */
 typedef struct esim_ad_batch esim_ad_batch;
 
@@ -293,6 +296,11 @@ esim_ad_status esim_ad_batch_get_state(esim_ad_batch* b, int32_t seq, float* l_l
  * the profile of the steps run while enabled (class 1 = the one persistent
  * regression launch per step).  lanes_out receives the autotuned lanes per pixel. */
 esim_ad_status esim_ad_batch_stats(esim_ad_batch* b, esim_ad_stats* out, int32_t* lanes_out);
+/* The tile shape (width x height in pixels) and lanes per pixel in use: the
+ * autotuned pair once tuning has finished, else the default 32x8 / 8 (or the
+ * pair being timed on the current tuning step's successor).  Null outputs are
+ * skipped.  EINVAL for a NULL batch. */
+esim_ad_status esim_ad_batch_tiling(esim_ad_batch* b, int32_t* tile_w, int32_t* tile_h, int32_t* lanes);
 esim_ad_status esim_ad_batch_profile_enable(esim_ad_batch* b, int on);
 esim_ad_status esim_ad_batch_profile_get(esim_ad_batch* b, esim_ad_profile* out);
 
@@ -383,25 +391,27 @@ esim_ad_status esim_ad_wlr2_forward(const esim_ad_wlr_desc* d, const float* radi
 
 /*
  * Write the events of one frame from a map of signed per-pixel event counts
- * (p*n, as Eq. 1 emission produces), in canonical order (row, column, repeat),
- * without allocating anything.  The paper has no counterpart: this is a
- * deployment entry point.
+ * (polarity times number of events at each pixel), in canonical order (row,
+ * column, repeat), without allocating anything.  The paper has no
+ * counterpart: this is a deployment entry point.
  *
  * Who it is for: callers that cannot call cudaMalloc where they need events
- * written - code inside their own CUDA stream capture under an allocation-free
- * policy, latency-critical loops where cudaMalloc's implicit device-wide
+ * written - latency-critical loops where cudaMalloc's implicit device-wide
  * synchronisation would stall other work, and plugins of a host framework that
  * owns all device memory.  It runs the same kernels as the context's event
- * writer, with their scratch (about 96 KB) in a fixed array inside the library
+ * writer, with their scratch (about 32 KB) in a fixed array inside the library
  * that every GPU loading the library keeps until the process exits.
  *
- * counts       [height][width] int32, device memory (input, caller-owned).
+ * counts       [height][width] int32, device memory (input, caller-owned);
+ *              each |count| at most 524,288 (2^19).
  * frame        frame index written into each record.
  * events       device memory for `capacity` records (output, caller-owned);
  *              may be NULL when capacity == 0.
  * total_device one uint64 in device memory (output): the number of events the
  *              counts call for; records past `capacity` are dropped, so
- *              *total_device > capacity means the buffer was too small.
+ *              *total_device > capacity means the buffer was too small.  If a
+ *              count lies outside +-2^19, nothing is written and
+ *              *total_device is UINT64_MAX.
  * cuda_stream  cudaStream_t the work is enqueued on; nothing is synchronised.
  * Limit: width * height <= 16,777,216 pixels (and each side <= 65535);
  * larger frames return EINVAL.  EINVAL also for NULL counts/total_device or

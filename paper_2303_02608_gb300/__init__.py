@@ -42,7 +42,7 @@ EXPORTS = (
     "esim_ad_init", "esim_ad_push_frame", "esim_ad_events", "esim_ad_denoised",
     "esim_ad_get_state", "esim_ad_set_state", "esim_ad_reset", "esim_ad_stats_get",
     "esim_ad_destroy", "esim_ad_status_string", "esim_ad_profile_enable", "esim_ad_profile_get",
-    "esim_ad_write_events_noalloc", "esim_ad_wlr_workspace_size", "esim_ad_wlr_forward",
+    "esim_ad_write_events_noalloc", "esim_ad_batch_tiling", "esim_ad_wlr_workspace_size", "esim_ad_wlr_forward",
     "esim_ad_wlr_backward", "esim_ad_batch_init", "esim_ad_batch_step", "esim_ad_batch_events",
     "esim_ad_batch_reset_sequence", "esim_ad_batch_denoised", "esim_ad_batch_get_state",
     "esim_ad_batch_stats", "esim_ad_batch_profile_enable", "esim_ad_batch_profile_get",
@@ -139,6 +139,9 @@ def load_library():
     lib.esim_ad_profile_enable.argtypes = [P, ctypes.c_int]
     lib.esim_ad_profile_get.restype = st
     lib.esim_ad_profile_get.argtypes = [P, ctypes.POINTER(esim_ad_profile)]
+    lib.esim_ad_batch_tiling.restype = st
+    lib.esim_ad_batch_tiling.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32)]
     lib.esim_ad_write_events_noalloc.restype = st
     lib.esim_ad_write_events_noalloc.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, P,
                                                  ctypes.c_uint64, P, P]
@@ -767,8 +770,11 @@ class Batch:
         lanes = ctypes.c_int32(0)
         _check(load_library().esim_ad_batch_stats(ctypes.c_void_p(self.b), ctypes.byref(s), ctypes.byref(lanes)),
                "esim_ad_batch_stats")
+        tw, th, ln = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load_library().esim_ad_batch_tiling(ctypes.c_void_p(self.b), ctypes.byref(tw), ctypes.byref(th),
+                                                   ctypes.byref(ln)), "esim_ad_batch_tiling")
         return {"steps": s.frames, "regressions": s.regressions, "events": s.events, "pixels": s.pixels,
-                "fp64_solves": s.fp64_solves, "lanes": lanes.value}
+                "fp64_solves": s.fp64_solves, "lanes": lanes.value, "tile": (tw.value, th.value)}
 
     def profile(self, on: bool | None = None):
         lib = load_library()

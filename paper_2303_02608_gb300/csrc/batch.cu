@@ -2,21 +2,28 @@
 // frame each per step, as one CUDA graph per step:
 //   1. copy of the step table (per-sequence frame pointers and frame index),
 //   2. clear of the per-step counters and the per-chunk event counts,
-//   3. one ingest/test launch over the tiles of every sequence; flagged pixels
-//      of all sequences are compacted into one queue of (sequence, pixel)
-//      entries (sequence in the top 8 bits),
-//   4. one persistent regression launch over that queue (per-warp window boxes
-//      staged in shared memory, as in the single-sequence sparse kernel; the
-//      work-item size, hence lanes per pixel, chosen by the autotuner),
-//   5. one event-writer launch over the chunks of every sequence.
-// Each sequence keeps its own ring, model state and maps, exactly as a
-// single-sequence context does; the per-pixel arithmetic is shared with it.
+//   3. one ingest/test launch over the tiles of every sequence (tile shape
+//      16x16, 32x8 or 64x4 pixels); flagged pixels of all sequences are
+//      compacted into one queue of (sequence, pixel) entries (sequence in the
+//      top 8 bits), each tile's run padded to four entries,
+//   4. one persistent accumulation launch over that queue (the single-sequence
+//      window-box form: per-warp boxes of an item's windows landed by bulk
+//      asynchronous copies, packed FP32 sums, one Gram record per entry; the
+//      item size, hence lanes per pixel, is a template choice),
+//   5. one solve launch over the records (solve, Eq. 1 emission into each
+//      sequence's maps, scan of the per-chunk event counts),
+//   6. one event-writer launch over the chunks of every sequence.
+// The tile shape and the lanes per pixel are picked jointly by an autotuner
+// that times the nine pairs on the first adaptive steps.  Each sequence keeps
+// its own ring, model state and maps, exactly as a single-sequence context
+// does; the per-pixel arithmetic is shared with it.
 #include <errno.h>
 #include <stdio.h>
 #include <sys/stat.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,6 +33,7 @@
 #include "sparse_stage.cuh"
 #include "internal.h"
 #include "wlr_math.cuh"
+#include "regress.cuh"
 
 namespace esim {
 namespace {
@@ -54,8 +62,25 @@ struct BatchGlobal {
     esim_ad_batch_event* events;
     unsigned long long capacity;
     int total_tiles, total_chunks, r;
+    int tx;                      // tile width in pixels (tile height 256 / tx)
     float s_px;
     Ctrl* ctrl;
+};
+
+// Tile shapes the autotuner chooses from: width in pixels (height 256 / width).
+constexpr int kTileShapes = 3;
+constexpr int kTileWidths[kTileShapes] = {16, 32, 64};
+
+// Sequences of a batch: list entries are (sequence << 24) | pixel.
+struct BatchSeq {
+    const SeqStep* steps;
+    __device__ __forceinline__ SeqView view(uint32_t e) const
+    {
+        const WlrParams& sp = steps[e >> kPixBits].wp;
+        return {sp.W, sp.H, sp.t, sp.T, sp.n_tau, sp.ring};
+    }
+    __device__ __forceinline__ uint32_t pixel(uint32_t e) const { return e & kPixMask; }
+    __device__ __forceinline__ const WlrParams& params(uint32_t e) const { return steps[e >> kPixBits].wp; }
 };
 
 __global__ void __launch_bounds__(kTilePix) batch_ingest_kernel(BatchGlobal g)
@@ -66,21 +91,23 @@ __global__ void __launch_bounds__(kTilePix) batch_ingest_kernel(BatchGlobal g)
     if (!st.active) return;
     const IngestParams& p = st.ip;
     const int tile = gt - st.tile_base;
-    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-    const int x = (tile % p.tiles_x) * kTileX + lx;
-    const int y = (tile / p.tiles_x) * kTileY + ly;
+    const int ty = kTilePix / g.tx;
+    const int x = (tile % p.tiles_x) * g.tx + (int)threadIdx.x % g.tx;
+    const int y = (tile / p.tiles_x) * ty + (int)threadIdx.x / g.tx;
     const int flag = ingest_pixel(p, x, y);
-    // compact this tile's regressed pixels into the global queue
+    // compact this tile's regressed pixels into the global queue, in raster
+    // order within the tile (= thread order)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ int warp_cnt[kTilePix / 32];
     __shared__ uint32_t s_base;
     const unsigned ballot = __ballot_sync(0xffffffffu, flag);
-    if (lx == 0) warp_cnt[ly] = __popc(ballot);
+    if (lane == 0) warp_cnt[wid] = __popc(ballot);
     __syncthreads();
     int base = 0, total = 0;
 #pragma unroll
     for (int w = 0; w < kTilePix / 32; ++w) {
         const int c = warp_cnt[w];
-        base += (w < ly) ? c : 0;
+        base += (w < wid) ? c : 0;
         total += c;
     }
     if (threadIdx.x == 0 && total > 0) {
@@ -91,216 +118,28 @@ __global__ void __launch_bounds__(kTilePix) batch_ingest_kernel(BatchGlobal g)
     __syncthreads();
     if (total > 0 && (int)threadIdx.x < ((-total) & 3)) g.flag_list[s_base + total + threadIdx.x] = kListPad;
     if (flag) {
-        const int pos = base + __popc(ballot & ((1u << lx) - 1u));
+        const int pos = base + __popc(ballot & ((1u << lane) - 1u));
         g.flag_list[s_base + pos] = ((uint32_t)seq << kPixBits) | (uint32_t)((size_t)y * p.W + x);
     }
 }
 
-// One persistent launch over the queue of every sequence.  A warp takes an
-// item of kItem consecutive queue entries (4, 2 or 1; each tile's run is
-// padded to a multiple of 4, so an item stays inside one tile of one
-// sequence), 32 / kItem lanes per pixel (wider when the item holds fewer real
-// entries).  For each frame of the window the warp copies the bounding box of
-// its pixels' windows from that sequence's ring into its shared-memory buffer
-// (16-byte asynchronous copies; boxes that do not fit are read through L1),
-// and the lanes split each window and are shuffle-reduced.  The last stretch
-// of the queue goes out one entry at a time so that warps finish together.
+// Pass 1: one persistent launch over the queue of every sequence, in the
+// single-sequence window-box form (items of kItem entries; an item stays
+// inside one tile of one sequence).
 template <int kItem, bool kMixed>
 __global__ void __launch_bounds__(kTilePix, 2) batch_wlr_kernel(BatchGlobal g, const WlrParams gp)
 {
-    using S = SparseStage<kMixed>;
-    extern __shared__ __align__(16) unsigned char sm[];
-    const SparseLayout L = sparse_layout(g.r, kMixed);
-    float4* table = reinterpret_cast<float4*>(sm);
-    const bool can_stage = L.buf_bytes > 0;
-    __shared__ unsigned long long s_pairs, s_pix, s_fp64;
-    const int r = g.r, side = 2 * r + 1, nq = side * side;
-    const float spx = g.s_px;
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-        const int ox = q % side - r, oy = q / side - r;
-        const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-        table[q] = make_float4(__int_as_float(oy * S::pitch + ox), u1, u2, -fmaf(u1, u1, u2 * u2));
-    }
-    if (threadIdx.x == 0) {
-        s_pairs = 0ull;
-        s_pix = 0ull;
-        s_fp64 = 0ull;
-    }
-    __syncthreads();
-    const uint32_t n_list = *(volatile uint32_t*)&g.ctrl->list_len;
-    const uint32_t tail_len = 2u * gridDim.x * (kTilePix / 32);
-    const uint32_t tail0 = n_list > tail_len ? (n_list - tail_len) & ~3u : 0u;   // multiple of 4
-    const int lane = threadIdx.x & 31;
-    unsigned char* wbuf = sm + L.buf_off + (threadIdx.x >> 5) * L.buf_bytes;
-    uint4* bufm = reinterpret_cast<uint4*>(wbuf);
-    float4* buf0 = reinterpret_cast<float4*>(wbuf);
-    float4* buf1 = buf0 + S::pitch * S::rows;
-    Acc acc;
-    float cf[7];
-    for (;;) {
-        uint32_t base = 0, single = 0;
-        if (lane == 0) {
-            base = atomicAdd(&g.ctrl->work_next, (uint32_t)kItem);
-            if (base >= tail0) {
-                base = tail0 + atomicAdd(&g.ctrl->tail_next, 1u);
-                single = 1;
-            }
-        }
-        base = __shfl_sync(0xffffffffu, base, 0);
-        single = __shfl_sync(0xffffffffu, single, 0);
-        if (base >= n_list) break;
-        const int lim = single ? 1 : kItem;
-        const uint32_t e4 = ((lane & 3) < lim) ? g.flag_list[base + (lane & 3)] : kListPad;
-        // an item's m real entries come first (padding closes a tile's run)
-        const int m = __popc(__ballot_sync(0xffffffffu, e4 != kListPad) & 0xfu);
-        if (m == 0) continue;   // a padding entry of the tail
-        const int lg = m >= 3 ? 3 : 6 - m;
-        const int gl = 1 << lg;
-        const int grp = lane >> lg, sub = lane & (gl - 1);
-        const uint32_t entry = __shfl_sync(0xffffffffu, e4, grp);
-        const bool active = grp < m;
-        // every entry of an item belongs to one sequence (entry 0 is real)
-        const int seq = (int)(__shfl_sync(0xffffffffu, e4, 0) >> kPixBits);
-        const WlrParams& sp = g.steps[seq].wp;
-        const int W = sp.W, H = sp.H;
-        const size_t N = (size_t)W * H;
-        const uint32_t pix = active ? (entry & kPixMask) : 0u;
-        const int cx = (int)(pix % (uint32_t)W), cy = (int)(pix / (uint32_t)W);
-        const float* sf = kMixed ? sp.q_scale : sp.s_feat;
-        const float4* ringf = reinterpret_cast<const float4*>(sp.ring);
-        const uint4* ringm = reinterpret_cast<const uint4*>(sp.ring);
-        const int slot_t = sp.t % sp.T;
-#pragma unroll
-        for (int i = 0; i < NG; ++i) acc.G[i] = 0.0f;
-#pragma unroll
-        for (int i = 0; i < NZ; ++i) acc.B[i] = 0.0f;
-        const int dxlo = max(-r, -cx), dxhi = min(r, W - 1 - cx);
-        const int dylo = max(-r, -cy), dyhi = min(r, H - 1 - cy);
-        const int nx = dxhi - dxlo + 1, ny = dyhi - dylo + 1;
-        // bounding box of the warp's windows (clipped to the image)
-        const int bx0 = __reduce_min_sync(0xffffffffu, active ? cx + dxlo : 0x7fffffff);
-        const int by0 = __reduce_min_sync(0xffffffffu, active ? cy + dylo : 0x7fffffff);
-        const int bx1 = __reduce_max_sync(0xffffffffu, active ? cx + dxhi : -1);
-        const int by1 = __reduce_max_sync(0xffffffffu, active ? cy + dyhi : -1);
-        const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
-        const bool staged = can_stage && bw > 0 && bw <= S::pitch && bh <= S::rows;   // warp-uniform
-        if (active) {
-            float c[7];
-            if (kMixed) {
-                float yc;
-                unpack_mixed(__ldg(ringm + (size_t)slot_t * N + pix), yc, c);
-            } else {
-                const float4 c0 = __ldg(ringf + (size_t)(2 * slot_t) * N + pix);
-                const float4 c1 = __ldg(ringf + (size_t)(2 * slot_t + 1) * N + pix);
-                c[0] = c0.y; c[1] = c0.z; c[2] = c0.w; c[3] = c1.x; c[4] = c1.y; c[5] = c1.z; c[6] = c1.w;
-            }
-#pragma unroll
-            for (int j = 0; j < 7; ++j) cf[j] = c[j] * sf[j];
-        }
-        const bool interior = nx == side && ny == side;
-        for (int k = 0; k < sp.n_tau; ++k) {
-            const int slot = (sp.t - k) % sp.T;
-            if (staged) {
-                __syncwarp();   // every lane is done with the previous frame's box
-                const size_t row0 = (size_t)by0 * W + bx0 + lane;
-                if (lane < bw) {
-                    for (int i = 0; i < bh; ++i) {
-                        const size_t gi = row0 + (size_t)i * W;
-                        if (kMixed) {
-                            cp_async16(bufm + i * S::pitch + lane, ringm + (size_t)slot * N + gi);
-                        } else {
-                            cp_async16(buf0 + i * S::pitch + lane, ringf + (size_t)(2 * slot) * N + gi);
-                            cp_async16(buf1 + i * S::pitch + lane, ringf + (size_t)(2 * slot + 1) * N + gi);
-                        }
-                    }
-                }
-                if (k + 1 < sp.n_tau) {
-                    // hint the next frame's box into L2 while this one lands and is summed
-                    const int nslot = (sp.t - k - 1) % sp.T;
-                    const int lines = (bw * S::rec + 127) >> 7;
-                    for (int j = lane; j < bh * lines; j += 32) {
-                        const int i = j / lines, l = j - i * lines;
-                        const size_t gi = (size_t)(by0 + i) * W + bx0;
-                        const char* row = kMixed
-                            ? reinterpret_cast<const char*>(ringm + (size_t)nslot * N + gi)
-                            : reinterpret_cast<const char*>(ringf + (size_t)(2 * nslot) * N + gi);
-                        prefetch_l2(row + l * 128);
-                        if (!kMixed) prefetch_l2(row + (size_t)N * 16 + l * 128);
-                    }
-                }
-                cp_async_wait_all();
-                __syncwarp();   // the box is visible to every lane of the warp
-                if (active) {
-                    const int cb = (cy - by0) * S::pitch + (cx - bx0);
-                    auto at = [&](int si, float u1, float u2, float en0) {
-                        if (kMixed)
-                            accumulate(acc, bufm[si], u1, u2, en0, sf, cf);
-                        else
-                            accumulate(acc, buf0[si], buf1[si], u1, u2, en0, sf, cf);
-                    };
-                    if (interior) {
-#pragma unroll 1
-                        for (int q = sub; q < nq; q += gl) {
-                            const float4 e = table[q];
-                            at(cb + __float_as_int(e.x), e.y, e.z, e.w);
-                        }
-                    } else {
-                        const int nvalid = nx * ny;
-                        int ox = dxlo + sub % nx;
-                        int oy = dylo + sub / nx;
-#pragma unroll 1
-                        for (int q = sub; q < nvalid; q += gl) {
-                            const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-                            at(cb + oy * S::pitch + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
-                            ox += gl;
-                            while (ox > dxhi) {
-                                ox -= nx;
-                                ++oy;
-                            }
-                        }
-                    }
-                }
-            } else if (active) {
-                // box too large for the buffer: read the windows through L1
-                const float4* __restrict__ R0 = ringf + (size_t)(2 * slot) * N + pix;
-                const float4* __restrict__ R1 = ringf + (size_t)(2 * slot + 1) * N + pix;
-                const uint4* __restrict__ RM = ringm + (size_t)slot * N + pix;
-                auto at = [&](int d, float u1, float u2, float en0) {
-                    if (kMixed)
-                        accumulate(acc, __ldg(RM + d), u1, u2, en0, sf, cf);
-                    else
-                        accumulate(acc, __ldg(R0 + d), __ldg(R1 + d), u1, u2, en0, sf, cf);
-                };
-                const int nvalid = nx * ny;
-                int ox = dxlo + sub % nx;
-                int oy = dylo + sub / nx;
-#pragma unroll 1
-                for (int q = sub; q < nvalid; q += gl) {
-                    const float u1 = (float)ox * spx, u2 = (float)oy * spx;
-                    at(oy * W + ox, u1, u2, -fmaf(u1, u1, u2 * u2));
-                    ox += gl;
-                    while (ox > dxhi) {
-                        ox -= nx;
-                        ++oy;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int off = gl >> 1; off >= 1; off >>= 1) {
-#pragma unroll
-            for (int i = 0; i < NG; ++i) acc.G[i] += __shfl_xor_sync(0xffffffffu, acc.G[i], off);
-#pragma unroll
-            for (int i = 0; i < NZ; ++i) acc.B[i] += __shfl_xor_sync(0xffffffffu, acc.B[i], off);
-        }
-        if (active && sub == 0) {
-            atomicAdd(&s_pairs, (unsigned long long)(nx * ny * sp.n_tau));
-            atomicAdd(&s_pix, 1ull);
-            solve_and_emit<kMixed, true>(sp, acc, cx, cy, &s_fp64);
-        }
-    }
-    __syncthreads();
-    finish(gp, s_pairs, s_pix, s_fp64, false);
+    sparse_body<kItem, kMixed>(gp, BatchSeq{g.steps});
+}
+
+// Pass 2: solve every record and emit into its sequence's maps; the last CTA
+// scans the per-chunk event counts of all sequences for the writer.
+template <bool kMixed>
+__global__ void __launch_bounds__(kSolveThreads, 3) batch_solve_kernel(BatchGlobal g, const WlrParams gp)
+{
+    const uint32_t n = *(volatile uint32_t*)&g.ctrl->list_len;
+    const unsigned long long fp64 = solve_records<kMixed>(gp, BatchSeq{g.steps}, n);
+    finish(gp, 0ull, 0ull, fp64, false, true);
 }
 
 __global__ void __launch_bounds__(kTilePix) batch_event_write_kernel(BatchGlobal g)
@@ -377,7 +216,13 @@ struct esim_ad_batch {
     bool mixed = false;
     // per sequence
     std::vector<size_t> N;
-    std::vector<int> tiles_x, n_tiles, n_chunks, tile_base, chunk_base;
+    std::vector<int> n_chunks, chunk_base;
+    // per tile shape: tiles across, tile count and first global tile of each
+    // sequence; global tile -> sequence table
+    std::vector<int> tiles_x[kTileShapes], n_tiles[kTileShapes], tile_base[kTileShapes];
+    int total_tiles_s[kTileShapes] = {0, 0, 0};
+    uint16_t* tile_seq_s[kTileShapes] = {nullptr, nullptr, nullptr};
+    float* gram = nullptr;   // Gram records, one per queue entry
     std::vector<void*> ring;
     std::vector<float4*> state;
     std::vector<float*> alpha;
@@ -385,9 +230,8 @@ struct esim_ad_batch {
     std::vector<int32_t*> nev;
     std::vector<uint64_t> t;        // frames pushed per sequence
     // global
-    int total_tiles = 0, total_chunks = 0;
+    int total_chunks = 0;
     size_t total_pix = 0;
-    uint16_t* tile_seq = nullptr;
     uint16_t* chunk_seq = nullptr;
     uint32_t* flag_list = nullptr;
     uint32_t* chunk_cnt = nullptr;
@@ -399,15 +243,16 @@ struct esim_ad_batch {
     cudaEvent_t h_free[2] = {nullptr, nullptr};
     int cur = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int graph_lanes = 0;
     int grid = 0;
-    int smem = 0;        // dynamic shared memory of the regression launch
-    int lanes = 16;
+    int solve_grid = 0;
+    int smem = 0;        // dynamic shared memory of the accumulation launch
+    int lanes = 8;       // lanes per pixel (items of 32 / lanes entries)
+    int shape = 1;       // tile shape index into kTileWidths
     bool tuned = false;
     int tune_stage = 0;                         // candidates measured so far
-    float tune_ms[3] = {0, 0, 0};
-    unsigned long long tune_reg[3] = {0, 0, 0};
-    cudaEvent_t tune_ev[6] = {};
+    float tune_ms[9] = {};
+    unsigned long long tune_reg[9] = {};
+    cudaEvent_t tune_ev[18] = {};
     unsigned long long reg_before = 0;
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -420,7 +265,9 @@ struct esim_ad_batch {
 
 namespace {
 
-const int kCandidates[3] = {8, 16, 32};
+// Tuning candidates: (tile shape index, lanes per pixel), all nine pairs.
+constexpr int kNumCandidates = 9;
+const int kCandLanes[3] = {8, 16, 32};
 
 std::string cache_key(const esim_ad_batch* b)
 {
@@ -430,13 +277,21 @@ std::string cache_key(const esim_ad_batch* b)
     return k;
 }
 
-int cache_lookup(const esim_ad_batch* b)
+// Cached choice encoded as 100 * tile shape index + lanes per pixel.
+bool cache_lookup(const esim_ad_batch* b, int* shape, int* lanes)
 {
     const int v = tune_cache_lookup(cache_key(b).c_str());
-    return (v == 8 || v == 16 || v == 32) ? v : 0;
+    const int sh = v / 100, l = v % 100;
+    if (sh < 0 || sh >= kTileShapes || (l != 8 && l != 16 && l != 32)) return false;
+    *shape = sh;
+    *lanes = l;
+    return true;
 }
 
-void cache_store(const esim_ad_batch* b, int lanes) { tune_cache_store(cache_key(b).c_str(), lanes); }
+void cache_store(const esim_ad_batch* b, int shape, int lanes)
+{
+    tune_cache_store(cache_key(b).c_str(), 100 * shape + lanes);
+}
 
 void batch_release(esim_ad_batch* b)
 {
@@ -447,8 +302,8 @@ void batch_release(esim_ad_batch* b)
         if (i < (int)b->flag.size() && b->flag[i]) cudaFree(b->flag[i]);
         if (i < (int)b->nev.size() && b->nev[i]) cudaFree(b->nev[i]);
     }
-    void* g[] = {b->tile_seq, b->chunk_seq, b->flag_list, b->chunk_cnt, b->chunk_off, b->events, b->ctrl,
-                 b->d_steps};
+    void* g[] = {b->tile_seq_s[0], b->tile_seq_s[1], b->tile_seq_s[2], b->chunk_seq, b->flag_list, b->gram,
+                 b->chunk_cnt, b->chunk_off, b->events, b->ctrl, b->d_steps};
     for (void* p : g)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k) {
@@ -461,30 +316,50 @@ void batch_release(esim_ad_batch* b)
     for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
 }
 
-BatchGlobal globals(const esim_ad_batch* b)
+BatchGlobal globals(const esim_ad_batch* b, int shape)
 {
     BatchGlobal g;
     g.steps = b->d_steps;
-    g.tile_seq = b->tile_seq;
+    g.tile_seq = b->tile_seq_s[shape];
     g.chunk_seq = b->chunk_seq;
     g.flag_list = b->flag_list;
     g.chunk_cnt = b->chunk_cnt;
     g.chunk_off = b->chunk_off;
     g.events = b->events;
     g.capacity = b->cfg[0].event_capacity;
-    g.total_tiles = b->total_tiles;
+    g.total_tiles = b->total_tiles_s[shape];
     g.total_chunks = b->total_chunks;
+    g.tx = kTileWidths[shape];
     g.r = b->cfg[0].radius;
     g.s_px = (float)(kExp2Scale / ((double)b->cfg[0].h * b->cfg[0].radius));
     g.ctrl = b->ctrl;
     return g;
 }
 
-// Global parameters of the regression launch's accounting (finish()).
+// Parameters shared by every sequence of the batch (window, bandwidths,
+// ridge), the queue, the Gram records and the accounting of finish(); the
+// per-sequence ones travel in the step table.
 WlrParams global_wlr(const esim_ad_batch* b)
 {
+    const esim_ad_config& c0 = b->cfg[0];
     WlrParams p;
     memset(&p, 0, sizeof(p));
+    p.r = c0.radius;
+    p.T = c0.frames;
+    p.mixed = b->mixed ? 1 : 0;
+    p.s_coord = (float)(kExp2Scale / c0.h);
+    p.s_coord_px = (float)(kExp2Scale / ((double)c0.h * c0.radius));
+    for (int j = 0; j < 7; ++j) {
+        p.s_feat[j] = (float)(kExp2Scale / ((double)c0.h * c0.bandwidth[j]));
+        p.fscale[j] = b->mixed ? c0.feature_scale[j] : 1.0f;
+        p.q_scale[j] = (float)((double)p.s_feat[j] * p.fscale[j]);
+    }
+    p.ridge = c0.ridge;
+    p.sparse_stage = 1;
+    p.poll_limit = kPollLimit;
+    p.withhold_copy = 0;
+    p.flag_list = b->flag_list;
+    p.gram = b->gram;
     p.chunk_cnt = b->chunk_cnt;
     p.chunk_off = b->chunk_off;
     p.n_chunks = b->total_chunks;
@@ -494,7 +369,7 @@ WlrParams global_wlr(const esim_ad_batch* b)
 }
 
 // Fill the host step table for the frames of this step.
-void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames)
+void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames, int shape)
 {
     const esim_ad_config& c0 = b->cfg[0];
     for (int i = 0; i < b->n; ++i) {
@@ -504,7 +379,7 @@ void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames)
         const esim_ad_frame& f = frames[i];
         const bool act = f.radiance != nullptr;
         st.active = act ? 1 : 0;
-        st.tile_base = b->tile_base[i];
+        st.tile_base = b->tile_base[shape][i];
         st.chunk_base = b->chunk_base[i];
         const uint64_t t64 = b->t[i];
         const int t = (int)(t64 % 0x7fffffff);
@@ -525,7 +400,7 @@ void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames)
         }
         ip.W = c.width;
         ip.H = c.height;
-        ip.tiles_x = b->tiles_x[i];
+        ip.tiles_x = b->tiles_x[shape][i];
         ip.slot = t % c0.frames;
         ip.test = (c0.mode == ESIM_AD_ADAPTIVE && t64 > 0) ? 1 : 0;
         ip.log_eps = c0.log_eps;
@@ -543,8 +418,8 @@ void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames)
         wp.T = c0.frames;
         wp.t = t;
         wp.n_tau = (int)((t64 + 1) < (uint64_t)c0.frames ? (t64 + 1) : (uint64_t)c0.frames);
-        wp.tiles_x = b->tiles_x[i];
-        wp.n_tiles = b->n_tiles[i];
+        wp.tiles_x = b->tiles_x[shape][i];
+        wp.n_tiles = b->n_tiles[shape][i];
         wp.mixed = b->mixed ? 1 : 0;
         wp.init = t64 == 0 ? 1 : 0;
         wp.C = c.contrast;
@@ -569,9 +444,10 @@ void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames)
 }
 
 // Enqueue one step's work (after the step table has been copied) on stream s.
-cudaError_t enqueue_step_body(esim_ad_batch* b, int lanes, cudaStream_t s, bool profile)
+cudaError_t enqueue_step_body(esim_ad_batch* b, int shape, int lanes, cudaStream_t s, bool profile)
 {
-    const BatchGlobal g = globals(b);
+    const BatchGlobal g = globals(b, shape);
+    const WlrParams gp = global_wlr(b);
     auto rec = [&](int cls, bool start) {
         if (!profile) return;
         if (start) {
@@ -593,19 +469,23 @@ cudaError_t enqueue_step_body(esim_ad_batch* b, int lanes, cudaStream_t s, bool 
     e = cudaMemsetAsync(b->chunk_cnt, 0, (size_t)b->total_chunks * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     rec(0, true);
-    batch_ingest_kernel<<<b->total_tiles, kTilePix, 0, s>>>(g);
+    batch_ingest_kernel<<<b->total_tiles_s[shape], kTilePix, 0, s>>>(g);
     rec(0, false);
     rec(1, true);
-    pick_kernel(lanes, b->mixed)<<<b->grid, kTilePix, b->smem, s>>>(g, global_wlr(b));
+    pick_kernel(lanes, b->mixed)<<<b->grid, kTilePix, b->smem, s>>>(g, gp);
+    if (b->mixed)
+        batch_solve_kernel<true><<<b->solve_grid, kSolveThreads, 0, s>>>(g, gp);
+    else
+        batch_solve_kernel<false><<<b->solve_grid, kSolveThreads, 0, s>>>(g, gp);
     rec(1, false);
     rec(2, true);
     batch_event_write_kernel<<<b->total_chunks, kTilePix, 0, s>>>(g);
     rec(2, false);
-    b->prof_kernels += 3;
+    b->prof_kernels += 4;
     return cudaGetLastError();
 }
 
-cudaError_t build_graphs(esim_ad_batch* b, int lanes)
+cudaError_t build_graphs(esim_ad_batch* b, int shape, int lanes)
 {
     for (int k = 0; k < 2; ++k) {
         if (b->graph[k]) {
@@ -625,7 +505,7 @@ cudaError_t build_graphs(esim_ad_batch* b, int lanes)
         }
         cudaMemcpyAsync(b->d_steps, b->h_steps[k], sizeof(SeqStep) * b->n, cudaMemcpyHostToDevice, cs);
         const uint64_t kern = b->prof_kernels;
-        enqueue_step_body(b, lanes, cs, false);
+        enqueue_step_body(b, shape, lanes, cs, false);
         b->prof_kernels = kern;
         e = cudaStreamEndCapture(cs, &gr);
         cudaStreamDestroy(cs);
@@ -634,7 +514,6 @@ cudaError_t build_graphs(esim_ad_batch* b, int lanes)
         cudaGraphDestroy(gr);
         if (e != cudaSuccess) return e;
     }
-    b->graph_lanes = lanes;
     return cudaSuccess;
 }
 
@@ -687,32 +566,40 @@ esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, voi
     b->mixed = c0.precision == ESIM_AD_MIXED;
     cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
     b->N.resize(n_seq);
-    b->tiles_x.resize(n_seq);
-    b->n_tiles.resize(n_seq);
     b->n_chunks.resize(n_seq);
-    b->tile_base.resize(n_seq);
     b->chunk_base.resize(n_seq);
+    for (int sh = 0; sh < kTileShapes; ++sh) {
+        b->tiles_x[sh].resize(n_seq);
+        b->n_tiles[sh].resize(n_seq);
+        b->tile_base[sh].resize(n_seq);
+    }
     b->ring.assign(n_seq, nullptr);
     b->state.assign(n_seq, nullptr);
     b->alpha.assign(n_seq, nullptr);
     b->flag.assign(n_seq, nullptr);
     b->nev.assign(n_seq, nullptr);
     b->t.assign(n_seq, 0);
-    std::vector<uint16_t> tseq, cseq;
+    std::vector<uint16_t> tseq[kTileShapes], cseq;
+    int max_tiles = 0;
     for (int i = 0; i < n_seq; ++i) {
         const esim_ad_config& c = cfgs[i];
         b->N[i] = (size_t)c.width * c.height;
-        b->tiles_x[i] = (c.width + kTileX - 1) / kTileX;
-        b->n_tiles[i] = b->tiles_x[i] * ((c.height + kTileY - 1) / kTileY);
         b->n_chunks[i] = (int)((b->N[i] + kChunk - 1) / kChunk);
-        b->tile_base[i] = b->total_tiles;
         b->chunk_base[i] = b->total_chunks;
-        b->total_tiles += b->n_tiles[i];
         b->total_chunks += b->n_chunks[i];
         b->total_pix += b->N[i];
-        tseq.insert(tseq.end(), b->n_tiles[i], (uint16_t)i);
         cseq.insert(cseq.end(), b->n_chunks[i], (uint16_t)i);
+        for (int sh = 0; sh < kTileShapes; ++sh) {
+            const int tw = kTileWidths[sh], th = kTilePix / tw;
+            b->tiles_x[sh][i] = (c.width + tw - 1) / tw;
+            b->n_tiles[sh][i] = b->tiles_x[sh][i] * ((c.height + th - 1) / th);
+            b->tile_base[sh][i] = b->total_tiles_s[sh];
+            b->total_tiles_s[sh] += b->n_tiles[sh][i];
+            tseq[sh].insert(tseq[sh].end(), b->n_tiles[sh][i], (uint16_t)i);
+        }
     }
+    for (int sh = 0; sh < kTileShapes; ++sh) max_tiles = std::max(max_tiles, b->total_tiles_s[sh]);
+    const size_t list_cap = b->total_pix + 4 * (size_t)max_tiles;   // queue entries incl. tile padding
     auto fail = [&](esim_ad_status st) {
         cudaGetLastError();
         batch_release(b);
@@ -732,9 +619,11 @@ esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, voi
             cudaMemset(b->nev[i], 0, N * sizeof(int32_t)) != cudaSuccess)
             return fail(ESIM_AD_ECUDA);
     }
-    if (cudaMalloc((void**)&b->tile_seq, tseq.size() * 2) != cudaSuccess ||
-        cudaMalloc((void**)&b->chunk_seq, cseq.size() * 2) != cudaSuccess ||
-        cudaMalloc((void**)&b->flag_list, (b->total_pix + 4 * (size_t)b->total_tiles) * 4) != cudaSuccess ||
+    for (int sh = 0; sh < kTileShapes; ++sh)
+        if (cudaMalloc((void**)&b->tile_seq_s[sh], tseq[sh].size() * 2) != cudaSuccess) return fail(ESIM_AD_ENOMEM);
+    if (cudaMalloc((void**)&b->chunk_seq, cseq.size() * 2) != cudaSuccess ||
+        cudaMalloc((void**)&b->flag_list, list_cap * 4) != cudaSuccess ||
+        cudaMalloc((void**)&b->gram, list_cap * kGramRecordBytes) != cudaSuccess ||
         cudaMalloc((void**)&b->chunk_cnt, (size_t)b->total_chunks * 4) != cudaSuccess ||
         cudaMalloc((void**)&b->chunk_off, (size_t)b->total_chunks * 8) != cudaSuccess ||
         cudaMalloc((void**)&b->events, (size_t)c0.event_capacity * sizeof(esim_ad_batch_event)) != cudaSuccess ||
@@ -750,12 +639,15 @@ esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, voi
     }
     for (cudaEvent_t& e : b->tune_ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(ESIM_AD_ECUDA);
-    if (cudaMemcpy(b->tile_seq, tseq.data(), tseq.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->chunk_seq, cseq.data(), cseq.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+    for (int sh = 0; sh < kTileShapes; ++sh)
+        if (cudaMemcpy(b->tile_seq_s[sh], tseq[sh].data(), tseq[sh].size() * 2, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return fail(ESIM_AD_ECUDA);
+    if (cudaMemcpy(b->chunk_seq, cseq.data(), cseq.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->ctrl, 0, sizeof(Ctrl)) != cudaSuccess)
         return fail(ESIM_AD_ECUDA);
-    // the regression kernels' dynamic shared memory: window table and per-warp boxes
-    b->smem = sparse_layout(b->cfg[0].radius, b->mixed).total;
+    // the accumulation kernels' dynamic shared memory: window tables and per-warp boxes
+    b->smem = box_layout(b->cfg[0].radius).total;
     for (int lanes : {8, 16, 32})
         if (cudaFuncSetAttribute(pick_kernel(lanes, b->mixed), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  b->smem) != cudaSuccess)
@@ -767,22 +659,24 @@ esim_ad_status esim_ad_batch_init(const esim_ad_config* cfgs, int32_t n_seq, voi
         per_sm = 1;
     cudaGetLastError();
     b->grid = per_sm * b->num_sms;
-    // lanes per pixel: forced, cached, or tuned on the first adaptive steps
-    if (const char* e = getenv("ESIM_AD_BATCH_LANES")) {
-        const int v = atoi(e);
-        if (v == 8 || v == 16 || v == 32) {
-            b->lanes = v;
+    b->solve_grid = 3 * b->num_sms;
+    // tile shape and lanes per pixel: forced (both variables set), cached, or
+    // tuned on the first adaptive steps
+    {
+        const char* el = getenv("ESIM_AD_BATCH_LANES");
+        const char* et = getenv("ESIM_AD_BATCH_TILE");
+        const int l = el ? atoi(el) : 0, tw = et ? atoi(et) : 0;
+        int sh = -1;
+        for (int k = 0; k < kTileShapes; ++k)
+            if (kTileWidths[k] == tw) sh = k;
+        if ((l == 8 || l == 16 || l == 32) && sh >= 0) {
+            b->lanes = l;
+            b->shape = sh;
             b->tuned = true;
         }
     }
-    if (!b->tuned) {
-        const int v = cache_lookup(b);
-        if (v) {
-            b->lanes = v;
-            b->tuned = true;
-        }
-    }
-    if (build_graphs(b, b->lanes) != cudaSuccess) return fail(ESIM_AD_ECUDA);
+    if (!b->tuned && cache_lookup(b, &b->shape, &b->lanes)) b->tuned = true;
+    if (build_graphs(b, b->shape, b->lanes) != cudaSuccess) return fail(ESIM_AD_ECUDA);
     *out = b;
     return ESIM_AD_OK;
 }
@@ -804,7 +698,11 @@ esim_ad_status esim_ad_batch_step(esim_ad_batch* b, const esim_ad_frame* frames)
     const int k = b->cur;
     // the pinned table k was last read by the step launched two steps ago
     if (cudaEventSynchronize(b->h_free[k]) != cudaSuccess) return ESIM_AD_ECUDA;
-    fill_steps(b, b->h_steps[k], frames);
+    // the tuning steps run their own candidate's tile shape
+    const bool tuning0 = !b->tuned && b->cfg[0].mode == ESIM_AD_ADAPTIVE;
+    const int cand = b->tune_stage;
+    const int step_shape = tuning0 ? cand / 3 : b->shape;
+    fill_steps(b, b->h_steps[k], frames, step_shape);
     bool any_init = false, any_active = false;
     for (int i = 0; i < b->n; ++i)
         if (frames[i].radiance) {
@@ -817,13 +715,17 @@ esim_ad_status esim_ad_batch_step(esim_ad_batch* b, const esim_ad_frame* frames)
     if (tuning || b->prof_on) {
         // direct launches (timed) instead of the graph
         e = cudaMemcpyAsync(b->d_steps, b->h_steps[k], sizeof(SeqStep) * b->n, cudaMemcpyHostToDevice, b->stream);
-        const int lanes = tuning ? kCandidates[b->tune_stage] : b->lanes;
-        if (tuning) cudaEventRecord(b->tune_ev[2 * b->tune_stage], b->stream);
-        if (e == cudaSuccess) e = enqueue_step_body(b, lanes, b->stream, b->prof_on);
-        if (tuning) cudaEventRecord(b->tune_ev[2 * b->tune_stage + 1], b->stream);
-    } else {
+        const int lanes = tuning ? kCandLanes[cand % 3] : b->lanes;
+        if (tuning) cudaEventRecord(b->tune_ev[2 * cand], b->stream);
+        if (e == cudaSuccess) e = enqueue_step_body(b, step_shape, lanes, b->stream, b->prof_on);
+        if (tuning) cudaEventRecord(b->tune_ev[2 * cand + 1], b->stream);
+    } else if (step_shape == b->shape) {
         e = cudaGraphLaunch(b->graph[k], b->stream);
-        b->prof_kernels += 3;
+        b->prof_kernels += 4;
+    } else {
+        // a start-up step while tuning is pending: the graph's tile shape may differ
+        e = cudaMemcpyAsync(b->d_steps, b->h_steps[k], sizeof(SeqStep) * b->n, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = enqueue_step_body(b, step_shape, b->lanes, b->stream, false);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->h_free[k], b->stream);
     if (e != cudaSuccess) {
@@ -837,24 +739,26 @@ esim_ad_status esim_ad_batch_step(esim_ad_batch* b, const esim_ad_frame* frames)
         cudaMemcpyAsync(&h, b->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream);
         cudaStreamSynchronize(b->stream);
         float ms = 0.0f;
-        cudaEventElapsedTime(&ms, b->tune_ev[2 * b->tune_stage], b->tune_ev[2 * b->tune_stage + 1]);
-        b->tune_ms[b->tune_stage] = ms;
-        b->tune_reg[b->tune_stage] = h.regressions - b->reg_before;
+        cudaEventElapsedTime(&ms, b->tune_ev[2 * cand], b->tune_ev[2 * cand + 1]);
+        b->tune_ms[cand] = ms;
+        b->tune_reg[cand] = h.regressions - b->reg_before;
         b->reg_before = h.regressions;
-        if (++b->tune_stage == 3) {
-            int best = 1;
+        if (++b->tune_stage == kNumCandidates) {
+            // the pair with the least step time per regressed pixel
+            int best = 4;   // 32x8 tiles, 8 lanes
             double best_cost = 1e300;
-            for (int c = 0; c < 3; ++c) {
+            for (int c = 0; c < kNumCandidates; ++c) {
                 const double cost = b->tune_ms[c] / (double)(b->tune_reg[c] ? b->tune_reg[c] : 1);
                 if (cost < best_cost) {
                     best_cost = cost;
                     best = c;
                 }
             }
-            b->lanes = kCandidates[best];
+            b->shape = best / 3;
+            b->lanes = kCandLanes[best % 3];
             b->tuned = true;
-            cache_store(b, b->lanes);
-            if (build_graphs(b, b->lanes) != cudaSuccess) return ESIM_AD_ECUDA;
+            cache_store(b, b->shape, b->lanes);
+            if (build_graphs(b, b->shape, b->lanes) != cudaSuccess) return ESIM_AD_ECUDA;
         }
     } else if (!b->tuned) {
         // keep the regression count current for the tuning steps to come
@@ -953,6 +857,15 @@ esim_ad_status esim_ad_batch_stats(esim_ad_batch* b, esim_ad_stats* out, int32_t
     out->pixels = b->total_pix;
     out->fp64_solves = h.fp64_solves;
     if (lanes_out) *lanes_out = b->lanes;
+    return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_batch_tiling(esim_ad_batch* b, int32_t* tile_w, int32_t* tile_h, int32_t* lanes)
+{
+    if (!b) return ESIM_AD_EINVAL;
+    if (tile_w) *tile_w = kTileWidths[b->shape];
+    if (tile_h) *tile_h = kTilePix / kTileWidths[b->shape];
+    if (lanes) *lanes = b->lanes;
     return ESIM_AD_OK;
 }
 

@@ -60,10 +60,11 @@ struct esim_ad_ctx {
     int W = 0, H = 0;
     size_t N = 0;
     int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_chunks = 0;
-    int smem_bytes = 0;
+    int smem_bytes = 0;          // dense tile-staged regression
+    int smem_adaptive = 0;       // adaptive regression: the larger of its two forms
     int nbuf = 2;
     int wlr_grid = 0;
-    int sparse_grid = 0;
+    int adaptive_grid = 0;
     int solve_grid = 0;
     int sparse_stage = 1;        // sparse kernel stages window boxes (ESIM_AD_SPARSE_STAGE=0: L1 only)
     int test_withhold = 0;       // ESIM_AD_TEST_WITHHOLD_COPY=1: timeout injection for tests
@@ -303,15 +304,19 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         delete c;
         return ESIM_AD_ECUDA;
     }
-    if (encode_ring_map(c) != ESIM_AD_OK || wlr_prepare(c->smem_bytes, c->mixed) != cudaSuccess ||
-        wlr_sparse_prepare(cfg->radius, c->mixed) != cudaSuccess) {
+    {
+        const int sp = wlr_sparse_smem(cfg->radius, c->mixed);
+        c->smem_adaptive = c->smem_bytes > sp ? c->smem_bytes : sp;
+    }
+    if (encode_ring_map(c) != ESIM_AD_OK ||
+        wlr_prepare(c->smem_bytes, c->smem_adaptive, c->mixed) != cudaSuccess) {
         cudaGetLastError();
         release(c);
         delete c;
         return ESIM_AD_ECUDA;
     }
-    c->wlr_grid = wlr_grid(c->smem_bytes, num_sms, c->mixed);
-    c->sparse_grid = wlr_sparse_grid(num_sms, c->mixed, cfg->radius);
+    c->wlr_grid = wlr_grid(c->smem_bytes, num_sms, c->mixed, false);
+    c->adaptive_grid = wlr_grid(c->smem_adaptive, num_sms, c->mixed, true);
     c->solve_grid = wlr_solve_grid(num_sms);
     // default: frames with up to 1/8 of the pixels flagged take the sparse kernel
     // (measured faster than tile staging at the 1-2% densities of edge-like
@@ -510,16 +515,15 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     wp.ctrl = c->ctrl;
     {
         ProfScope ps(c, 1);
-        const int grid = wp.dense ? (c->n_tiles < c->wlr_grid ? c->n_tiles : c->wlr_grid) : c->wlr_grid;
-        if (launch_wlr(c->tmap, wp, c->mixed, grid, c->smem_bytes, c->stream) != cudaSuccess)
+        // pass 1: dense frames tile-staged over every tile; adaptive frames in one
+        // launch that picks window boxes or the tile queue from the flagged total
+        const int grid = wp.dense ? (c->n_tiles < c->wlr_grid ? c->n_tiles : c->wlr_grid) : c->adaptive_grid;
+        if (launch_wlr(c->tmap, wp, c->mixed, grid, wp.dense ? c->smem_bytes : c->smem_adaptive, c->stream) !=
+            cudaSuccess)
             return ESIM_AD_ECUDA;
-        // adaptive frames: the sparse kernel takes the frame when few pixels are
-        // flagged; each of the two launches returns at once on the other's frames
-        if (!wp.dense && launch_wlr_sparse(wp, c->mixed, c->sparse_grid, c->stream) != cudaSuccess)
-            return ESIM_AD_ECUDA;
-        // solve every accumulated system, emit, and scan the event counts
+        // pass 2: solve every accumulated system, emit, and scan the event counts
         if (launch_wlr_solve(wp, c->mixed, c->solve_grid, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
-        c->prof_kernels += wp.dense ? 2 : 3;
+        c->prof_kernels += 2;
     }
 
     if (c->t > 0) {

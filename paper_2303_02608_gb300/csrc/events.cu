@@ -1,18 +1,17 @@
 // Ordered event writer (Eq. 1 records at fixed frame times).
 //
-// The regression kernel leaves a signed per-pixel event count p*n in a map
-// and, in the simulator's own path, already sums |p*n| per 2048-pixel chunk
-// and scans the chunk counts (its last CTA), so only the write launch runs.
-// The stand-alone writer runs both launches below.  Either way the records
-// come out in canonical order (row, column, repeat) without sorting and
-// without atomics on the output position, so the output is deterministic:
-//   1. count: each 2048-pixel chunk sums |p*n|; the last CTA to finish (ticket
-//      from an atomic counter, after a release fence) scans the chunk counts
-//      into global offsets and advances the event total.  No CTA waits on
-//      another.
-//   2. write: each chunk rescans its pixels and writes its records at its
-//      offset.  Records past the buffer capacity are dropped and the sticky
-//      overflow bit is set; the total still counts them.
+// The solve kernel leaves a signed per-pixel event count p*n in a map and,
+// in the simulator's own path, already sums |p*n| per 2048-pixel chunk, so
+// only the write launch runs; the stand-alone writer runs both launches below.
+// Either way the records come out in canonical order (row, column, repeat)
+// without sorting and without atomics on the output position, so the output
+// is deterministic:
+//   1. count: each 2048-pixel chunk sums |p*n| (counts beyond
+//      kMaxCountPerPixel in magnitude set a status bit instead).
+//   2. write: each chunk's CTA adds up the counts of all earlier chunks for
+//      its offset, rescans its pixels and writes its records there.  Records
+//      past the buffer capacity are dropped and the sticky overflow bit is
+//      set; the total still counts them.
 #include "internal.h"
 #include "block_scan.cuh"
 
@@ -26,56 +25,76 @@ constexpr int kPer = kChunk / kThreads;  // 8 pixels per thread
 __global__ void __launch_bounds__(kThreads) event_count_kernel(EventParams p)
 {
     __shared__ int s_warp[kThreads / 32];
-    __shared__ bool s_last;
     const long long p0 = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * kPer;
     int c = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k)
-        if (p0 + k < p.n_pix) c += abs(p.nev[p0 + k]);
-    int total;
-    block_exclusive_scan(c, s_warp, total);
-    if (threadIdx.x == 0) {
-        p.chunk_cnt[blockIdx.x] = (uint32_t)total;
-        __threadfence();
-        const uint32_t ticket = atomicAdd(&p.ctrl->chunk_done, 1u);
-        s_last = (ticket == (uint32_t)p.n_chunks - 1u);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // last CTA: exclusive scan of the chunk counts, in chunk order
-    unsigned long long running = *(volatile unsigned long long*)&p.ctrl->ev_total;
-    for (int base = 0; base < p.n_chunks; base += kThreads) {
-        const int j = base + threadIdx.x;
-        const int v = (j < p.n_chunks) ? (int)*(volatile uint32_t*)&p.chunk_cnt[j] : 0;
-        int seg;
-        const int off = block_exclusive_scan(v, s_warp, seg);
-        if (j < p.n_chunks) p.chunk_off[j] = running + (unsigned long long)off;
-        running += (unsigned long long)seg;
-    }
-    if (threadIdx.x == 0) {
-        const unsigned long long added = running - p.ctrl->ev_total;
-        p.ctrl->ev_total = running;
-        p.ctrl->ev_cum += added;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) event_write_kernel(EventParams p)
-{
-    __shared__ int s_warp[kThreads / 32];
-    if (p.chunk_cnt[blockIdx.x] == 0u) return;   // no events in this chunk
-    const long long p0 = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * kPer;
-    int v[kPer];
-    int c = 0;
+    bool bad = false;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-        v[k] = (p0 + k < p.n_pix) ? p.nev[p0 + k] : 0;
-        c += abs(v[k]);
+        if (p0 + k >= p.n_pix) continue;
+        const int v = p.nev[p0 + k];
+        if (v > kMaxCountPerPixel || v < -kMaxCountPerPixel) bad = true;
+        else c += v < 0 ? -v : v;
     }
+    if (bad) atomicOr(&p.ctrl->status, kStatusCountRange);
+    int total;
+    block_exclusive_scan(c, s_warp, total);
+    if (threadIdx.x == 0) p.chunk_cnt[blockIdx.x] = (uint32_t)total;
+}
+
+// Sum of chunk_cnt[0, n) by the whole block (every thread gets the sum).
+__device__ __forceinline__ unsigned long long block_prefix_count(const uint32_t* cnt, int n, unsigned long long* s_red)
+{
+    unsigned long long v = 0;
+    for (int j = (int)threadIdx.x; j < n; j += kThreads) v += cnt[j];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
+    return t;
+}
+
+// Each chunk finds its output offset itself: the event total before this
+// frame (ev_base) plus the counts of all earlier chunks, summed by the block
+// (no CTA waits on another and no serial scan); the last chunk's CTA records
+// the new total.
+__global__ void __launch_bounds__(kThreads, 8) event_write_kernel(EventParams p)
+{
+    __shared__ int s_warp[kThreads / 32];
+    __shared__ unsigned long long s_red[kThreads / 32];
+    const bool last = blockIdx.x == gridDim.x - 1;
+    const uint32_t cnt = p.chunk_cnt[blockIdx.x];
+    if (cnt == 0u && !last) return;   // no events in this chunk
+    const long long p0 = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * kPer;
+    int v[kPer];
+    if (p0 + kPer <= p.n_pix && ((reinterpret_cast<uintptr_t>(p.nev + p0) & 15u) == 0)) {
+        const int4 a = *reinterpret_cast<const int4*>(p.nev + p0);
+        const int4 b = *reinterpret_cast<const int4*>(p.nev + p0 + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) v[k] = (p0 + k < p.n_pix) ? p.nev[p0 + k] : 0;
+    }
+    const unsigned long long before = p.ctrl->ev_base + block_prefix_count(p.chunk_cnt, blockIdx.x, s_red);
+    const bool range_ok = (p.ctrl->status & kStatusCountRange) == 0u;
+    if (last && threadIdx.x == 0) {
+        if (!range_ok) {
+            p.ctrl->ev_total = ~0ull;   // the map was out of range: nothing is written
+        } else {
+            p.ctrl->ev_total = before + cnt;
+            p.ctrl->ev_cum += before + cnt - p.ctrl->ev_base;
+        }
+    }
+    if (cnt == 0u || !range_ok) return;
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) c += abs(v[k]);
     int total;
     const int off = block_exclusive_scan(c, s_warp, total);
     if (total == 0) return;
-    unsigned long long pos = p.chunk_off[blockIdx.x] + (unsigned long long)off;
+    unsigned long long pos = before + (unsigned long long)off;
     bool overflow = false;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {

@@ -1,14 +1,13 @@
 // Ordered event writer that allocates nothing.
 //
 // Some callers cannot allocate device memory at the point where they need
-// events written: code running under a caller's CUDA stream capture with an
-// allocation-free policy, latency-critical loops where cudaMalloc's implicit
+// events written: latency-critical loops where cudaMalloc's implicit
 // device-wide synchronisation would stall other streams, and plugins hosted by
 // a framework that owns every device allocation.  For them,
 // esim_ad_write_events_noalloc runs the same two event-writer kernels as the
-// simulator context, but their scratch (the chunk counts, chunk offsets and
-// the control block) lives in one fixed-size array of this file that every
-// GPU loading the library holds until the process exits.
+// simulator context, but their scratch (the control block and the per-chunk
+// counts) lives in one fixed-size array of this file that every GPU loading
+// the library holds until the process exits.
 //
 // The array's name in host code is only a host-side stand-in, not a device
 // address, so its device address is looked up once per device with
@@ -24,8 +23,7 @@ constexpr long long kNoAllocMaxPixels = 1ll << 24;                        // 16,
 constexpr int kNoAllocMaxChunks = (int)(kNoAllocMaxPixels / kChunk);      // 8192 chunks
 constexpr size_t kCtrlBytes = 256;
 constexpr size_t kCntBytes = (size_t)kNoAllocMaxChunks * sizeof(uint32_t);
-constexpr size_t kOffBytes = (size_t)kNoAllocMaxChunks * sizeof(unsigned long long);
-constexpr size_t kScratchBytes = kCtrlBytes + kCntBytes + kOffBytes;      // 98,560 bytes
+constexpr size_t kScratchBytes = kCtrlBytes + kCntBytes;                  // 33,024 bytes
 static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block must fit its slot");
 
 // Shared by every call on a device; holds the last call's contents.
@@ -84,7 +82,7 @@ extern "C" esim_ad_status esim_ad_write_events_noalloc(const int32_t* counts, in
     p.n_chunks = (int)((n_pix + kChunk - 1) / kChunk);
     p.frame = frame;
     p.chunk_cnt = reinterpret_cast<uint32_t*>(base + kCtrlBytes);
-    p.chunk_off = reinterpret_cast<unsigned long long*>(base + kCtrlBytes + kCntBytes);
+    p.chunk_off = nullptr;   // the writer places each chunk from the counts alone
     p.events = events;
     p.capacity = capacity;
     p.ctrl = ctrl;

@@ -41,8 +41,13 @@ struct Ctrl {
     unsigned long long fp64_solves; // mixed form: systems re-solved in FP64
     uint32_t status;                // sticky kStatus* bits
     uint32_t pad2;
+    unsigned long long ev_base;     // ev_total before this frame's events (set by the solve kernel)
 };
 constexpr size_t kCtrlPerFrameBytes = 24;
+// Largest |signed event count| of one pixel in one frame: a 2048-pixel chunk then
+// sums to at most 2^30 events, within the 32-bit chunk counts.
+constexpr int kMaxCountPerPixel = 1 << 19;
+constexpr uint32_t kStatusCountRange = 4u;   // a count map held |count| > kMaxCountPerPixel
 constexpr size_t kGramRecordBytes = 272;   // one Gram record: 66 sums padded to 68 floats
 constexpr uint32_t kPollLimit = 1u << 24;   // default bound on an mbarrier wait (polls)
 
@@ -179,15 +184,16 @@ cudaError_t launch_ingest(const IngestParams& p, int n_tiles, cudaStream_t s);
 // Autotuning cache (tune_cache.cu): value for key, or 0 if none.
 int tune_cache_lookup(const char* key);
 void tune_cache_store(const char* key, int value);
-cudaError_t wlr_prepare(int smem_bytes, bool mixed);
+// Regression pass 1: dense frames (every tile) and adaptive frames (one launch
+// choosing on the device between the sparse window-box form and the
+// tile-staged queue form); the adaptive kernel's shared memory is the larger
+// of the two forms'.
+cudaError_t wlr_prepare(int smem_dense, int smem_adaptive, bool mixed);
 size_t wlr_smem_bytes(int r, bool mixed, int max_smem_per_sm, int* nbuf);
-int wlr_grid(int smem_bytes, int num_sms, bool mixed);
+int wlr_grid(int smem_bytes, int num_sms, bool mixed, bool adaptive);
 int wlr_sparse_smem(int r, bool mixed);
-cudaError_t wlr_sparse_prepare(int r, bool mixed);
-int wlr_sparse_grid(int num_sms, bool mixed, int r);
 cudaError_t launch_wlr(const CUtensorMap& tmap, const WlrParams& p, bool mixed, int grid,
                        int smem_bytes, cudaStream_t s);
-cudaError_t launch_wlr_sparse(const WlrParams& p, bool mixed, int grid, cudaStream_t s);
 cudaError_t launch_wlr_solve(const WlrParams& p, bool mixed, int grid, cudaStream_t s);
 int wlr_solve_grid(int num_sms);
 cudaError_t launch_events(const EventParams& p, cudaStream_t s);

@@ -713,8 +713,12 @@ __device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const f
     } else {
         L = p.state[3 * N + i].w;
         const float dl = alpha - L;
-        const float n = floorf(fabsf(dl) / p.C);
+        float n = floorf(fabsf(dl) / p.C);
         if (!(n >= 1.0f)) return;  // no event: keep the model
+        if (n > (float)kMaxCountPerPixel) {   // beyond what the writer's counts hold
+            n = (float)kMaxCountPerPixel;
+            atomicOr(&p.ctrl->status, kStatusOverflow);
+        }
         const float pol = dl > 0.0f ? 1.0f : -1.0f;
         L = fmaf(pol * n, p.C, L);
         p.nev[i] = (int32_t)(pol * n);

@@ -129,6 +129,22 @@ def test_dense_form_descriptors_checked_on_the_host(lib):
         lib.ESIM_AD_EINVAL
 
 
+def test_noalloc_writer_checks_arguments_on_the_host(lib):
+    """The allocation-free writer refuses bad arguments before any CUDA call:
+    NULL counts or total, NULL events with a capacity, sides outside
+    1..65535, and frames above 16,777,216 pixels (the fixed scratch)."""
+    f = lib.load_library().esim_ad_write_events_noalloc
+    p = 256   # a non-NULL dummy address (never dereferenced: the checks come first)
+    EINVAL = lib.ESIM_AD_EINVAL
+    assert f(None, 64, 64, 0, p, 10, p, None) == EINVAL          # counts
+    assert f(p, 64, 64, 0, p, 10, None, None) == EINVAL          # total_device
+    assert f(p, 64, 64, 0, None, 10, p, None) == EINVAL          # events with capacity > 0
+    for w, h in ((0, 64), (64, 0), (-1, 64), (65536, 1), (1, 65536)):
+        assert f(p, w, h, 0, p, 10, p, None) == EINVAL, (w, h)
+    assert f(p, 4097, 4096, 0, p, 10, p, None) == EINVAL         # 16,781,312 pixels
+    assert f(p, 65535, 65535, 0, p, 10, p, None) == EINVAL
+
+
 def test_init_without_gpu_reports_cuda_error(lib):
     import torch
     if torch.cuda.is_available():
