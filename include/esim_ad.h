@@ -29,8 +29,8 @@
  *   - ESIM_AD_EOVERFLOW (device event buffer overflowed) and ESIM_AD_ETIMEOUT
  *     (a bounded device wait expired) are sticky: every later call except
  *     esim_ad_stats, esim_ad_reset and esim_ad_destroy returns ESIM_AD_ESTATE.
- *   - Planar image buffers are [channel][height][width], row-major, densely
- *     packed (row pitch = width elements).
+ *   - Planar image buffers are [channel][height][pitch], row-major; the pitch
+ *     is esim_ad_frame.pitch_elems (0 = width, densely packed).
  *   - A context is not thread-safe; use one context per host thread.
  */
 #ifndef ESIM_AD_H
@@ -131,6 +131,10 @@ typedef struct esim_ad_frame {
                                 albedo rgb, each stored as x_j / feature_scale_j */
     int32_t      on_host;    /* 0: device pointers, 1: host pointers            */
     int32_t      reserved0;
+    int64_t      pitch_elems; /* row pitch of every input plane in elements (0 =
+                                width); a plane is then [H][pitch], and plane c
+                                of a multi-plane input starts c*H*pitch elements
+                                in.  EINVAL if nonzero and below width.        */
 } esim_ad_frame;
 
 /* One DVS event e = (q_k, t_l, p_k) of Eq. 1; 12 bytes. */
@@ -365,7 +369,7 @@ esim_ad_status esim_ad_wlr_backward(const esim_ad_wlr_desc* d, const float* radi
 /*
  * Second-order form: the dense regression of Eqs. 4-5 with the Taylor
  * expansion of Eq. 3 carried to second order, the non-linear regression that
- * the paper's conclusion (Section 5) names as its extension.  Per frame t and
+ * the paper's conclusion (Section 4) names as its extension.  Per frame t and
  * pixel c, over the same window and weights as esim_ad_wlr_forward, it fits
  *     y ~ alpha + beta^T d + sum_{a<=b} gamma_ab d_a d_b,   d = x^i - x^c
  * (55 unknowns over the 9-D feature: coordinate offset (q - c)/r, normal,
@@ -427,7 +431,7 @@ esim_ad_status esim_ad_write_events_noalloc(const int32_t* counts, int32_t width
                                             uint64_t* total_device, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
- * Evaluation (Section 4, quantitative comparison).
+ * Evaluation (Section 3, quantitative comparison).
  *
  * esim_ad_esim_frame: one frame of the plain ESIM simulator the paper compares
  * against (and, run on noise-free frames, the stand-in for its reference

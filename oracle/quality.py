@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the event-quality evaluation (Section 4, quantitative
+"""FP64 CPU oracle of the event-quality evaluation (Section 3, quantitative
 comparison).
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: the CUDA evaluation

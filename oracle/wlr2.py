@@ -7,7 +7,7 @@ CPU-baseline leg use it; the library never does.  Plain numpy in float64.
 What it computes.  Eq. 3 approximates the unknown log brightness f around the
 centre feature x^c by its first-order Taylor expansion, and Eqs. 4-5 fit that
 expansion by Gaussian-weighted least squares over the window Omega_c.  The
-paper's conclusion (Section 5) names a non-linear regression as the natural
+paper's conclusion (Section 4) names a non-linear regression as the natural
 extension.  Here the expansion is carried one order further:
 
     f(x) ~ alpha + beta^T d + sum_{a <= b} gamma_ab d_a d_b,   d = x - x^c,

@@ -67,7 +67,7 @@ class esim_ad_frame(ctypes.Structure):
     _fields_ = [
         ("radiance", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("normal", ctypes.c_void_p),
         ("albedo", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("features", ctypes.c_void_p),
-        ("on_host", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("on_host", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("pitch_elems", ctypes.c_int64),
     ]
 
 
@@ -237,9 +237,9 @@ def esim_ad_init(cfg: esim_ad_config, cuda_stream: int = 0) -> int:
 
 
 def esim_ad_push_frame(ctx: int, radiance: int, normal: int = 0, albedo: int = 0, depth: int = 0,
-                       variance: int = 0, on_host: bool = False, features: int = 0) -> None:
+                       variance: int = 0, on_host: bool = False, features: int = 0, pitch: int = 0) -> None:
     f = esim_ad_frame(radiance, variance or None, normal or None, albedo or None, depth or None,
-                      features or None, int(on_host), 0)
+                      features or None, int(on_host), 0, int(pitch))
     _check(load_library().esim_ad_push_frame(ctypes.c_void_p(ctx), ctypes.byref(f)), "esim_ad_push_frame")
 
 
@@ -585,7 +585,9 @@ class Simulator:
 
     __del__ = close
 
-    def push(self, frame: dict) -> None:
+    def push(self, frame: dict, pitch: int = 0) -> None:
+        """Push one frame: planes [C][H][W] (or [C][H][pitch] with only the first
+        W columns read, when pitch is given)."""
         t = self._torch
         keys = ["radiance"] + (["features"] if "features" in frame else ["normal", "albedo", "depth"])
         if self.cfg.guard_kappa > 0 and frame.get("variance") is not None:
@@ -598,7 +600,7 @@ class Simulator:
         ptr = {k: v.data_ptr() for k, v in zip(keys, planes)}
         esim_ad_push_frame(self.ctx, ptr["radiance"], ptr.get("normal", 0), ptr.get("albedo", 0),
                            ptr.get("depth", 0), variance=ptr.get("variance", 0), on_host=on_host,
-                           features=ptr.get("features", 0))
+                           features=ptr.get("features", 0), pitch=pitch)
         # inputs (device planes, or pinned host planes copied asynchronously) are
         # read in stream order; keep them alive until the next sync point
         self._keep.append(planes)

@@ -3,7 +3,7 @@ Gaussian (Eq. 5) fitted by gradient descent on the differentiation form's loss,
 mean over pixels and frames of (alpha - ln(Y_clean + eps))^2, so that the
 fitted b can be fed back into the adaptive simulator.  The paper keeps
 h = 1, b_j = 1 and reports that per-pixel bandwidth optimisation (after
-Moon et al.) costs about 8x the time for little gain (Section 4); this is the
+Moon et al.) costs about 8x the time for little gain (Section 3); this is the
 global, learned alternative.
 
 Every forward and backward pass runs the library's dense regression and its

@@ -400,6 +400,7 @@ void fill_steps(esim_ad_batch* b, SeqStep* h, const esim_ad_frame* frames, int s
         }
         ip.W = c.width;
         ip.H = c.height;
+        ip.pitch = f.pitch_elems ? f.pitch_elems : c.width;
         ip.tiles_x = b->tiles_x[shape][i];
         ip.slot = t % c0.frames;
         ip.test = (c0.mode == ESIM_AD_ADAPTIVE && t64 > 0) ? 1 : 0;
@@ -689,6 +690,7 @@ esim_ad_status esim_ad_batch_step(esim_ad_batch* b, const esim_ad_frame* frames)
         const esim_ad_frame& f = frames[i];
         if (!f.radiance) continue;
         if (f.on_host) return ESIM_AD_EINVAL;
+        if (f.pitch_elems != 0 && f.pitch_elems < b->cfg[i].width) return ESIM_AD_EINVAL;
         if (b->cfg[0].feature_fmt == ESIM_AD_FEAT_BF16 ? !f.features : (!f.normal || !f.albedo || !f.depth))
             return ESIM_AD_EINVAL;
     }

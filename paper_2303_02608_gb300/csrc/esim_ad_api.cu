@@ -367,39 +367,51 @@ static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, e
     if (cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[s], 0) != cudaSuccess) return ESIM_AD_ECUDA;
     // landing layout: radiance at 0 (up to 3N floats), features after it, the
     // guard's variance plane last
-    const size_t rad_bytes = c->cfg.radiance_fmt == ESIM_AD_LOGLUMA_F16 ? N * 2
-                           : (c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1) * N * 4;
+    // each input (planes of `elem` bytes, rows of `pitch` elements on the host)
+    // lands densely packed; the staged frame has row pitch = width
     struct Copy {
         const void* src;
-        size_t off, bytes;
+        size_t off, elem;
+        int planes;
     };
     Copy cp[5];
     int n = 0;
-    cp[n++] = {f->radiance, 0, rad_bytes};
+    const int rad_planes = c->cfg.radiance_fmt == ESIM_AD_RGB_F32 ? 3 : 1;
+    const size_t rad_elem = c->cfg.radiance_fmt == ESIM_AD_LOGLUMA_F16 ? 2 : 4;
+    cp[n++] = {f->radiance, 0, rad_elem, rad_planes};
     *dev = *f;
     dev->on_host = 0;
+    dev->pitch_elems = 0;
     dev->radiance = base;
     if (c->cfg.feature_fmt == ESIM_AD_FEAT_BF16) {
-        cp[n++] = {f->features, 12 * N, 7 * N * 2};
+        cp[n++] = {f->features, 12 * N, 2, 7};
         dev->features = base + 12 * N;
     } else {
-        cp[n++] = {f->normal, 12 * N, 3 * N * 4};
-        cp[n++] = {f->albedo, 24 * N, 3 * N * 4};
-        cp[n++] = {f->depth, 36 * N, N * 4};
+        cp[n++] = {f->normal, 12 * N, 4, 3};
+        cp[n++] = {f->albedo, 24 * N, 4, 3};
+        cp[n++] = {f->depth, 36 * N, 4, 1};
         dev->normal = reinterpret_cast<const float*>(base + 12 * N);
         dev->albedo = reinterpret_cast<const float*>(base + 24 * N);
         dev->depth = reinterpret_cast<const float*>(base + 36 * N);
     }
     if (c->cfg.guard_kappa > 0.0f && f->variance) {
-        cp[n++] = {f->variance, 40 * N, N * 4};
+        cp[n++] = {f->variance, 40 * N, 4, 1};
         dev->variance = reinterpret_cast<const float*>(base + 40 * N);
     } else {
         dev->variance = nullptr;
     }
-    for (int k = 0; k < n; ++k)
-        if (cudaMemcpyAsync(base + cp[k].off, cp[k].src, cp[k].bytes, cudaMemcpyHostToDevice,
-                            c->copy_stream) != cudaSuccess)
-            return ESIM_AD_ECUDA;
+    const size_t pitch = f->pitch_elems ? (size_t)f->pitch_elems : (size_t)c->W;
+    for (int k = 0; k < n; ++k) {
+        const size_t e = cp[k].elem;
+        cudaError_t err;
+        if (pitch == (size_t)c->W)
+            err = cudaMemcpyAsync(base + cp[k].off, cp[k].src, cp[k].planes * N * e, cudaMemcpyHostToDevice,
+                                  c->copy_stream);
+        else   // all planes at once: rows of W elements out of rows of `pitch`
+            err = cudaMemcpy2DAsync(base + cp[k].off, c->W * e, cp[k].src, pitch * e, c->W * e,
+                                    (size_t)cp[k].planes * c->H, cudaMemcpyHostToDevice, c->copy_stream);
+        if (err != cudaSuccess) return ESIM_AD_ECUDA;
+    }
     if (cudaEventRecord(c->ev_copied[s], c->copy_stream) != cudaSuccess) return ESIM_AD_ECUDA;
     if (cudaStreamWaitEvent(c->stream, c->ev_copied[s], 0) != cudaSuccess) return ESIM_AD_ECUDA;
     *slot_out = s;
@@ -410,6 +422,7 @@ static esim_ad_status stage_host_frame(esim_ad_ctx* c, const esim_ad_frame* f, e
 esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
 {
     if (!c || !fin || !fin->radiance) return ESIM_AD_EINVAL;
+    if (fin->pitch_elems != 0 && fin->pitch_elems < c->W) return ESIM_AD_EINVAL;
     if (c->cfg.feature_fmt == ESIM_AD_FEAT_BF16 ? !fin->features
                                                 : (!fin->normal || !fin->albedo || !fin->depth))
         return ESIM_AD_EINVAL;
@@ -443,6 +456,7 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     }
     ip.W = c->W;
     ip.H = c->H;
+    ip.pitch = f->pitch_elems ? f->pitch_elems : c->W;
     ip.tiles_x = c->tiles_x;
     ip.slot = t % c->cfg.frames;
     ip.test = adaptive_test ? 1 : 0;

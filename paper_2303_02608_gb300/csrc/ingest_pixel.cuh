@@ -16,19 +16,21 @@ __device__ __forceinline__ int ingest_pixel(const IngestParams& p, int x, int y)
     const size_t N = (size_t)p.W * p.H;
     int flag = 0;
     if (inside) {
-        const size_t i = (size_t)y * p.W + x;
+        const size_t i = (size_t)y * p.W + x;                 // ring, model and maps (dense)
+        const size_t ii = (size_t)y * p.pitch + x;            // inputs (row pitch p.pitch)
+        const size_t NP = (size_t)p.H * p.pitch;              // input plane stride
         float yv;
         float Yeps = -1.0f;   // Y + eps when the input is linear radiance
         if (p.rad_fmt == ESIM_AD_LOGLUMA_F16) {
-            yv = __half2float(reinterpret_cast<const __half*>(p.rad)[i]);
+            yv = __half2float(reinterpret_cast<const __half*>(p.rad)[ii]);
         } else {
             const float* rad = reinterpret_cast<const float*>(p.rad);
             float Y;
             if (p.rad_fmt == ESIM_AD_RGB_F32) {
                 // Rec.709 luminance of the RGB radiance
-                Y = 0.2126f * __ldg(rad + i) + 0.7152f * __ldg(rad + N + i) + 0.0722f * __ldg(rad + 2 * N + i);
+                Y = 0.2126f * __ldg(rad + ii) + 0.7152f * __ldg(rad + NP + ii) + 0.0722f * __ldg(rad + 2 * NP + ii);
             } else {
-                Y = __ldg(rad + i);
+                Y = __ldg(rad + ii);
             }
             Yeps = Y + p.log_eps;
             yv = logf(Yeps);
@@ -37,15 +39,15 @@ __device__ __forceinline__ int ingest_pixel(const IngestParams& p, int x, int y)
         if (p.feat_fmt == ESIM_AD_FEAT_BF16) {
 #pragma unroll
             for (int j = 0; j < 7; ++j)
-                f[j] = __uint_as_float((uint32_t)__ldg(p.feat_bf16 + j * N + i) << 16) * p.fscale[j];
+                f[j] = __uint_as_float((uint32_t)__ldg(p.feat_bf16 + j * NP + ii) << 16) * p.fscale[j];
         } else {
-            f[0] = __ldg(p.normal + i);
-            f[1] = __ldg(p.normal + N + i);
-            f[2] = __ldg(p.normal + 2 * N + i);
-            f[3] = __ldg(p.depth + i);
-            f[4] = __ldg(p.albedo + i);
-            f[5] = __ldg(p.albedo + N + i);
-            f[6] = __ldg(p.albedo + 2 * N + i);
+            f[0] = __ldg(p.normal + ii);
+            f[1] = __ldg(p.normal + NP + ii);
+            f[2] = __ldg(p.normal + 2 * NP + ii);
+            f[3] = __ldg(p.depth + ii);
+            f[4] = __ldg(p.albedo + ii);
+            f[5] = __ldg(p.albedo + NP + ii);
+            f[6] = __ldg(p.albedo + 2 * NP + ii);
         }
         if (p.mixed) {
             // FP16 log brightness and BF16 features; the test below sees the
@@ -76,7 +78,7 @@ __device__ __forceinline__ int ingest_pixel(const IngestParams& p, int x, int y)
                 float sigma = 0.0f;
                 if (p.variance) {
                     const float ye = Yeps > 0.0f ? Yeps : expf(yv);
-                    sigma = sqrtf(fmaxf(__ldg(p.variance + i), 0.0f)) / ye;
+                    sigma = sqrtf(fmaxf(__ldg(p.variance + ii), 0.0f)) / ye;
                 }
                 const float L = p.state[3 * N + i].w;
                 flag = fabsf(yv - L) >= fmaf(p.guard_kappa, sigma, p.C) ? 1 : 0;

@@ -110,6 +110,7 @@ struct IngestParams {
     float fscale[7];       // feature_scale
     float inv_fscale[7];
     int W, H, tiles_x;
+    long long pitch;       // input row pitch in elements (>= W)
     int slot;              // ring slot of this frame
     int test;              // 1: Proposition-1 test; 0: flag every pixel
     float log_eps, C;

@@ -1,4 +1,4 @@
-// Evaluation kernels (Section 4, quantitative comparison): the plain ESIM
+// Evaluation kernels (Section 3, quantitative comparison): the plain ESIM
 // simulator, and polarity-aware precision, recall, F-score and chamfer
 // distance between two event sets with an exact nearest-neighbour search.
 //

@@ -1,6 +1,6 @@
 // Second-order form: the dense weighted local regression of Eqs. 4-5 with the
 // Taylor expansion of Eq. 3 carried one order further (the non-linear
-// regression that Section 5 names as the extension).  Per frame t and centre c
+// regression that Section 4 names as the extension).  Per frame t and centre c
 // the design row of neighbour i is built from the scaled offset u = s d
 // (s_j = k / (h b_j), k = sqrt(log2(e) / 2), so w = 2^-|u|^2 is the product
 // Gaussian of Eq. 5):

@@ -45,10 +45,10 @@ def test_struct_layout_matches_header(lib):
 #include <stddef.h>
 #include "esim_ad.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(esim_ad_config), offsetof(esim_ad_config, contrast),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(esim_ad_config), offsetof(esim_ad_config, contrast),
          offsetof(esim_ad_config, event_capacity), offsetof(esim_ad_config, feature_scale),
          sizeof(esim_ad_frame), offsetof(esim_ad_frame, on_host), offsetof(esim_ad_frame, features),
-         sizeof(esim_ad_event), sizeof(esim_ad_stats));
+         offsetof(esim_ad_frame, pitch_elems), sizeof(esim_ad_event), sizeof(esim_ad_stats));
   return 0;
 }
 """
@@ -61,7 +61,7 @@ int main(void) {
     want = [ctypes.sizeof(lib.esim_ad_config), lib.esim_ad_config.contrast.offset,
             lib.esim_ad_config.event_capacity.offset, lib.esim_ad_config.feature_scale.offset,
             ctypes.sizeof(lib.esim_ad_frame), lib.esim_ad_frame.on_host.offset, lib.esim_ad_frame.features.offset,
-            lib.EVENT_DTYPE.itemsize, ctypes.sizeof(lib.esim_ad_stats)]
+            lib.esim_ad_frame.pitch_elems.offset, lib.EVENT_DTYPE.itemsize, ctypes.sizeof(lib.esim_ad_stats)]
     assert got == want
 
 
@@ -305,6 +305,48 @@ def test_host_frames_match_device_frames(lib):
         outs.append(np.concatenate(evs))
         sim.close()
     assert len(outs[0]) > 0 and np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.gpu
+def test_pitched_frames_match_dense_frames(lib):
+    """Input planes with a row pitch wider than the image (device and pinned
+    host frames) give the same alpha, flags and events as densely packed ones;
+    a pitch below the width is refused."""
+    import torch
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    W, H, P = 45, 30, 64
+    f0 = _frame(W, H, device="cpu")
+    f1 = {k: (v * 1.5 if k == "radiance" else v.flip(-1)).contiguous() for k, v in f0.items()}
+
+    def pitched(f):
+        out = {}
+        for k, v in f.items():
+            w = torch.full(v.shape[:-1] + (P,), -7.0)   # junk beyond the width is never read
+            w[..., :W] = v
+            out[k] = w.contiguous()
+        return out
+
+    results = []
+    for mode in ("dense", "pitch_dev", "pitch_host"):
+        sim = Simulator(SimConfig(width=W, height=H, radius=3, frames=2, contrast=0.1, mode=lib.ESIM_AD_ADAPTIVE))
+        for f in (f0, f1):
+            if mode == "dense":
+                sim.push({k: v.cuda() for k, v in f.items()})
+            elif mode == "pitch_dev":
+                sim.push({k: v.cuda() for k, v in pitched(f).items()}, pitch=P)
+            else:
+                sim.push({k: v.pin_memory() for k, v in pitched(f).items()}, pitch=P)
+        a, fl = sim.denoised()
+        results.append((a.cpu(), fl.cpu(), sim.events()))
+        sim.close()
+    for a, fl, ev in results[1:]:
+        assert torch.equal(a, results[0][0]) and torch.equal(fl, results[0][1])
+        assert np.array_equal(ev, results[0][2])
+    sim = Simulator(SimConfig(width=W, height=H, radius=3, frames=2, contrast=0.1))
+    with pytest.raises(lib.EsimError) as e:
+        sim.push({k: v.cuda() for k, v in f0.items()}, pitch=W - 1)
+    assert e.value.status == lib.ESIM_AD_EINVAL
+    sim.close()
 
 
 @pytest.mark.gpu

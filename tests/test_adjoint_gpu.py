@@ -1,7 +1,8 @@
 """Differentiation form on the GPU: forward alpha against the FP64 oracle, and
 the hand-written adjoint's gradients against (a) FP64 central finite
-differences of the oracle's loss and (b) autograd through the FP64 dense
-reference, on a 32x32 crop (radiance and the seven bandwidths)."""
+differences of the oracle's loss (h = 1e-4) and (b) autograd through the FP64
+dense reference (least squares on the augmented system, and the normal
+equations), on a 32x32 crop (radiance and the seven bandwidths)."""
 import numpy as np
 import pytest
 import torch
@@ -60,17 +61,24 @@ def test_forward_alpha_matches_oracle():
     assert err <= 1e-4, err
 
 
-def test_gradients_match_dense_autograd_reference():
+@pytest.mark.parametrize("solver", ["lstsq", "solve"])
+def test_gradients_match_dense_autograd_reference(solver):
+    """Against autograd through the FP64 dense regression: least squares on the
+    sqrt(w)-weighted augmented system, and the weighted normal equations."""
     rad, feat, clean = _crop(RECTS, 40, 40, 32, 32, 4)
     _, g_rad, g_b, _ = _gpu(rad, feat, clean, B)
     b64 = torch.tensor(B, dtype=torch.float64, requires_grad=True)
     r64 = rad.double().requires_grad_(True)
-    mse_loss(wlr_alpha(r64, feat.double(), b64, R, T, eps=EPS, ridge=RIDGE), clean.double(), EPS).backward()
+    mse_loss(wlr_alpha(r64, feat.double(), b64, R, T, eps=EPS, ridge=RIDGE, solver=solver),
+             clean.double(), EPS).backward()
     gb_ref = b64.grad.numpy()
     np.testing.assert_allclose(g_b.numpy(), gb_ref, rtol=2e-3, atol=2e-3 * np.abs(gb_ref).max())
     gr_ref = r64.grad.numpy()
     scale = np.abs(gr_ref).max()
-    np.testing.assert_allclose(g_rad.numpy(), gr_ref, rtol=1e-2, atol=1e-3 * scale)
+    err = np.abs(g_rad.numpy() - gr_ref)
+    print(f"radiance gradient vs FP64 {solver}: max abs {err.max():.3e} (scale {scale:.3e}), "
+          f"max rel where |g| > 1e-2 scale {np.max(err[np.abs(gr_ref) > 1e-2 * scale] / np.abs(gr_ref[np.abs(gr_ref) > 1e-2 * scale])):.3e}")
+    np.testing.assert_allclose(g_rad.numpy(), gr_ref, rtol=1e-4, atol=1e-5 * scale)
 
 
 def test_gradients_match_oracle_finite_differences():
@@ -88,13 +96,16 @@ def test_gradients_match_oracle_finite_differences():
         bm[j] -= hb
         fd = (loss(rad, bp) - loss(rad, bm)) / (2 * hb)
         assert g_b[j].item() == pytest.approx(fd, rel=2e-3, abs=1e-6)
-    he = 2.0 ** -13
-    for (t, c, yy, xx) in [(0, 0, 10, 12), (2, 1, 0, 31), (3, 2, 16, 16)]:
+    # radiance: h = 1e-4; the oracle reads float32, so the step actually taken
+    # is the float32 difference of the perturbed and original values (FP64 sums)
+    he = 1e-4
+    for (t, c, yy, xx) in [(0, 0, 10, 12), (2, 1, 0, 31), (3, 2, 16, 16), (1, 0, 31, 0)]:
         rp, rm = rad.clone(), rad.clone()
         rp[t, c, yy, xx] += he
         rm[t, c, yy, xx] -= he
-        fd = (loss(rp, B) - loss(rm, B)) / (2 * he)
-        assert g_rad[t, c, yy, xx].item() == pytest.approx(fd, rel=1e-2, abs=1e-7)
+        step = float(rp[t, c, yy, xx]) - float(rm[t, c, yy, xx])
+        fd = (loss(rp, B) - loss(rm, B)) / step
+        assert g_rad[t, c, yy, xx].item() == pytest.approx(fd, rel=2e-3, abs=1e-7)
 
 
 def test_backward_is_deterministic():

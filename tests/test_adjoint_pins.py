@@ -1,6 +1,7 @@
 """Pins of the FP64 autograd reference (tests/wlr_reference.py): its alpha equals
 the oracle's, and its gradients equal central finite differences of the
-oracle's loss (FP64, perturbations exact in the float32 inputs)."""
+oracle's loss (FP64 sums, h = 1e-4, the step taken as the float32 difference
+of the perturbed inputs the oracle reads)."""
 import numpy as np
 import pytest
 import torch
@@ -60,10 +61,32 @@ def test_reference_gradients_equal_oracle_finite_differences():
         bm[j] -= hb
         fd = (_oracle_loss(rad, feat, clean, bp) - _oracle_loss(rad, feat, clean, bm)) / (2 * hb)
         assert b.grad[j].item() == pytest.approx(fd, rel=1e-5, abs=1e-9)
-    he = 2.0 ** -13        # exact in the float32 inputs the oracle reads
+    # h = 1e-4 on the radiance; the oracle reads float32, so the step taken is
+    # the float32 difference of the two perturbed values
+    he = 1e-4
     for (t, c, yy, xx) in [(0, 0, 4, 5), (1, 1, 0, 0), (2, 2, 9, 11), (1, 0, 5, 3)]:
         rp, rm = rad.clone(), rad.clone()
-        rp[t, c, yy, xx] += he
-        rm[t, c, yy, xx] -= he
-        fd = (_oracle_loss(rp, feat, clean, B) - _oracle_loss(rm, feat, clean, B)) / (2 * he)
+        rp[t, c, yy, xx] = float(torch.tensor(float(rad[t, c, yy, xx]) + he, dtype=torch.float32))
+        rm[t, c, yy, xx] = float(torch.tensor(float(rad[t, c, yy, xx]) - he, dtype=torch.float32))
+        step = float(rp[t, c, yy, xx] - rm[t, c, yy, xx])
+        fd = (_oracle_loss(rp, feat, clean, B) - _oracle_loss(rm, feat, clean, B)) / step
         assert radv.grad[t, c, yy, xx].item() == pytest.approx(fd, rel=1e-4, abs=1e-9)
+
+
+def test_least_squares_reference_equals_normal_equations_and_oracle():
+    """The augmented least-squares form of the reference (torch.linalg.lstsq on
+    sqrt(w) Z stacked on the ridge rows) gives the oracle's alpha, and its
+    autograd gradients equal those through the normal equations."""
+    rad, feat, clean = _inputs()
+    grads = {}
+    for solver in ("solve", "lstsq"):
+        b = torch.tensor(B, dtype=torch.float64, requires_grad=True)
+        radv = rad.clone().requires_grad_(True)
+        a = wlr_alpha(radv, feat, b, R, T, eps=EPS, ridge=RIDGE, solver=solver)
+        if solver == "lstsq":
+            np.testing.assert_allclose(a.detach().numpy(), _oracle_alpha(rad, feat, B), atol=1e-10)
+        mse_loss(a, clean, EPS).backward()
+        grads[solver] = (b.grad.numpy(), radv.grad.numpy())
+    np.testing.assert_allclose(grads["lstsq"][0], grads["solve"][0], rtol=1e-8, atol=1e-12)
+    np.testing.assert_allclose(grads["lstsq"][1], grads["solve"][1], rtol=1e-8, atol=1e-12)
+

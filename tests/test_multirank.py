@@ -60,3 +60,58 @@ def test_single_rank_identity():
     import bench
     assert bench.max_over_ranks([1.5, 2.5], None, "cpu") == [1.5, 2.5]
     assert bench.whole_job_rate(1, 100, 10, 1000.0) == pytest.approx(1000.0)
+
+
+def _strip_main(rank, world, port, out, H, W, r):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2303_02608_gb300.strips import halo_exchange, strip_rows
+        g = torch.Generator().manual_seed(7)
+        frame = torch.rand(8, H, W, generator=g)            # the new frame's ring records, whole image
+        s = strip_rows(H, world, rank, r)
+        a, b = s["held"]
+        local = torch.full((8, b - a, W), float("nan"))
+        local[:, s["top"]:s["top"] + s["hi"] - s["lo"]] = frame[:, s["lo"]:s["hi"]]   # own rows only
+        halo_exchange(local, H, world, rank, r, dist)
+        out[rank] = {"equal": bool(torch.equal(local, frame[:, a:b])), "held": (a, b), "own": (s["lo"], s["hi"])}
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,H,r", [(2, 37, 7), (3, 40, 3), (4, 29, 7)])
+def test_strip_split_halo_exchange(world, H, r):
+    """The strip split's per-frame exchange on gloo ranks: after each rank
+    wrote only its owned rows of the new frame, the halo exchange leaves every
+    rank holding exactly the whole frame's rows [lo - r, hi + r) (clipped)."""
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_strip_main, args=(k, world, port, out, H, 11, r)) for k in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    assert all(res[k]["equal"] for k in range(world))
+    owns = [res[k]["own"] for k in range(world)]
+    assert owns[0][0] == 0 and owns[-1][1] == H and all(owns[k][1] == owns[k + 1][0] for k in range(world - 1))
+
+
+def test_strip_rows_and_event_merge():
+    import numpy as np
+    from paper_2303_02608_gb300 import EVENT_DTYPE
+    from paper_2303_02608_gb300.strips import merge_events, strip_rows
+    with pytest.raises(ValueError):
+        strip_rows(9, 2, 0, 7)          # strips thinner than the radius
+    s0, s1 = strip_rows(10, 2, 0, 3), strip_rows(10, 2, 1, 3)
+    assert (s0["lo"], s0["hi"], s0["top"], s0["bottom"]) == (0, 5, 0, 3)
+    assert (s1["lo"], s1["hi"], s1["top"], s1["bottom"]) == (5, 10, 3, 0)
+    e0 = np.array([(1, 2, 0, 1), (1, 3, 4, -1), (2, 0, 1, 1)], dtype=EVENT_DTYPE)
+    e1 = np.array([(1, 0, 0, 1), (2, 5, 2, -1)], dtype=EVENT_DTYPE)
+    m = merge_events([e0, e1], [0, 5])
+    key = m["frame"].astype(np.int64) * 1000 + m["y"].astype(np.int64) * 10 + m["x"]
+    assert np.all(np.diff(key) > 0) and len(m) == 5 and set(m["y"]) == {0, 4, 1, 5, 7}
+
