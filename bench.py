@@ -64,8 +64,13 @@ FLOP_PER_SOLVE_2 = 63472
 # capture, valid only while the regression's source text is unchanged (the
 # capture's workload and command are recorded under profiles/).
 # {sha256(regression sources)[:16]: bytes per frame at the bench workload}
-NCU_TRAFFIC = {}
-REGRESSION_SOURCES = ("wlr.cu", "wlr_math.cuh", "sparse_stage.cuh", "ptx.cuh", "internal.h")
+REGRESSION_SOURCES = ("wlr.cu", "wlr_math.cuh", "regress.cuh", "sparse_stage.cuh", "ptx.cuh", "internal.h")
+NCU_TRAFFIC = {
+    # frame 4 of the adaptive precision-form run on rects1080p, unscaled:
+    # wlr_adaptive_kernel 44,741,376 read + 67,840 written, wlr_solve_kernel
+    # 14,659,328 read + 41,216 written
+    "e0d5bfdbf35f3890": 44741376 + 67840 + 14659328 + 41216,
+}
 
 
 def _regression_source_hash() -> str:
@@ -397,12 +402,25 @@ def run_ours(args):
             "traffic": NCU_TRAFFIC.get(src_hash)}
     roof.update(roofline(prof_a))
 
-    # path-level HBM accounting (precision form, adaptive): minimum bytes per pixel-frame
-    bytes_pf = 16 + 16 + 32 + 1 + 4 + 4 + 4    # FP16+BF16 input, ring write, model read, flag, counts
+    # path-level HBM accounting (precision form, adaptive): minimum bytes per pixel-frame:
+    # FP16+BF16 input 16, ring write 16, model read 32, flag 1, event-pixel mask
+    # cleared and read 0.25; per flagged pixel alpha 4 + model write-back 64;
+    # 12 per event
+    bytes_pf = 16 + 16 + 32 + 1 + 0.25
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     path_bytes = bytes_pf * N * K + phi * N * K * (4 + 64) + ev_a * 12
     hbm_path = {"bytes_per_pixel_frame_min": bytes_pf, "achieved_gbs": round(path_bytes / (ms_a * 1e-3) / 1e9, 1),
                 "peak_gbs": hbm_gbs, "frac": round(path_bytes / (ms_a * 1e-3) / 1e9 / hbm_gbs, 4)}
+    # the ingest + test kernel alone: per pixel 16 B of inputs, 32 B of model,
+    # 16 B ring record, 1 B flag; per frame the mask words and chunk counts it
+    # clears; per flagged pixel 5 B of list entries
+    n_chunks = -(-N // 2048)
+    ing_bytes = N * (16 + 32 + 16 + 1) + n_chunks * (64 + 1) * 4 + phi * N * 5
+    ing_ms = prof_a["ms"]["ingest_test"] / K
+    ingest_roof = {"kernel": "ingest_test (staged form: TMA-fed persistent CTAs)", "bound": "hbm", "unit": "GB/s",
+                   "bytes_per_launch": round(ing_bytes), "launch_ms": round(ing_ms, 4),
+                   "achieved": round(ing_bytes / (ing_ms * 1e-3) / 1e9, 1), "peak": hbm_gbs,
+                   "frac": round(ing_bytes / (ing_ms * 1e-3) / 1e9 / hbm_gbs, 4)}
 
     def form(name):
         ms, prof, ev = runs[name]
@@ -428,6 +446,7 @@ def run_ours(args):
         "events_per_step": round(ev_a / K, 1),
         "kernel_ms_per_step": {k: round(v / K, 4) for k, v in prof_a["ms"].items()},
         "roofline": roof,
+        "ingest_roofline": ingest_roof,
         "hbm_path": hbm_path,
         "gpu_launches": int(prof_a["kernels"]),
         "clocks": clocks,

@@ -151,6 +151,10 @@ typedef struct esim_ad_stats {
     uint64_t events;         /* events emitted since init/reset                 */
     uint64_t pixels;         /* W*H                                             */
     uint64_t fp64_solves;    /* MIXED: regressions re-solved in FP64 (cond > 1e6) */
+    uint64_t staged_ingests; /* frames ingested by the staged (TMA, persistent) kernel:
+                                MIXED with FP16/BF16 frames whose planes are 16-byte
+                                aligned with a row pitch of a multiple of 8 elements;
+                                the others take the one-tile kernel (same results) */
 } esim_ad_stats;
 
 /*
@@ -170,6 +174,13 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
  * t >= 1), the weighted local regression of flagged pixels (every pixel at
  * t = 0 and in exhaustive mode), and event emission with the last-event update
  * (Eq. 1).  Frame 0 only initialises L_last and the models and emits no events.
+ * In the MIXED precision with LOGLUMA_F16 + FEAT_BF16 frames of at least
+ * 32 x 8 pixels whose planes start on 16-byte boundaries with a row pitch
+ * that is a multiple of 8 elements, the ingest reads the frame by TMA
+ * (persistent CTAs, each tile's loads issued a tile ahead); other frames take the one-tile
+ * ingest kernel, with identical results (esim_ad_stats.staged_ingests counts
+ * the former).  Pinned host frames land in such a layout when W*H is a
+ * multiple of 4 and W a multiple of 8.
  * Does not synchronise unless frame->on_host (then it waits for its own
  * host-to-device copies only).  EINVAL on NULL/missing planes (normal, albedo
  * and depth for FEAT_F32, features for FEAT_BF16), ESTATE after a sticky

@@ -73,7 +73,8 @@ class esim_ad_frame(ctypes.Structure):
 
 class esim_ad_stats(ctypes.Structure):
     _fields_ = [("frames", ctypes.c_uint64), ("regressions", ctypes.c_uint64),
-                ("events", ctypes.c_uint64), ("pixels", ctypes.c_uint64), ("fp64_solves", ctypes.c_uint64)]
+                ("events", ctypes.c_uint64), ("pixels", ctypes.c_uint64), ("fp64_solves", ctypes.c_uint64),
+                ("staged_ingests", ctypes.c_uint64)]
 
 
 class esim_ad_profile(ctypes.Structure):
@@ -278,7 +279,7 @@ def esim_ad_stats_get(ctx: int) -> dict:
     s = esim_ad_stats()
     _check(load_library().esim_ad_stats_get(ctypes.c_void_p(ctx), ctypes.byref(s)), "esim_ad_stats_get")
     return {"frames": s.frames, "regressions": s.regressions, "events": s.events, "pixels": s.pixels,
-            "fp64_solves": s.fp64_solves}
+            "fp64_solves": s.fp64_solves, "staged_ingests": s.staged_ingests}
 
 
 def esim_ad_profile_enable(ctx: int, on: bool = True) -> None:

@@ -858,6 +858,7 @@ esim_ad_status esim_ad_batch_stats(esim_ad_batch* b, esim_ad_stats* out, int32_t
     out->events = h.ev_cum;
     out->pixels = b->total_pix;
     out->fp64_solves = h.fp64_solves;
+    out->staged_ingests = 0;   // the batched ingest has one form
     if (lanes_out) *lanes_out = b->lanes;
     return ESIM_AD_OK;
 }

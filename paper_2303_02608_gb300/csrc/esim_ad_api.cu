@@ -83,6 +83,7 @@ struct esim_ad_ctx {
     float* gram = nullptr;       // Gram records of the frame's regressed pixels
     uint32_t* chunk_cnt = nullptr;
     unsigned long long* chunk_off = nullptr;
+    uint32_t* ev_mask = nullptr;  // one bit per pixel that emits this frame (64 words per chunk)
     esim_ad_event* events = nullptr;
     Ctrl* ctrl = nullptr;
     float* staging[2] = {nullptr, nullptr};   // host-frame landing buffers [11][H][W]
@@ -90,6 +91,12 @@ struct esim_ad_ctx {
     cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
     int staging_next = 0;
     CUtensorMap tmap;
+    // staged ingest (precision form, FP16/BF16 frames): the model-state map is
+    // fixed; the input maps are encoded per frame (its pointers and pitch)
+    CUtensorMap ingest_map_s;
+    bool ingest_staged = false;
+    int ingest_grid = 0;
+    uint64_t staged_ingests = 0;   // frames that took the staged ingest since init/reset
     // kernel timing (esim_ad_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_events;      // pool, pairs (start, stop)
@@ -142,8 +149,8 @@ esim_ad_status check_config(const esim_ad_config* c)
 void release(esim_ad_ctx* c)
 {
     void* ptrs[] = {c->ring, c->state, c->alpha, c->flag, c->nev, c->tile_queue, c->tile_nflag,
-                    c->tile_pix, c->flag_list, c->tile_base, c->gram, c->chunk_cnt, c->chunk_off, c->events, c->ctrl,
-                    c->staging[0], c->staging[1]};
+                    c->tile_pix, c->flag_list, c->tile_base, c->gram, c->chunk_cnt, c->chunk_off, c->ev_mask, c->events,
+                    c->ctrl, c->staging[0], c->staging[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 2; ++i) {
@@ -180,14 +187,54 @@ struct ProfScope {
     }
 };
 
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+
+// Tiled map without swizzle or interleave; out-of-range elements read as zero.
+bool encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, cuuint32_t rank, const void* ptr, const cuuint64_t* dims,
+                  const cuuint64_t* strides, const cuuint32_t* box)
+{
+    EncodeTiledFn fn = encode_fn();
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn && fn(m, dt, rank, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Input maps of one FP16/BF16 frame for the staged ingest: {W, H} log
+// brightness and {W, H, 7} features, boxes of one 32 x 8 tile.  False when the
+// frame does not meet TMA's rules (16-byte aligned planes, row pitch a
+// multiple of 16 bytes) or the encode fails: the frame takes the one-tile
+// kernel then.
+bool encode_frame_maps(const esim_ad_ctx* c, const esim_ad_frame* f, CUtensorMap* my, CUtensorMap* mf)
+{
+    const size_t pitch = f->pitch_elems ? (size_t)f->pitch_elems : (size_t)c->W;
+    if ((pitch * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(f->radiance) & 15u) ||
+        (reinterpret_cast<uintptr_t>(f->features) & 15u))
+        return false;
+    const cuuint64_t dy[2] = {(cuuint64_t)c->W, (cuuint64_t)c->H};
+    const cuuint64_t sy[1] = {(cuuint64_t)pitch * 2};
+    const cuuint32_t by[2] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY};
+    const cuuint64_t df[3] = {(cuuint64_t)c->W, (cuuint64_t)c->H, 7};
+    const cuuint64_t sf[2] = {(cuuint64_t)pitch * 2, (cuuint64_t)pitch * 2 * c->H};
+    const cuuint32_t bf[3] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 7};
+    return encode_tiled(my, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, f->radiance, dy, sy, by) &&
+           encode_tiled(mf, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, f->features, df, sf, bf);
+}
+
 esim_ad_status encode_ring_map(esim_ad_ctx* c)
 {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-        return ESIM_AD_ECUDA;
     // ring viewed as a 4-D tensor of 16-byte records: FP32 form {4 floats, W, H,
     // 2T half-planes}, box of both half-planes; mixed form {8 halves, W, H, T}
     const bool mixed = c->cfg.precision == ESIM_AD_MIXED;
@@ -196,13 +243,10 @@ esim_ad_status encode_ring_map(esim_ad_ctx* c)
     const cuuint64_t strides[3] = {16, (cuuint64_t)16 * c->W, (cuuint64_t)16 * c->W * c->H};
     const cuuint32_t box[4] = {mixed ? 8u : 4u, (cuuint32_t)(kTileX + 2 * c->cfg.radius),
                                (cuuint32_t)(kTileY + 2 * c->cfg.radius), mixed ? 1u : 2u};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = reinterpret_cast<EncodeTiledFn>(fn)(
-        &c->tmap, mixed ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->ring, dims,
-        strides, box, estr,
-        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? ESIM_AD_OK : ESIM_AD_ECUDA;
+    return encode_tiled(&c->tmap, mixed ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                        c->ring, dims, strides, box)
+               ? ESIM_AD_OK
+               : ESIM_AD_ECUDA;
 }
 
 esim_ad_status sync_and_check(esim_ad_ctx* c, Ctrl* host_ctrl)
@@ -285,6 +329,7 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         {(void**)&c->gram, (N + 4 * (size_t)c->n_tiles) * kGramRecordBytes},       // one per list entry or pixel
         {(void**)&c->chunk_cnt, (size_t)c->n_chunks * sizeof(uint32_t)},
         {(void**)&c->chunk_off, (size_t)c->n_chunks * sizeof(unsigned long long)},
+        {(void**)&c->ev_mask, (size_t)c->n_chunks * (kChunk / 32) * sizeof(uint32_t)},
         {(void**)&c->events, (size_t)cfg->event_capacity * sizeof(esim_ad_event)},
         {(void**)&c->ctrl, sizeof(Ctrl)},
     };
@@ -299,6 +344,7 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     if (cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess ||
         cudaMemset(c->alpha, 0, N * sizeof(float)) != cudaSuccess ||
         cudaMemset(c->flag, 0, N) != cudaSuccess || cudaMemset(c->nev, 0, N * sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(c->ev_mask, 0, (size_t)c->n_chunks * (kChunk / 32) * sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(c->state, 0, 4 * N * sizeof(float4)) != cudaSuccess) {
         release(c);
         delete c;
@@ -318,6 +364,21 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     c->wlr_grid = wlr_grid(c->smem_bytes, num_sms, c->mixed, false);
     c->adaptive_grid = wlr_grid(c->smem_adaptive, num_sms, c->mixed, true);
     c->solve_grid = wlr_solve_grid(num_sms);
+    // staged ingest for FP16/BF16 frames in the precision form (frames of at
+    // least one tile); ESIM_AD_INGEST_STAGED=0 keeps the one-tile kernel
+    if (c->mixed && cfg->radiance_fmt == ESIM_AD_LOGLUMA_F16 && cfg->feature_fmt == ESIM_AD_FEAT_BF16 &&
+        c->W >= kTileX && c->H >= kTileY) {
+        const char* e = getenv("ESIM_AD_INGEST_STAGED");
+        // the model state {float4 [4][H][W]} as {4W, H, 4} floats; box: planes 0-1 of one tile
+        const cuuint64_t dims[3] = {(cuuint64_t)4 * c->W, (cuuint64_t)c->H, 4};
+        const cuuint64_t strides[2] = {(cuuint64_t)16 * c->W, (cuuint64_t)16 * c->W * c->H};
+        const cuuint32_t box[3] = {(cuuint32_t)(4 * kTileX), (cuuint32_t)kTileY, 2};
+        if (!(e && *e == '0') &&
+            encode_tiled(&c->ingest_map_s, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->state, dims, strides, box)) {
+            c->ingest_staged = true;
+            c->ingest_grid = ingest_staged_grid(num_sms);
+        }
+    }
     // default: frames with up to 1/8 of the pixels flagged take the sparse kernel
     // (measured faster than tile staging at the 1-2% densities of edge-like
     // flag patterns); ESIM_AD_SPARSE_MAX overrides it (0: always the tile-staged
@@ -475,10 +536,21 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     ip.n_chunks = c->n_chunks;
     ip.flag_list = c->flag_list;
     ip.tile_base = c->tile_base;
+    ip.ev_mask = c->ev_mask;
+    ip.n_mask_words = c->n_chunks * (kChunk / 32);
+    ip.n_tiles = c->n_tiles;
+    ip.poll_limit = kPollLimit;
     ip.ctrl = c->ctrl;
     {
         ProfScope ps(c, 0);
-        if (launch_ingest(ip, c->n_tiles, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        CUtensorMap my, mf;
+        cudaError_t err;
+        if (c->ingest_staged && encode_frame_maps(c, f, &my, &mf)) {
+            err = launch_ingest_staged(my, mf, c->ingest_map_s, ip, c->ingest_grid, c->stream);
+            ++c->staged_ingests;
+        } else
+            err = launch_ingest(ip, c->n_tiles, c->stream);
+        if (err != cudaSuccess) return ESIM_AD_ECUDA;
         c->prof_kernels += 1;
     }
     if (slot >= 0 && cudaEventRecord(c->ev_consumed[slot], c->stream) != cudaSuccess)
@@ -526,6 +598,7 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     wp.gram = c->gram;
     wp.poll_limit = c->test_withhold ? 64u : kPollLimit;
     wp.withhold_copy = c->test_withhold;
+    wp.ev_mask = c->ev_mask;
     wp.ctrl = c->ctrl;
     {
         ProfScope ps(c, 1);
@@ -543,6 +616,7 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     if (c->t > 0) {
         EventParams ep;
         ep.nev = c->nev;
+        ep.ev_mask = c->ev_mask;
         ep.n_pix = (long long)c->N;
         ep.W = c->W;
         ep.n_chunks = c->n_chunks;
@@ -683,6 +757,7 @@ esim_ad_status esim_ad_reset(esim_ad_ctx* c)
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return ESIM_AD_ECUDA;
     c->t = 0;
+    c->staged_ingests = 0;
     c->sticky = ESIM_AD_OK;
     return ESIM_AD_OK;
 }
@@ -698,6 +773,7 @@ esim_ad_status esim_ad_stats_get(esim_ad_ctx* c, esim_ad_stats* out)
     out->events = h.ev_cum;
     out->pixels = c->N;
     out->fp64_solves = h.fp64_solves;
+    out->staged_ingests = c->staged_ingests;
     return ESIM_AD_OK;
 }
 

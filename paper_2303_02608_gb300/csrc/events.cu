@@ -1,8 +1,11 @@
 // Ordered event writer (Eq. 1 records at fixed frame times).
 //
 // The solve kernel leaves a signed per-pixel event count p*n in a map and,
-// in the simulator's own path, already sums |p*n| per 2048-pixel chunk, so
-// only the write launch runs; the stand-alone writer runs both launches below.
+// in the simulator's own path, already sums |p*n| per 2048-pixel chunk and
+// sets one bit per emitting pixel in a mask, so only the write launch runs and
+// it reads counts only under set bits (the frame's other counts are stale:
+// the ingest clears the mask, not the map); the stand-alone writer runs both
+// launches below on a dense map.
 // Either way the records come out in canonical order (row, column, repeat)
 // without sorting and without atomics on the output position, so the output
 // is deterministic:
@@ -60,7 +63,7 @@ __device__ __forceinline__ unsigned long long block_prefix_count(const uint32_t*
 // frame (ev_base) plus the counts of all earlier chunks, summed by the block
 // (no CTA waits on another and no serial scan); the last chunk's CTA records
 // the new total.
-__global__ void __launch_bounds__(kThreads, 8) event_write_kernel(EventParams p)
+__global__ void __launch_bounds__(kThreads) event_write_kernel(EventParams p)
 {
     __shared__ int s_warp[kThreads / 32];
     __shared__ unsigned long long s_red[kThreads / 32];
@@ -69,7 +72,13 @@ __global__ void __launch_bounds__(kThreads, 8) event_write_kernel(EventParams p)
     if (cnt == 0u && !last) return;   // no events in this chunk
     const long long p0 = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * kPer;
     int v[kPer];
-    if (p0 + kPer <= p.n_pix && ((reinterpret_cast<uintptr_t>(p.nev + p0) & 15u) == 0)) {
+    if (p.ev_mask) {
+        // the thread's 8 pixels are one byte of the chunk's 64 mask words
+        const uint32_t word = p.ev_mask[(size_t)blockIdx.x * (kChunk / 32) + (threadIdx.x >> 2)];
+        const uint32_t m = (word >> ((threadIdx.x & 3u) * 8u)) & 0xffu;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) v[k] = ((m >> k) & 1u) ? p.nev[p0 + k] : 0;
+    } else if (p0 + kPer <= p.n_pix && ((reinterpret_cast<uintptr_t>(p.nev + p0) & 15u) == 0)) {
         const int4 a = *reinterpret_cast<const int4*>(p.nev + p0);
         const int4 b = *reinterpret_cast<const int4*>(p.nev + p0 + 4);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "esim_ad.h"
@@ -43,7 +44,8 @@ struct Ctrl {
     uint32_t pad2;
     unsigned long long ev_base;     // ev_total before this frame's events (set by the solve kernel)
 };
-constexpr size_t kCtrlPerFrameBytes = 24;
+constexpr size_t kCtrlPerFrameBytes = 24;   // the per-frame counters above ev_total
+static_assert(offsetof(Ctrl, ev_total) == kCtrlPerFrameBytes, "per-frame part of Ctrl");
 // Largest |signed event count| of one pixel in one frame: a 2048-pixel chunk then
 // sums to at most 2^30 events, within the 32-bit chunk counts.
 constexpr int kMaxCountPerPixel = 1 << 19;
@@ -128,6 +130,12 @@ struct IngestParams {
     uint32_t* flag_list;   // frame-wide list of flagged pixel indices: each tile's run, in raster
                            // order, padded with 0xffffffff to a multiple of 4 entries
     uint32_t* tile_base;   // position of each queued tile's run in flag_list
+    // one bit per pixel, set by the solve where the pixel emits; cleared here
+    // (nullptr: the count map itself is cleared instead, for a dense writer)
+    uint32_t* ev_mask = nullptr;
+    int n_mask_words = 0;
+    int n_tiles = 0;             // staged ingest: tiles of the frame
+    uint32_t poll_limit = 0;     // staged ingest: bound of each mbarrier wait
     Ctrl* ctrl;
 };
 
@@ -164,11 +172,13 @@ struct WlrParams {
                                      // position in flag_list (adaptive frames)
     uint32_t poll_limit;             // bound on each mbarrier wait of the sparse kernel (polls)
     int withhold_copy;               // test only: the sparse kernel never issues its first box copy
+    uint32_t* ev_mask = nullptr;     // bit per pixel, set where the pixel emits (nullptr: none kept)
     Ctrl* ctrl;
 };
 
 struct EventParams {
     const int32_t* nev;
+    const uint32_t* ev_mask = nullptr;   // bit per pixel with events (nullptr: read every count)
     long long n_pix;
     int W;
     int n_chunks;
@@ -181,6 +191,15 @@ struct EventParams {
 };
 
 cudaError_t launch_ingest(const IngestParams& p, int n_tiles, cudaStream_t s);
+// Staged ingest of FP16 log brightness + BF16 feature frames (precision form):
+// persistent CTAs, each tile's inputs and model landed by TMA a tile ahead.
+// map_y: {W, H} u16, map_f: {W, H, 7} u16, map_s: the model state as {4W, H, 4}
+// f32; boxes {32, 8}, {32, 8, 7}, {128, 8, 2}.
+constexpr int kIngestStageBytes = 12288;
+constexpr int kIngestStages = 2;
+cudaError_t launch_ingest_staged(const CUtensorMap& map_y, const CUtensorMap& map_f, const CUtensorMap& map_s,
+                                 const IngestParams& p, int grid, cudaStream_t s);
+int ingest_staged_grid(int sms);
 
 // Autotuning cache (tune_cache.cu): value for key, or 0 if none.
 int tune_cache_lookup(const char* key);

@@ -723,6 +723,7 @@ __device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const f
         L = fmaf(pol * n, p.C, L);
         p.nev[i] = (int32_t)(pol * n);
         atomicAdd(&p.chunk_cnt[i / kChunk], (uint32_t)n);
+        if (p.ev_mask) atomicOr(&p.ev_mask[i >> 5], 1u << (i & 31u));
     }
     const int slot = p.t % p.T;
     float x[7];

@@ -171,3 +171,65 @@ def test_storage_rounding_deviation_reported():
     print(f"storage-rounding deviation of alpha on rows {rows}: max {dev.max():.3e} "
           f"p99 {np.percentile(dev, 99):.3e} mean {dev.mean():.3e}")
     assert dev.mean() < 1e-2 and np.isfinite(dev).all()
+
+
+@pytest.mark.parametrize("mode", [ADAPTIVE, EXHAUSTIVE])
+def test_staged_ingest_matches_one_tile_ingest(mode, monkeypatch):
+    """FP16/BF16 frames take the staged ingest (TMA-fed persistent CTAs) when
+    their planes are 16-byte aligned with a row pitch of a multiple of 8
+    elements, and the one-tile kernel otherwise.  Both give bit-identical
+    alpha, flags and events: packed device frames (staged), the same frames
+    with the staged kernel switched off, pitched frames (staged), planes
+    starting 2 bytes past a 16-byte boundary (one-tile) and pinned host frames
+    (staged, from the landing buffer).  200 x 100 leaves ragged tiles at the
+    right and bottom edges."""
+    import paper_2303_02608_gb300 as m
+    cfg = SceneConfig(kind="rects", width=200, height=100, frames=6, spp=1, seed=11, rgb=True, n_rects=12,
+                      bg_depth=10.0)
+    W, H, P = cfg.width, cfg.height, 216
+    frames = [storage_frame(f)["gpu"] for f in Scene(cfg).sequence(6)]
+
+    def packed(f):
+        return {k: v.cuda() for k, v in f.items()}, 0
+
+    def pitched(f):
+        out = {}
+        for k, v in f.items():
+            w = torch.zeros(v.shape[:-1] + (P,), dtype=v.dtype)
+            w[..., :W] = v
+            out[k] = w.cuda()
+        return out, P
+
+    def misaligned(f):
+        out = {}
+        for k, v in f.items():
+            flat = torch.zeros(v.numel() + 8, dtype=v.dtype, device="cuda")
+            flat[1:1 + v.numel()] = v.flatten().cuda()
+            out[k] = flat[1:1 + v.numel()].view(v.shape)
+            assert out[k].data_ptr() % 16 != 0
+        return out, 0
+
+    def host(f):
+        return {k: v.pin_memory() for k, v in f.items()}, 0
+
+    variants = [("staged", "1", packed, 6), ("one_tile", "0", packed, 0), ("pitched", "1", pitched, 6),
+                ("misaligned", "1", misaligned, 0), ("host", "1", host, 6)]
+    results = {}
+    for name, env, prep, staged in variants:
+        monkeypatch.setenv("ESIM_AD_INGEST_STAGED", env)
+        sim = _sim(W, H, 3, 3, 0.1, mode, m.ESIM_AD_MIXED, "bf16")
+        evs = []
+        for f in frames:
+            fr, pitch = prep(f)
+            sim.push(fr, pitch=pitch)
+            evs.append(sim.events())
+        a, fl = sim.denoised()
+        st = sim.stats()
+        sim.close()
+        assert st["staged_ingests"] == staged, (name, st)
+        results[name] = (a.cpu(), fl.cpu(), np.concatenate(evs))
+    a0, f0, e0 = results["staged"]
+    assert e0.size > 0
+    for name, (a, fl, ev) in results.items():
+        assert torch.equal(a, a0) and torch.equal(fl, f0), name
+        assert np.array_equal(ev, e0), name
