@@ -184,7 +184,12 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
  * Does not synchronise unless frame->on_host (then it waits for its own
  * host-to-device copies only).  EINVAL on NULL/missing planes (normal, albedo
  * and depth for FEAT_F32, features for FEAT_BF16), ESTATE after a sticky
- * error, ECUDA if a launch fails.
+ * error, ECUDA if a launch fails.  The frame's ordered event writer runs on
+ * an internal stream that the context's stream joins before the next frame's
+ * solve and in every synchronising call (esim_ad_events, esim_ad_denoised,
+ * esim_ad_stats_get, ...), so events are only ever read complete; work the
+ * caller enqueues on the context's stream after this call is ordered after
+ * the frame's regression, not after its event writer.
  */
 esim_ad_status esim_ad_push_frame(esim_ad_ctx* ctx, const esim_ad_frame* frame);
 
@@ -225,7 +230,11 @@ esim_ad_status esim_ad_set_state(esim_ad_ctx* ctx, const float* l_last, const fl
 /*
  * Kernel timing for tracing and roofline accounting (no paper counterpart:
  * instrumentation).  While enabled, every kernel launch of esim_ad_push_frame
- * is bracketed by CUDA events on the context's stream.  Classes: 0 = ingest +
+ * is bracketed by CUDA events on the context's stream, and each frame's event
+ * writer runs there after the frame's solve, so that every kernel is timed
+ * alone.  (Otherwise the writer runs on an internal stream beside the next
+ * frame's ingest and regression pass 1; every synchronising call of this API
+ * waits for it.)  Classes: 0 = ingest +
  * Proposition-1 test, 1 = weighted local regression + emission, 2 = ordered
  * event writer (class 1 covers both regression launches of an adaptive
  * frame).  `kernels` counts every kernel launch the library issued while

@@ -56,6 +56,12 @@ struct esim_ad_ctx {
     esim_ad_config cfg;
     cudaStream_t stream = nullptr;
     cudaStream_t copy_stream = nullptr;
+    // The event writer of a frame runs on its own stream, beside the next
+    // frame's ingest and pass 1; the context's stream waits for it (ev_written)
+    // before the next solve and before anything that reads what it writes.
+    cudaStream_t writer_stream = nullptr;
+    cudaEvent_t ev_solved = nullptr, ev_written = nullptr;
+    bool writer_pending = false;
     int device = 0;
     int W = 0, H = 0;
     size_t N = 0;
@@ -83,7 +89,7 @@ struct esim_ad_ctx {
     float* gram = nullptr;       // Gram records of the frame's regressed pixels
     uint32_t* chunk_cnt = nullptr;
     unsigned long long* chunk_off = nullptr;
-    uint32_t* ev_mask = nullptr;  // one bit per pixel that emits this frame (64 words per chunk)
+    uint32_t* ev_mask = nullptr;  // one bit per pixel that emits (64 words per chunk), two buffers by frame parity
     esim_ad_event* events = nullptr;
     Ctrl* ctrl = nullptr;
     float* staging[2] = {nullptr, nullptr};   // host-frame landing buffers [11][H][W]
@@ -158,6 +164,9 @@ void release(esim_ad_ctx* c)
         if (c->ev_consumed[i]) cudaEventDestroy(c->ev_consumed[i]);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->writer_stream) cudaStreamDestroy(c->writer_stream);
+    if (c->ev_solved) cudaEventDestroy(c->ev_solved);
+    if (c->ev_written) cudaEventDestroy(c->ev_written);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     c->prof_events.clear();
 }
@@ -165,8 +174,9 @@ void release(esim_ad_ctx* c)
 // Bracket one launch with a pair of pooled events when profiling is on.
 struct ProfScope {
     esim_ad_ctx* c;
+    cudaStream_t s;
     size_t pair = (size_t)-1;
-    ProfScope(esim_ad_ctx* ctx, int cls) : c(ctx)
+    ProfScope(esim_ad_ctx* ctx, int cls, cudaStream_t stream) : c(ctx), s(stream)
     {
         if (!c->prof_on) return;
         if (2 * c->prof_used + 2 > c->prof_events.size()) {
@@ -179,13 +189,26 @@ struct ProfScope {
         pair = c->prof_used++;
         if (c->prof_class.size() < c->prof_used) c->prof_class.resize(c->prof_used);
         c->prof_class[pair] = cls;
-        cudaEventRecord(c->prof_events[2 * pair], c->stream);
+        cudaEventRecord(c->prof_events[2 * pair], s);
     }
     ~ProfScope()
     {
-        if (pair != (size_t)-1) cudaEventRecord(c->prof_events[2 * pair + 1], c->stream);
+        if (pair != (size_t)-1) cudaEventRecord(c->prof_events[2 * pair + 1], s);
     }
 };
+
+// Order the context's stream after the latest frame's event writer.
+cudaError_t join_writer(esim_ad_ctx* c)
+{
+    return c->writer_pending ? cudaStreamWaitEvent(c->stream, c->ev_written, 0) : cudaSuccess;
+}
+
+// Synchronise the context's stream, the event writer included.
+cudaError_t sync_stream(esim_ad_ctx* c)
+{
+    const cudaError_t e = join_writer(c);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
+}
 
 EncodeTiledFn encode_fn()
 {
@@ -253,7 +276,8 @@ esim_ad_status sync_and_check(esim_ad_ctx* c, Ctrl* host_ctrl)
 {
     Ctrl tmp;
     Ctrl* h = host_ctrl ? host_ctrl : &tmp;
-    if (cudaMemcpyAsync(h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    if (join_writer(c) != cudaSuccess ||
+        cudaMemcpyAsync(h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return ESIM_AD_ECUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
     if (h->status & kStatusTimeout) c->sticky = ESIM_AD_ETIMEOUT;
@@ -327,9 +351,9 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         {(void**)&c->flag_list, (N + 4 * (size_t)c->n_tiles) * sizeof(uint32_t)},   // + tile padding
         {(void**)&c->tile_base, (size_t)c->n_tiles * sizeof(uint32_t)},
         {(void**)&c->gram, (N + 4 * (size_t)c->n_tiles) * kGramRecordBytes},       // one per list entry or pixel
-        {(void**)&c->chunk_cnt, (size_t)c->n_chunks * sizeof(uint32_t)},
+        {(void**)&c->chunk_cnt, 2 * (size_t)c->n_chunks * sizeof(uint32_t)},
         {(void**)&c->chunk_off, (size_t)c->n_chunks * sizeof(unsigned long long)},
-        {(void**)&c->ev_mask, (size_t)c->n_chunks * (kChunk / 32) * sizeof(uint32_t)},
+        {(void**)&c->ev_mask, 2 * (size_t)c->n_chunks * (kChunk / 32) * sizeof(uint32_t)},
         {(void**)&c->events, (size_t)cfg->event_capacity * sizeof(esim_ad_event)},
         {(void**)&c->ctrl, sizeof(Ctrl)},
     };
@@ -344,7 +368,10 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
     if (cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess ||
         cudaMemset(c->alpha, 0, N * sizeof(float)) != cudaSuccess ||
         cudaMemset(c->flag, 0, N) != cudaSuccess || cudaMemset(c->nev, 0, N * sizeof(int32_t)) != cudaSuccess ||
-        cudaMemset(c->ev_mask, 0, (size_t)c->n_chunks * (kChunk / 32) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c->ev_mask, 0, 2 * (size_t)c->n_chunks * (kChunk / 32) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->writer_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_solved, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_written, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemset(c->state, 0, 4 * N * sizeof(float4)) != cudaSuccess) {
         release(c);
         delete c;
@@ -499,6 +526,9 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     }
     const int t = (int)(c->t % 0x7fffffff);
     const bool adaptive_test = c->cfg.mode == ESIM_AD_ADAPTIVE && c->t > 0;
+    // chunk counts and the event-pixel mask alternate by frame parity, so the
+    // previous frame's writer reads its own while this frame's ingest clears these
+    const int par = (int)(c->t & 1);
     if (cudaMemsetAsync(c->ctrl, 0, kCtrlPerFrameBytes, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
 
     IngestParams ip;
@@ -532,17 +562,17 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     ip.tile_queue = c->tile_queue;
     ip.tile_nflag = c->tile_nflag;
     ip.tile_pix = c->tile_pix;
-    ip.chunk_cnt = c->chunk_cnt;
+    ip.chunk_cnt = c->chunk_cnt + par * c->n_chunks;
     ip.n_chunks = c->n_chunks;
     ip.flag_list = c->flag_list;
     ip.tile_base = c->tile_base;
-    ip.ev_mask = c->ev_mask;
+    ip.ev_mask = c->ev_mask + (size_t)par * c->n_chunks * (kChunk / 32);
     ip.n_mask_words = c->n_chunks * (kChunk / 32);
     ip.n_tiles = c->n_tiles;
     ip.poll_limit = kPollLimit;
     ip.ctrl = c->ctrl;
     {
-        ProfScope ps(c, 0);
+        ProfScope ps(c, 0, c->stream);
         CUtensorMap my, mf;
         cudaError_t err;
         if (c->ingest_staged && encode_frame_maps(c, f, &my, &mf)) {
@@ -587,7 +617,7 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     wp.tile_queue = c->tile_queue;
     wp.tile_nflag = c->tile_nflag;
     wp.tile_pix = c->tile_pix;
-    wp.chunk_cnt = c->chunk_cnt;
+    wp.chunk_cnt = c->chunk_cnt + par * c->n_chunks;
     wp.chunk_off = c->chunk_off;
     wp.n_chunks = c->n_chunks;
     wp.emit_events = c->t > 0 ? 1 : 0;
@@ -598,36 +628,53 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     wp.gram = c->gram;
     wp.poll_limit = c->test_withhold ? 64u : kPollLimit;
     wp.withhold_copy = c->test_withhold;
-    wp.ev_mask = c->ev_mask;
+    wp.ev_mask = c->ev_mask + (size_t)par * c->n_chunks * (kChunk / 32);
     wp.ctrl = c->ctrl;
     {
-        ProfScope ps(c, 1);
+        ProfScope ps(c, 1, c->stream);
         // pass 1: dense frames tile-staged over every tile; adaptive frames in one
         // launch that picks window boxes or the tile queue from the flagged total
         const int grid = wp.dense ? (c->n_tiles < c->wlr_grid ? c->n_tiles : c->wlr_grid) : c->adaptive_grid;
         if (launch_wlr(c->tmap, wp, c->mixed, grid, wp.dense ? c->smem_bytes : c->smem_adaptive, c->stream) !=
             cudaSuccess)
             return ESIM_AD_ECUDA;
-        // pass 2: solve every accumulated system, emit, and scan the event counts
-        if (launch_wlr_solve(wp, c->mixed, c->solve_grid, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        // pass 2: solve every accumulated system and emit; it follows the
+        // previous frame's event writer (it sets ev_base from that frame's total)
+        if (join_writer(c) != cudaSuccess ||
+            launch_wlr_solve(wp, c->mixed, c->solve_grid, c->stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
         c->prof_kernels += 2;
     }
 
     if (c->t > 0) {
         EventParams ep;
         ep.nev = c->nev;
-        ep.ev_mask = c->ev_mask;
         ep.n_pix = (long long)c->N;
         ep.W = c->W;
         ep.n_chunks = c->n_chunks;
         ep.frame = (uint32_t)c->t;
-        ep.chunk_cnt = c->chunk_cnt;
+        ep.chunk_cnt = c->chunk_cnt + par * c->n_chunks;
+        ep.ev_mask = c->ev_mask + (size_t)par * c->n_chunks * (kChunk / 32);
         ep.chunk_off = c->chunk_off;
         ep.events = c->events;
         ep.capacity = c->cfg.event_capacity;
         ep.ctrl = c->ctrl;
-        ProfScope ps(c, 2);
-        if (launch_event_write(ep, c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+        // on the writer stream, so that the next frame's ingest and pass 1 run
+        // beside it; while profiling, on the context's stream, so that every
+        // kernel is timed alone
+        const bool overlap = !c->prof_on;
+        if (overlap && (cudaEventRecord(c->ev_solved, c->stream) != cudaSuccess ||
+                        cudaStreamWaitEvent(c->writer_stream, c->ev_solved, 0) != cudaSuccess))
+            return ESIM_AD_ECUDA;
+        {
+            const cudaStream_t ws = overlap ? c->writer_stream : c->stream;
+            ProfScope ps(c, 2, ws);
+            if (launch_event_write(ep, ws) != cudaSuccess) return ESIM_AD_ECUDA;
+        }
+        if (overlap) {
+            if (cudaEventRecord(c->ev_written, c->writer_stream) != cudaSuccess) return ESIM_AD_ECUDA;
+            c->writer_pending = true;
+        }
         c->prof_kernels += 1;
     }
     if (slot >= 0) {
@@ -719,7 +766,7 @@ esim_ad_status esim_ad_set_state(esim_ad_ctx* c, const float* l_last, const floa
     float4* h = (float4*)malloc(4 * N * sizeof(float4));
     if (!h) return ESIM_AD_ENOMEM;
     if (cudaMemcpyAsync(h, c->state, 4 * N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        sync_stream(c) != cudaSuccess) {
         free(h);
         return ESIM_AD_ECUDA;
     }
@@ -742,7 +789,7 @@ esim_ad_status esim_ad_set_state(esim_ad_ctx* c, const float* l_last, const floa
     }
     esim_ad_status st = ESIM_AD_OK;
     if (cudaMemcpyAsync(c->state, h, 4 * N * sizeof(float4), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        sync_stream(c) != cudaSuccess)
         st = ESIM_AD_ECUDA;
     free(h);
     return st;
@@ -752,9 +799,9 @@ esim_ad_status esim_ad_reset(esim_ad_ctx* c)
 {
     if (!c) return ESIM_AD_EINVAL;
     DeviceGuard guard(c->device);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    if (sync_stream(c) != cudaSuccess) return ESIM_AD_ECUDA;
     if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        sync_stream(c) != cudaSuccess)
         return ESIM_AD_ECUDA;
     c->t = 0;
     c->staged_ingests = 0;
@@ -781,7 +828,7 @@ esim_ad_status esim_ad_profile_enable(esim_ad_ctx* c, int on)
 {
     if (!c) return ESIM_AD_EINVAL;
     DeviceGuard guard(c->device);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
+    if (sync_stream(c) != cudaSuccess) return ESIM_AD_ECUDA;
     c->prof_on = on != 0;
     c->prof_used = 0;
     c->prof_kernels = 0;
@@ -813,7 +860,8 @@ void esim_ad_destroy(esim_ad_ctx* c)
     if (!c) return;
     {
         DeviceGuard guard(c->device);
-        cudaStreamSynchronize(c->stream);
+        sync_stream(c);
+        if (c->writer_stream) cudaStreamSynchronize(c->writer_stream);
         if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
         release(c);
     }

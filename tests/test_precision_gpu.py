@@ -233,3 +233,42 @@ def test_staged_ingest_matches_one_tile_ingest(mode, monkeypatch):
     for name, (a, fl, ev) in results.items():
         assert torch.equal(a, a0) and torch.equal(fl, f0), name
         assert np.array_equal(ev, e0), name
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_overlapped_event_writers_match_per_frame_drains(precision):
+    """A frame's event writer runs on its own stream beside the next frame's
+    ingest and pass 1.  Pushing 12 frames with no drain in between (so every
+    writer overlaps the next frame) gives the same events, alpha and flags as
+    draining after every frame (each drain waits for the writer)."""
+    import paper_2303_02608_gb300 as m
+    cfg = SceneConfig(kind="rects", width=200, height=100, frames=12, spp=1, seed=5, rgb=True, n_rects=14,
+                      bg_depth=10.0)
+    W, H = cfg.width, cfg.height
+    scene_frames = Scene(cfg).sequence(12)
+    if precision == "mixed":
+        frames = [{k: v.cuda() for k, v in storage_frame(f)["gpu"].items()} for f in scene_frames]
+        mk = lambda: _sim(W, H, 3, 3, 0.1, ADAPTIVE, m.ESIM_AD_MIXED, "bf16")
+    else:
+        from paper_2303_02608_gb300 import SimConfig, Simulator
+        frames = [{k: v.cuda() for k, v in f.items() if k in ("radiance", "normal", "albedo", "depth")}
+                  for f in scene_frames]
+        mk = lambda: Simulator(SimConfig(width=W, height=H, radius=3, frames=3, contrast=0.1, mode=ADAPTIVE,
+                                         rgb=True))
+    out = []
+    for drain_each in (True, False):
+        sim = mk()
+        evs = []
+        for f in frames:
+            sim.push(f)
+            if drain_each:
+                evs.append(sim.events())
+        if not drain_each:
+            evs.append(sim.events())
+        a, fl = sim.denoised()
+        sim.close()
+        out.append((np.concatenate(evs), a.cpu(), fl.cpu()))
+    (e0, a0, f0), (e1, a1, f1) = out
+    assert e0.size > 100
+    assert np.array_equal(e0, e1)
+    assert torch.equal(a0, a1) and torch.equal(f0, f1)
