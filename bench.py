@@ -197,6 +197,31 @@ def _gen_frames(scene, n, device):
     return frames
 
 
+def _regression_min_bytes(sim, r, T):
+    """Fused-minimum DRAM bytes of one adaptive frame's regression (the last
+    frame pushed, precision form): every 16-byte ring record under the union
+    of the flagged pixels' windows read once for each of the T frames, and per
+    flagged pixel alpha written (4 B) and L_last read (16 B).  The Gram records
+    between the two passes are not counted (a fused kernel keeps them on
+    chip); the model write-back of emitting pixels is left out too."""
+    import torch
+    _, flags = sim.denoised()
+    f = flags.float()[None, None]
+    union = torch.nn.functional.max_pool2d(f, 2 * r + 1, stride=1, padding=r)
+    n_union = int(union.sum().item())
+    n_flag = int(f.sum().item())
+    return {"bytes": n_union * T * 16 + n_flag * (4 + 16), "window_union_pixels": n_union,
+            "flagged_pixels": n_flag}
+
+
+def _frames_timed(W, K, F):
+    """The frame indices a timed run of K steps after W warm-up steps covers
+    (the index wraps to frame 0, with a reset, after F frames)."""
+    if W + K <= F:
+        return f"{W}-{W + K - 1}"
+    return f"{W % F}-{F - 1}, then 0-{(W + K - 1) % F} with a reset ({K} steps)"
+
+
 def _timed_run(sim, frames, W, K, stream, drain_every=8, sink=None, profile=True):
     """W untimed warm-up steps, then exactly K timed steps (frame index wraps
     with a reset to frame 0).  Events are drained into the device buffer
@@ -361,6 +386,8 @@ def run_ours(args):
             sim.reset()
             _, prof, _ = _timed_run(sim, fr, args.warmup, args.steps, stream, sink=sink, profile=True)
             prof["fp64_solves"] = sim.stats()["fp64_solves"]
+            if name == "mixed_adaptive":
+                prof["min_bytes_last"] = _regression_min_bytes(sim, wl["r"], wl["T"])
             sim.close()
             runs[name] = (ms, prof, ev)
     clocks = clk.summary()
@@ -399,7 +426,8 @@ def run_ours(args):
             "bound": "alu", "unit": "TFLOP/s", "peak": round(fp32_peak, 2),
             "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
                            f"(max SM clock, {peak_src} peaks file)",
-            "traffic": NCU_TRAFFIC.get(src_hash)}
+            "traffic": NCU_TRAFFIC.get(src_hash),
+            "min_bytes_last_frame": prof_a["min_bytes_last"]}
     roof.update(roofline(prof_a))
 
     # path-level HBM accounting (precision form, adaptive): minimum bytes per pixel-frame:
@@ -438,7 +466,8 @@ def run_ours(args):
                            "refined FP32 Cholesky, FP64 re-solve above cond 1e6)",
                    "width": Wd, "height": H, "radius": wl["r"], "T": wl["T"], "C": wl["C"],
                    "spp": scfg.spp, "sequence_frames": F,
-                   "l2": "inputs larger than L2: each step reads a distinct frame; 240-frame sequence"},
+                   "frames_timed": _frames_timed(args.warmup, K, n_gen),
+                   "l2": "inputs larger than L2: each step reads a distinct frame of the sequence"},
         "exhaustive": form("mixed_exhaustive"),
         "fp32_form": {"adaptive": form("fp32_adaptive"), "exhaustive": form("fp32_exhaustive")},
         "speedup_adaptive_vs_exhaustive": round(value / rate("mixed_exhaustive"), 3),
@@ -456,7 +485,7 @@ def run_ours(args):
     if rank == 0 and not args.no_paper_density:
         line["paper_density"] = _paper_density(args, dev, stream, fp32_peak, sink)
     if rank == 0 and not args.no_diff:
-        line["differentiation_form"] = _differentiation(dev)
+        line["differentiation_form"] = _differentiation(dev, fp32_peak)
     if rank == 0 and not args.no_second_order:
         try:   # a side measurement: its failure is reported in the line, not fatal to it
             line["second_order_form"] = _second_order(dev, fp32_peak)
@@ -799,7 +828,17 @@ def _quality(dev, C_values=(0.25, 0.5, 0.75, 1.0), taus=(5e-4, 1e-3, 2e-3, 5e-3,
     return out
 
 
-def _differentiation(dev, reps=5):
+# Differentiation form, flop per (centre, window neighbour) pair: the forward
+# accumulation is the simulator's (162); bwd_center_kernel re-forms the
+# regressors (14), the squared distance (17), exp2 (1), the fit and v'^T u
+# (18 each), dalpha/dw (3), its weight (2) and the seven bandwidth terms (21) =
+# 94; bwd_source_kernel the regressors, distance, exp2, v'^T u and one FMA =
+# 52.  Per centre the forward solve for theta' and v' (ridge, equilibration,
+# Cholesky, two substitution pairs): about 900.
+FLOP_FWD_PAIR, FLOP_BWD_CENTER_PAIR, FLOP_BWD_SOURCE_PAIR, FLOP_FWD_SOLVE = 162, 94, 52, 900
+
+
+def _differentiation(dev, fp32_peak, reps=5):
     """The differentiation workload (512x512, 16 frames, 2 spp, 7x7x3 window):
     dense regression forward + hand-written adjoint for dL/dE and dL/db."""
     import torch
@@ -832,10 +871,22 @@ def _differentiation(dev, reps=5):
             bwd.append(e_b0.elapsed_time(ev[2]))
     n_pf = rad.shape[0] * rad.shape[2] * rad.shape[3]
     f_ms, b_ms = statistics.median(fwd), statistics.median(bwd)
+    pairs = _window_pairs(rad.shape[3], rad.shape[2], rad.shape[0], 3, 3)
+    flops_f = pairs * FLOP_FWD_PAIR + n_pf * FLOP_FWD_SOLVE
+    flops_b = pairs * (FLOP_BWD_CENTER_PAIR + FLOP_BWD_SOURCE_PAIR)
+
+    def roof(flops, ms):
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"flops": flops, "achieved": round(ach, 3), "frac": round(ach / fp32_peak, 4)}
+
     return {"workload": "rects512: 512x512 RGB, 16 frames, 2 spp, 7x7x3 window, 7 bandwidths",
             "forward_ms": round(f_ms, 3), "backward_ms": round(b_ms, 3),
             "value": round(n_pf / ((f_ms + b_ms) * 1e-3), 1), "unit": "pixel-frames/s (forward + backward)",
-            "grad_bandwidth_finite": bool(torch.isfinite(b.grad).all())}
+            "grad_bandwidth_finite": bool(torch.isfinite(b.grad).all()),
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": round(fp32_peak, 2), "neighbour_pairs": pairs,
+                         "flop_per_pair": {"forward": FLOP_FWD_PAIR, "bwd_center": FLOP_BWD_CENTER_PAIR,
+                                           "bwd_source": FLOP_BWD_SOURCE_PAIR},
+                         "forward": roof(flops_f, f_ms), "backward": roof(flops_b, b_ms)}}
 
 
 def _window_pairs(W, H, F, r, T):
