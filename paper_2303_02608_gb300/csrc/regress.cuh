@@ -27,6 +27,39 @@ struct SingleSeq {
 
 constexpr int kSolveThreads = 128;
 
+// Sum each pixel's partial sums over its g lanes through the warp's (idle)
+// box buffer and store the Gram records.  Pixel q of the pass owns lanes
+// q g .. q g + g - 1 and record entry0 + q.  Every lane writes its 66 sums as
+// one row (pitch 67 floats, so the 32 rows of a column sit in distinct
+// banks); the lanes then split the records' slots, consecutive lanes taking
+// consecutive slots, and each adds its column over the pixel's rows in lane
+// order.  Fewer instructions than a shuffle tree (3-5 levels of 65 shuffles
+// and adds), and the stores come out coalesced.
+constexpr int kRowPitch = 67;
+static_assert(32 * kRowPitch * 4 <= kBoxBytes, "partial sums fit a box buffer");
+
+__device__ __forceinline__ void store_records(const AccP& a, float* rows, float* __restrict__ gram, uint32_t entry0,
+                                              int npix, int g)
+{
+    const int lane = threadIdx.x & 31;
+    float v[kGramStride];
+    accp_values(a, v);
+    __syncwarp();   // every lane is past its reads of the box
+#pragma unroll
+    for (int s = 0; s < kGramFloats; ++s) rows[lane * kRowPitch + s] = v[s];
+    __syncwarp();
+    for (int k = lane; k < npix * kGramStride; k += 32) {
+        const int q = k / kGramStride, s = k - q * kGramStride;
+        float sum = 0.0f;
+        if (s < kGramFloats) {
+            const float* col = rows + q * g * kRowPitch + s;
+            for (int i = 0; i < g; ++i) sum += col[i * kRowPitch];
+        }
+        gram[(size_t)(entry0 + (uint32_t)q) * kGramStride + s] = sum;
+    }
+    __syncwarp();   // the buffer is free for the next item's copies
+}
+
 // Error-free sum of two floats (Knuth's TwoSum): s + err == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err)
 {
@@ -423,13 +456,11 @@ __device__ __forceinline__ void sparse_body(const WlrParams& p, const Src& src)
         }
         first_item = false;
         if (timed_out) break;
-        accp_reduce(acc, g);
-        if (active) {
-            accp_store(acc, p.gram + (size_t)entry * kGramStride, sub, g);
-            if (sub == 0) {
-                atomicAdd(&s_pairs, (unsigned long long)(nx * ny * sv.n_tau));
-                atomicAdd(&s_pix, 1ull);
-            }
+        store_records(acc, reinterpret_cast<float*>(wbuf), p.gram, split ? base + (uint32_t)part : base,
+                      split ? 1 : m, g);
+        if (active && sub == 0) {
+            atomicAdd(&s_pairs, (unsigned long long)(nx * ny * sv.n_tau));
+            atomicAdd(&s_pix, 1ull);
         }
         }   // passes
         if (timed_out) break;

@@ -214,12 +214,9 @@ __device__ __forceinline__ void accp_reduce(AccP& a, int g)
     }
 }
 
-// Store the sums as one Gram record (rec: kGramStride floats, 16-byte aligned).
-// The g lanes of a pixel (all holding the reduced sums) split the 17 16-byte
-// pieces; sub is the lane's index among them.
-__device__ __forceinline__ void accp_store(const AccP& a, float* __restrict__ rec, int sub, int g)
+// The sums in Gram-record order (kGramStride floats, the last two zero).
+__device__ __forceinline__ void accp_values(const AccP& a, float (&v)[kGramStride])
 {
-    float v[kGramStride];
     v[0] = a.g0;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
@@ -238,6 +235,15 @@ __device__ __forceinline__ void accp_store(const AccP& a, float* __restrict__ re
     }
     v[66] = 0.0f;
     v[67] = 0.0f;
+}
+
+// Store the sums as one Gram record (rec: kGramStride floats, 16-byte aligned).
+// The g lanes of a pixel (all holding the reduced sums) split the 17 16-byte
+// pieces; sub is the lane's index among them.
+__device__ __forceinline__ void accp_store(const AccP& a, float* __restrict__ rec, int sub, int g)
+{
+    float v[kGramStride];
+    accp_values(a, v);
     float4* out = reinterpret_cast<float4*>(rec);
 #pragma unroll
     for (int q = 0; q < kGramStride / 4; ++q)
