@@ -240,7 +240,8 @@ def test_overlapped_event_writers_match_per_frame_drains(precision):
     """A frame's event writer runs on its own stream beside the next frame's
     ingest and pass 1.  Pushing 12 frames with no drain in between (so every
     writer overlaps the next frame) gives the same events, alpha and flags as
-    draining after every frame (each drain waits for the writer)."""
+    draining after every frame (each drain waits for the writer) and as a
+    profiled run (the writer serialised on the context's stream)."""
     import paper_2303_02608_gb300 as m
     cfg = SceneConfig(kind="rects", width=200, height=100, frames=12, spp=1, seed=5, rgb=True, n_rects=14,
                       bg_depth=10.0)
@@ -256,8 +257,12 @@ def test_overlapped_event_writers_match_per_frame_drains(precision):
         mk = lambda: Simulator(SimConfig(width=W, height=H, radius=3, frames=3, contrast=0.1, mode=ADAPTIVE,
                                          rgb=True))
     out = []
-    for drain_each in (True, False):
+    # drained every frame, never drained, and profiled (the writer then runs on
+    # the context's stream, serialised)
+    for drain_each, profiled in ((True, False), (False, False), (False, True)):
         sim = mk()
+        if profiled:
+            sim.profile(True)
         evs = []
         for f in frames:
             sim.push(f)
@@ -268,7 +273,8 @@ def test_overlapped_event_writers_match_per_frame_drains(precision):
         a, fl = sim.denoised()
         sim.close()
         out.append((np.concatenate(evs), a.cpu(), fl.cpu()))
-    (e0, a0, f0), (e1, a1, f1) = out
+    e0, a0, f0 = out[0]
     assert e0.size > 100
-    assert np.array_equal(e0, e1)
-    assert torch.equal(a0, a1) and torch.equal(f0, f1)
+    for e1, a1, f1 in out[1:]:
+        assert np.array_equal(e0, e1)
+        assert torch.equal(a0, a1) and torch.equal(f0, f1)
