@@ -1062,8 +1062,9 @@ def _pingpong(s: int, n: int) -> int:
 def _e2e(args, scene, wl, N, stream):
     """Same metric through the public API with pinned host buffers (precision
     form): every step copies its frame in (inside esim_ad_push_frame) and
-    drains its events to the host (esim_ad_events).  The host frames are a
-    pinned pool of 8 distinct frames played forward and backward."""
+    drains its events into a pinned host buffer (esim_ad_events).  The host
+    frames are a pinned pool of 8 distinct frames played forward and
+    backward."""
     import torch
     import paper_2303_02608_gb300 as lib
     from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, SimConfig, Simulator
@@ -1095,9 +1096,11 @@ def _e2e(args, scene, wl, N, stream):
                               mode=ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=1 << 24,
                               radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
                               precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE), stream)
+    # the events land in a pinned host buffer of the caller's (the step's result read)
+    ev_host = torch.empty((1 << 22) * 12, dtype=torch.uint8, pin_memory=True)
     for s in range(W):
         sim.push(host[_pingpong(s, n)])
-        sim.events()
+        sim.events_into(ev_host)
     torch.cuda.synchronize()
     import gc
     gc.collect()
@@ -1111,7 +1114,7 @@ def _e2e(args, scene, wl, N, stream):
             idx = _pingpong(s, n)
             sim.push(host[idx])
             tm = time.perf_counter()
-            d2h += len(sim.events()) * 12 + 64
+            d2h += sim.events_into(ev_host) * 12 + 64
             te = time.perf_counter()
             push_ms.append((tm - ts) * 1e3)
             step_ms.append((te - ts) * 1e3)

@@ -624,6 +624,18 @@ class Simulator:
         self._keep.clear()
         return out
 
+    def events_into(self, dst) -> int:
+        """Drain the events produced so far into `dst`, a tensor owned by the
+        caller (pinned host memory, or device memory), as 12-byte records of
+        EVENT_DTYPE; returns their number.  One synchronising call and one
+        copy, no array allocated; raises EsimError (ENOSPACE) when they do not
+        fit, draining nothing."""
+        cap = dst.numel() * dst.element_size() // EVENT_DTYPE.itemsize
+        st, n = esim_ad_events(self.ctx, dst.data_ptr(), cap, dst_is_device=bool(dst.is_cuda))
+        _check(st, "esim_ad_events")
+        self._keep.clear()
+        return n
+
     def events_device(self, dst, cap: int) -> int:
         st, n = esim_ad_events(self.ctx, dst.data_ptr(), cap, dst_is_device=True)
         _check(st, "esim_ad_events")

@@ -383,3 +383,35 @@ def test_state_roundtrip_resume(lib):
     assert np.array_equal(got[["x", "y", "polarity"]], want[["x", "y", "polarity"]])
     for s in (a, b, c):
         s.close()
+
+
+@pytest.mark.gpu
+def test_events_into_pinned_and_device_buffers(lib):
+    """events_into drains into the caller's own buffer (pinned host or device)
+    with the same records as events(); a buffer too small raises ENOSPACE and
+    drains nothing."""
+    import torch
+    from paper_2303_02608_gb300 import EVENT_DTYPE, SimConfig, Simulator
+    W, H = 40, 24
+    f0 = _frame(W, H)
+    f1 = {k: (v * 2.0 if k == "radiance" else v).contiguous() for k, v in f0.items()}
+    runs = []
+    for dest in ("events", "pinned", "device"):
+        sim = Simulator(SimConfig(width=W, height=H, radius=1, frames=1, contrast=0.1, mode=lib.ESIM_AD_EXHAUSTIVE))
+        sim.push(f0)
+        sim.push(f1)
+        if dest == "events":
+            runs.append(sim.events())
+        else:
+            if dest == "pinned":
+                small = torch.empty(12, dtype=torch.uint8, pin_memory=True)
+                with pytest.raises(lib.EsimError) as e:
+                    sim.events_into(small)
+                assert e.value.status == lib.ESIM_AD_ENOSPACE
+            buf = torch.empty(1 << 20, dtype=torch.uint8, pin_memory=(dest == "pinned"),
+                              device="cuda" if dest == "device" else "cpu")
+            n = sim.events_into(buf)
+            runs.append(buf.cpu().numpy()[: n * 12].view(EVENT_DTYPE).copy())
+        sim.close()
+    assert runs[0].size > 0
+    assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2])
