@@ -199,12 +199,26 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* ctx, const esim_ad_frame* frame);
  * column x, repeated events of a pixel adjacent.  Synchronises the stream.
  * *n_out receives the number of events.  If cap is smaller than that number,
  * nothing is drained, *n_out holds the required count and ENOSPACE is
- * returned.  If the device buffer (event_capacity) overflowed since the last
- * drain, events were lost: returns EOVERFLOW (sticky) with *n_out = the
- * number of events that were produced.  dst may be NULL when cap == 0 (query).
+ * returned.  The device buffer (event_capacity records) is a ring: a frame's
+ * records are lost when, with those not yet drained, they would exceed it;
+ * then this returns EOVERFLOW (sticky) with *n_out = the number of events
+ * produced since the last drain.  dst may be NULL when cap == 0 (query).
  */
 esim_ad_status esim_ad_events(esim_ad_ctx* ctx, esim_ad_event* dst, uint64_t cap,
                               uint64_t* n_out, int dst_is_device);
+
+/*
+ * Drain the events of the frames up to and including `frame` (an index of a
+ * pushed frame, t = 0, 1, ...; at most 7 frames older than the latest), with
+ * the semantics of esim_ad_events otherwise.  It waits for that frame's event
+ * writer only, copying on an internal stream: frames pushed after it keep
+ * computing (and their host-to-device copies keep landing) meanwhile, so a
+ * caller can push frame t + 1 before draining frame t.  Events of that frame
+ * already drained by a wider drain give 0.  No paper counterpart: a
+ * streaming interface.  EINVAL for a frame not pushed or too old.
+ */
+esim_ad_status esim_ad_events_frame(esim_ad_ctx* ctx, uint64_t frame, esim_ad_event* dst, uint64_t cap,
+                                    uint64_t* n_out, int dst_is_device);
 
 /*
  * Copy the last frame's per-pixel results: alpha = f(x^c) of Eq. 4 (denoised

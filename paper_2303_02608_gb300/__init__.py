@@ -39,7 +39,7 @@ ESIM_AD_MIXED = 1
 
 # Every exported symbol of the library, as declared in include/esim_ad.h.
 EXPORTS = (
-    "esim_ad_init", "esim_ad_push_frame", "esim_ad_events", "esim_ad_denoised",
+    "esim_ad_init", "esim_ad_push_frame", "esim_ad_events", "esim_ad_events_frame", "esim_ad_denoised",
     "esim_ad_get_state", "esim_ad_set_state", "esim_ad_reset", "esim_ad_stats_get",
     "esim_ad_destroy", "esim_ad_status_string", "esim_ad_profile_enable", "esim_ad_profile_get",
     "esim_ad_write_events_noalloc", "esim_ad_batch_tiling", "esim_ad_wlr_workspace_size", "esim_ad_wlr_forward",
@@ -124,6 +124,9 @@ def load_library():
     lib.esim_ad_push_frame.argtypes = [P, ctypes.POINTER(esim_ad_frame)]
     lib.esim_ad_events.restype = st
     lib.esim_ad_events.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+    lib.esim_ad_events_frame.restype = st
+    lib.esim_ad_events_frame.argtypes = [P, ctypes.c_uint64, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.c_int]
     lib.esim_ad_denoised.restype = st
     lib.esim_ad_denoised.argtypes = [P, P, P, ctypes.c_int]
     lib.esim_ad_get_state.restype = st
@@ -250,6 +253,14 @@ def esim_ad_events(ctx: int, dst: int, cap: int, dst_is_device: bool = False) ->
     n = ctypes.c_uint64(0)
     st = load_library().esim_ad_events(ctypes.c_void_p(ctx), ctypes.c_void_p(dst or None),
                                        ctypes.c_uint64(cap), ctypes.byref(n), int(dst_is_device))
+    return st, n.value
+
+
+def esim_ad_events_frame(ctx: int, frame: int, dst: int, cap: int, dst_is_device: bool = False) -> tuple[int, int]:
+    """Drain the events of frames up to `frame`; returns (status, n) like esim_ad_events."""
+    n = ctypes.c_uint64(0)
+    st = load_library().esim_ad_events_frame(ctypes.c_void_p(ctx), ctypes.c_uint64(frame), ctypes.c_void_p(dst or None),
+                                             ctypes.c_uint64(cap), ctypes.byref(n), int(dst_is_device))
     return st, n.value
 
 
@@ -577,6 +588,7 @@ class Simulator:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = esim_ad_init(cfg.c_config(), self.stream.cuda_stream)
         self._keep = []
+        self._t = 0            # index of the next frame pushed
         self._ev_host = None   # pinned landing buffer of events(), grown on demand
 
     def close(self):
@@ -603,8 +615,9 @@ class Simulator:
                            ptr.get("depth", 0), variance=ptr.get("variance", 0), on_host=on_host,
                            features=ptr.get("features", 0), pitch=pitch)
         # inputs (device planes, or pinned host planes copied asynchronously) are
-        # read in stream order; keep them alive until the next sync point
-        self._keep.append(planes)
+        # read in stream order; keep them alive until a sync point covers them
+        self._keep.append((self._t, planes))
+        self._t += 1
 
     def events(self) -> np.ndarray:
         """Drain the events produced so far (one synchronising call when they
@@ -634,6 +647,18 @@ class Simulator:
         st, n = esim_ad_events(self.ctx, dst.data_ptr(), cap, dst_is_device=bool(dst.is_cuda))
         _check(st, "esim_ad_events")
         self._keep.clear()
+        return n
+
+    def events_frame_into(self, frame: int, dst) -> int:
+        """Drain the events of the frames up to `frame` (the index of a pushed
+        frame, at most 7 behind the latest) into the caller's tensor `dst`
+        (pinned host or device memory); waits for that frame's event writer
+        only, so the frames pushed after it keep running.  Returns the number
+        of events; raises EsimError (ENOSPACE) when they do not fit."""
+        cap = dst.numel() * dst.element_size() // EVENT_DTYPE.itemsize
+        st, n = esim_ad_events_frame(self.ctx, frame, dst.data_ptr(), cap, dst_is_device=bool(dst.is_cuda))
+        _check(st, "esim_ad_events_frame")
+        self._keep = [e for e in self._keep if e[0] > frame]   # frames up to `frame` are done
         return n
 
     def events_device(self, dst, cap: int) -> int:
@@ -666,6 +691,7 @@ class Simulator:
     def reset(self) -> None:
         esim_ad_reset(self.ctx)
         self._keep.clear()
+        self._t = 0
 
     def stats(self) -> dict:
         return esim_ad_stats_get(self.ctx)

@@ -60,8 +60,15 @@ struct esim_ad_ctx {
     // frame's ingest and pass 1; the context's stream waits for it (ev_written)
     // before the next solve and before anything that reads what it writes.
     cudaStream_t writer_stream = nullptr;
-    cudaEvent_t ev_solved = nullptr, ev_written = nullptr;
+    cudaEvent_t ev_solved = nullptr;
+    cudaEvent_t ev_wr[kFrameEnds] = {};   // after frame f's writer (frame 0: its solve), at f % kFrameEnds
+    int last_wr = 0;                      // slot of the latest pushed frame
     bool writer_pending = false;
+    // drains of single frames copy on their own stream, so that they wait for
+    // that frame's writer only, not for the frames pushed after it
+    cudaStream_t drain_stream = nullptr;
+    uint64_t drained = 0;                 // event positions drained so far
+    unsigned long long* hmark = nullptr;  // pinned: a frame's end mark and the status word
     int device = 0;
     int W = 0, H = 0;
     size_t N = 0;
@@ -165,8 +172,11 @@ void release(esim_ad_ctx* c)
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->writer_stream) cudaStreamDestroy(c->writer_stream);
+    if (c->drain_stream) cudaStreamDestroy(c->drain_stream);
+    if (c->hmark) cudaFreeHost(c->hmark);
     if (c->ev_solved) cudaEventDestroy(c->ev_solved);
-    if (c->ev_written) cudaEventDestroy(c->ev_written);
+    for (cudaEvent_t e : c->ev_wr)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     c->prof_events.clear();
 }
@@ -200,7 +210,7 @@ struct ProfScope {
 // Order the context's stream after the latest frame's event writer.
 cudaError_t join_writer(esim_ad_ctx* c)
 {
-    return c->writer_pending ? cudaStreamWaitEvent(c->stream, c->ev_written, 0) : cudaSuccess;
+    return c->writer_pending ? cudaStreamWaitEvent(c->stream, c->ev_wr[c->last_wr], 0) : cudaSuccess;
 }
 
 // Synchronise the context's stream, the event writer included.
@@ -369,9 +379,22 @@ esim_ad_status esim_ad_init(const esim_ad_config* cfg, void* cuda_stream, esim_a
         cudaMemset(c->alpha, 0, N * sizeof(float)) != cudaSuccess ||
         cudaMemset(c->flag, 0, N) != cudaSuccess || cudaMemset(c->nev, 0, N * sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(c->ev_mask, 0, 2 * (size_t)c->n_chunks * (kChunk / 32) * sizeof(uint32_t)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->writer_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        [&] {
+            // the writer stream at the highest priority: its CTAs take the SMs as
+            // the frame's solve drains, ahead of the next frame's ingest, instead
+            // of waiting behind that frame's register-filling kernels
+            int lo = 0, hi = 0;
+            if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return false;
+            return cudaStreamCreateWithPriority(&c->writer_stream, cudaStreamNonBlocking, hi) == cudaSuccess;
+        }() == false ||
+        cudaStreamCreateWithFlags(&c->drain_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaHostAlloc((void**)&c->hmark, 2 * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_solved, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_written, cudaEventDisableTiming) != cudaSuccess ||
+        [&] {
+            for (cudaEvent_t& e : c->ev_wr)
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+            return true;
+        }() == false ||
         cudaMemset(c->state, 0, 4 * N * sizeof(float4)) != cudaSuccess) {
         release(c);
         delete c;
@@ -649,6 +672,7 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
     if (c->t > 0) {
         EventParams ep;
         ep.nev = c->nev;
+        ep.drained = c->drained;
         ep.n_pix = (long long)c->N;
         ep.W = c->W;
         ep.n_chunks = c->n_chunks;
@@ -671,17 +695,41 @@ esim_ad_status esim_ad_push_frame(esim_ad_ctx* c, const esim_ad_frame* fin)
             ProfScope ps(c, 2, ws);
             if (launch_event_write(ep, ws) != cudaSuccess) return ESIM_AD_ECUDA;
         }
-        if (overlap) {
-            if (cudaEventRecord(c->ev_written, c->writer_stream) != cudaSuccess) return ESIM_AD_ECUDA;
-            c->writer_pending = true;
-        }
+        c->last_wr = (int)(c->t % kFrameEnds);
+        if (cudaEventRecord(c->ev_wr[c->last_wr], overlap ? c->writer_stream : c->stream) != cudaSuccess)
+            return ESIM_AD_ECUDA;
+        c->writer_pending = true;
         c->prof_kernels += 1;
+    } else {
+        // frame 0 writes no events: its mark is the end of its solve
+        c->last_wr = 0;
+        if (cudaEventRecord(c->ev_wr[0], c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
     }
     if (slot >= 0) {
         // the caller may reuse its host buffers once its copies are done
         if (cudaEventSynchronize(c->ev_copied[slot]) != cudaSuccess) return ESIM_AD_ECUDA;
     }
     c->t += 1;
+    return ESIM_AD_OK;
+}
+
+// Copy n event records from ring position `from` (wrapping at the buffer's
+// end: at most two pieces) and record them as drained.
+static esim_ad_status copy_ring(esim_ad_ctx* c, esim_ad_event* dst, uint64_t from, uint64_t n,
+                                int dst_is_device, cudaStream_t s)
+{
+    const uint64_t cap = c->cfg.event_capacity;
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (n > 0) {
+        const uint64_t i0 = from % cap;
+        const uint64_t first = n < cap - i0 ? n : cap - i0;
+        if (cudaMemcpyAsync(dst, c->events + i0, first * sizeof(esim_ad_event), k, s) != cudaSuccess ||
+            (n > first &&
+             cudaMemcpyAsync(dst + first, c->events, (n - first) * sizeof(esim_ad_event), k, s) != cudaSuccess))
+            return ESIM_AD_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ESIM_AD_ECUDA;
+    c->drained = from + n;   // the next frames' writers see it as pushed
     return ESIM_AD_OK;
 }
 
@@ -693,7 +741,7 @@ esim_ad_status esim_ad_events(esim_ad_ctx* c, esim_ad_event* dst, uint64_t cap, 
     DeviceGuard guard(c->device);
     Ctrl h;
     if (sync_and_check(c, &h) != ESIM_AD_OK) return ESIM_AD_ECUDA;
-    const unsigned long long total = h.ev_total;
+    const unsigned long long total = h.ev_total - c->drained;
     if (c->sticky == ESIM_AD_EOVERFLOW) {
         *n_out = total;
         return ESIM_AD_EOVERFLOW;
@@ -701,16 +749,45 @@ esim_ad_status esim_ad_events(esim_ad_ctx* c, esim_ad_event* dst, uint64_t cap, 
     if (c->sticky != ESIM_AD_OK) return c->sticky;
     *n_out = total;
     if (cap < total) return ESIM_AD_ENOSPACE;
-    if (total > 0) {
-        if (cudaMemcpyAsync(dst, c->events, total * sizeof(esim_ad_event),
-                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                            c->stream) != cudaSuccess)
-            return ESIM_AD_ECUDA;
-        if (cudaMemsetAsync(&c->ctrl->ev_total, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
-            return ESIM_AD_ECUDA;
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ESIM_AD_ECUDA;
-    }
+    if (total > 0) return copy_ring(c, dst, c->drained, total, dst_is_device, c->stream);
     return ESIM_AD_OK;
+}
+
+esim_ad_status esim_ad_events_frame(esim_ad_ctx* c, uint64_t frame, esim_ad_event* dst, uint64_t cap,
+                                    uint64_t* n_out, int dst_is_device)
+{
+    if (!c || !n_out || (cap > 0 && !dst)) return ESIM_AD_EINVAL;
+    if (c->sticky != ESIM_AD_OK) return ESIM_AD_ESTATE;
+    if (frame >= c->t || c->t - 1 - frame >= (uint64_t)kFrameEnds) return ESIM_AD_EINVAL;
+    DeviceGuard guard(c->device);
+    // wait for that frame's writer only, on the drain stream; its end mark and
+    // the status word land in pinned memory
+    struct {
+        unsigned long long end;
+        uint32_t status;
+    } h = {0, 0};
+    const cudaStream_t s = c->drain_stream;
+    c->hmark[1] = 0;
+    if (cudaStreamWaitEvent(s, c->ev_wr[frame % kFrameEnds], 0) != cudaSuccess ||
+        cudaMemcpyAsync(&c->hmark[0], &c->ctrl->frame_end[frame % kFrameEnds], sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&c->hmark[1], &c->ctrl->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return ESIM_AD_ECUDA;
+    h.end = c->hmark[0];
+    h.status = (uint32_t)c->hmark[1];
+    if (frame == 0) h.end = c->drained;   // frame 0 writes no events (and no end mark)
+    if (h.status & kStatusTimeout) c->sticky = ESIM_AD_ETIMEOUT;
+    else if (h.status & kStatusOverflow) c->sticky = ESIM_AD_EOVERFLOW;
+    const unsigned long long n = h.end > c->drained ? h.end - c->drained : 0ull;
+    if (c->sticky == ESIM_AD_EOVERFLOW) {
+        *n_out = n;
+        return ESIM_AD_EOVERFLOW;
+    }
+    if (c->sticky != ESIM_AD_OK) return c->sticky;
+    *n_out = n;
+    if (cap < n) return ESIM_AD_ENOSPACE;
+    return n > 0 ? copy_ring(c, dst, c->drained, n, dst_is_device, s) : ESIM_AD_OK;
 }
 
 esim_ad_status esim_ad_denoised(esim_ad_ctx* c, float* alpha, uint8_t* flags, int dst_is_device)
@@ -804,6 +881,7 @@ esim_ad_status esim_ad_reset(esim_ad_ctx* c)
         sync_stream(c) != cudaSuccess)
         return ESIM_AD_ECUDA;
     c->t = 0;
+    c->drained = 0;
     c->staged_ingests = 0;
     c->sticky = ESIM_AD_OK;
     return ESIM_AD_OK;

@@ -12,9 +12,11 @@
 //   1. count: each 2048-pixel chunk sums |p*n| (counts beyond
 //      kMaxCountPerPixel in magnitude set a status bit instead).
 //   2. write: each chunk's CTA adds up the counts of all earlier chunks for
-//      its offset, rescans its pixels and writes its records there.  Records
-//      past the buffer capacity are dropped and the sticky overflow bit is
-//      set; the total still counts them.
+//      its offset, rescans its pixels and writes its records there.  The
+//      buffer is a ring: position pos sits at pos mod capacity.  A record
+//      that would leave more than capacity records undrained (from the
+//      positions drained when the frame was pushed on) is dropped and the
+//      sticky overflow bit is set; the total still counts it.
 #include "internal.h"
 #include "block_scan.cuh"
 
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(kThreads) event_write_kernel(EventParams p)
 #pragma unroll
         for (int k = 0; k < kPer; ++k) v[k] = (p0 + k < p.n_pix) ? p.nev[p0 + k] : 0;
     }
+    const unsigned long long drained = p.drained;
     const unsigned long long before = p.ctrl->ev_base + block_prefix_count(p.chunk_cnt, blockIdx.x, s_red);
     const bool range_ok = (p.ctrl->status & kStatusCountRange) == 0u;
     if (last && threadIdx.x == 0) {
@@ -94,16 +97,26 @@ __global__ void __launch_bounds__(kThreads) event_write_kernel(EventParams p)
         } else {
             p.ctrl->ev_total = before + cnt;
             p.ctrl->ev_cum += before + cnt - p.ctrl->ev_base;
+            p.ctrl->frame_end[p.frame % kFrameEnds] = before + cnt;
         }
     }
     if (cnt == 0u || !range_ok) return;
+    // the ring index of the chunk's first record: one division per CTA,
+    // published by the scan's barriers
+    __shared__ unsigned long long s_base_idx;
+    if (threadIdx.x == 0) s_base_idx = p.capacity ? before % p.capacity : 0ull;
     int c = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) c += abs(v[k]);
     int total;
     const int off = block_exclusive_scan(c, s_warp, total);
     if (total == 0) return;
+    // positions run on from the earlier frames' records; position pos is kept
+    // at pos mod capacity while it leaves the undrained records (from
+    // `drained` on) no more than capacity long, else it is dropped
     unsigned long long pos = before + (unsigned long long)off;
+    unsigned long long idx = s_base_idx + (unsigned long long)off;
+    if (idx >= p.capacity) idx = p.capacity ? idx % p.capacity : 0ull;   // rare: a wrap inside the chunk
     bool overflow = false;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
@@ -113,15 +126,17 @@ __global__ void __launch_bounds__(kThreads) event_write_kernel(EventParams p)
         const uint32_t x = (uint32_t)(pix % p.W), y = (uint32_t)(pix / p.W);
         const uint32_t w1 = x | (y << 16);
         const uint32_t w2 = (uint32_t)(uint8_t)(int8_t)(v[k] > 0 ? 1 : -1);
-        for (int e = 0; e < n; ++e, ++pos) {
-            if (pos >= p.capacity) {
+        for (int e = 0; e < n; ++e) {
+            if (pos - drained >= p.capacity) {
                 overflow = true;
-                continue;
+            } else {
+                uint32_t* rec = reinterpret_cast<uint32_t*>(p.events + idx);
+                rec[0] = p.frame;
+                rec[1] = w1;
+                rec[2] = w2;
             }
-            uint32_t* rec = reinterpret_cast<uint32_t*>(p.events + pos);
-            rec[0] = p.frame;
-            rec[1] = w1;
-            rec[2] = w2;
+            ++pos;
+            if (++idx == p.capacity) idx = 0;
         }
     }
     if (overflow) atomicOr(&p.ctrl->status, kStatusOverflow);

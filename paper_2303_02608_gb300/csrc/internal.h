@@ -35,7 +35,8 @@ struct Ctrl {
     uint32_t flag_total;            // pixels flagged by the test kernel this frame
     uint32_t list_len;              // flagged-list length: each tile's run padded to a multiple of 4
     uint32_t tail_next;             // sparse regression: next single entry of the list's tail
-    unsigned long long ev_total;    // events produced since the last drain
+    unsigned long long ev_total;    // record positions used: since init/reset (simulator: the event
+                                    // buffer is a ring), or since the last drain (batching form)
     unsigned long long ev_cum;      // events since init/reset
     unsigned long long regressions; // pixels regressed since init/reset
     unsigned long long neighbours;  // (pixel, neighbour) pairs regressed
@@ -43,7 +44,9 @@ struct Ctrl {
     uint32_t status;                // sticky kStatus* bits
     uint32_t pad2;
     unsigned long long ev_base;     // ev_total before this frame's events (set by the solve kernel)
+    unsigned long long frame_end[8];  // simulator: ev_total after frame f's writer, at f % 8
 };
+constexpr int kFrameEnds = 8;
 constexpr size_t kCtrlPerFrameBytes = 24;   // the per-frame counters above ev_total
 static_assert(offsetof(Ctrl, ev_total) == kCtrlPerFrameBytes, "per-frame part of Ctrl");
 // Largest |signed event count| of one pixel in one frame: a 2048-pixel chunk then
@@ -179,6 +182,7 @@ struct WlrParams {
 struct EventParams {
     const int32_t* nev;
     const uint32_t* ev_mask = nullptr;   // bit per pixel with events (nullptr: read every count)
+    unsigned long long drained = 0;      // ring positions drained when the frame was pushed
     long long n_pix;
     int W;
     int n_chunks;

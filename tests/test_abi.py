@@ -415,3 +415,112 @@ def test_events_into_pinned_and_device_buffers(lib):
         sim.close()
     assert runs[0].size > 0
     assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2])
+
+
+def _ring_frames(n):
+    """n device frames whose radiance steps up and down, so every frame emits."""
+    import torch
+    f0 = _frame(40, 24)
+    out = []
+    for t in range(n):
+        s = 1.0 + 0.6 * (t % 3)
+        out.append({k: (v * s if k == "radiance" else v).contiguous() for k, v in f0.items()})
+    return out
+
+
+def _ring_sim(lib, capacity):
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    return Simulator(SimConfig(width=40, height=24, radius=1, frames=1, contrast=0.1,
+                               mode=lib.ESIM_AD_EXHAUSTIVE, event_capacity=capacity))
+
+
+@pytest.mark.gpu
+def test_events_frame_lookahead_matches_per_frame_drains(lib):
+    """Draining frame t after frame t + 1 was pushed (esim_ad_events_frame)
+    gives each frame's events exactly as draining after every push."""
+    import torch
+    from paper_2303_02608_gb300 import EVENT_DTYPE
+    frames = _ring_frames(12)
+    sim = _ring_sim(lib, 1 << 20)
+    ref = []
+    for f in frames:
+        sim.push(f)
+        ref.append(sim.events())
+    sim.close()
+    sim = _ring_sim(lib, 1 << 20)
+    buf = torch.empty(1 << 22, dtype=torch.uint8, pin_memory=True)
+    got = []
+    sim.push(frames[0])
+    for t in range(1, len(frames)):
+        sim.push(frames[t])
+        n = sim.events_frame_into(t - 1, buf)
+        got.append(buf.numpy()[: n * 12].view(EVENT_DTYPE).copy())
+    n = sim.events_frame_into(len(frames) - 1, buf)
+    got.append(buf.numpy()[: n * 12].view(EVENT_DTYPE).copy())
+    sim.close()
+    assert sum(len(e) for e in ref) > 1000
+    for t, (a, b) in enumerate(zip(ref, got)):
+        assert np.array_equal(a, b), t
+        assert len(a) == 0 or np.all(a["frame"] == t)
+
+
+@pytest.mark.gpu
+def test_event_ring_wraps(lib):
+    """A capacity a little above one frame's events: positions wrap round the
+    ring many times over the sequence, and per-frame drains (full or bounded)
+    still return every event, in order; three frames left undrained overflow
+    it (sticky), the count still covering every event produced."""
+    import torch
+    from paper_2303_02608_gb300 import EVENT_DTYPE
+    frames = _ring_frames(12)
+    big = _ring_sim(lib, 1 << 20)
+    ref = []
+    for f in frames:
+        big.push(f)
+        ref.append(big.events())
+    big.close()
+    per_frame = max(len(e) for e in ref)
+    cap = per_frame + 37
+    for mode in ("full", "frame"):
+        sim = _ring_sim(lib, cap)
+        buf = torch.empty(cap * 12, dtype=torch.uint8, pin_memory=True)
+        for t, f in enumerate(frames):
+            sim.push(f)
+            if mode == "full":
+                got = sim.events()
+            else:
+                n = sim.events_frame_into(t, buf)
+                got = buf.numpy()[: n * 12].view(EVENT_DTYPE).copy()
+            assert np.array_equal(got, ref[t]), (mode, t)
+        sim.close()
+    assert sum(len(e) for e in ref) > 3 * cap      # the ring wrapped
+    sim = _ring_sim(lib, cap)
+    for f in frames[:4]:
+        sim.push(f)                                # frames 1-3 undrained: more than cap
+    assert len(ref[1]) + len(ref[2]) + len(ref[3]) > cap
+    st, n = lib.esim_ad_events(sim.ctx, 0, 0)
+    assert st == lib.ESIM_AD_EOVERFLOW and n == len(ref[1]) + len(ref[2]) + len(ref[3])
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_events_frame_arguments(lib):
+    import torch
+    frames = _ring_frames(10)
+    sim = _ring_sim(lib, 1 << 20)
+    buf = torch.empty(1 << 20, dtype=torch.uint8, pin_memory=True)
+    with pytest.raises(lib.EsimError) as e:
+        sim.events_frame_into(0, buf)               # nothing pushed yet
+    assert e.value.status == lib.ESIM_AD_EINVAL
+    sim.push(frames[0])
+    assert sim.events_frame_into(0, buf) == 0       # frame 0 emits nothing
+    for f in frames[1:]:
+        sim.push(f)
+    with pytest.raises(lib.EsimError) as e:
+        sim.events_frame_into(1, buf)               # 8 frames behind the latest
+    assert e.value.status == lib.ESIM_AD_EINVAL
+    n = sim.events_frame_into(5, buf)               # frames 1-5
+    assert n > 0 and sim.events_frame_into(3, buf) == 0   # already drained
+    rest = sim.events()                             # frames 6-9
+    assert len(rest) > 0 and np.all(rest["frame"] >= 6)
+    sim.close()
