@@ -110,28 +110,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-// Hint the next use of a global line into L1 (never faults; no effect on values).
-__device__ __forceinline__ void prefetch_l1(const void* p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 // 2^x on the MUFU unit (ex2.approx, flush-to-zero).
-// 16-byte asynchronous copy global -> shared (L2 only), and the wait for all
-// of the thread's outstanding copies.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gsrc)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-__device__ __forceinline__ void prefetch_l2(const void* p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;

@@ -374,203 +374,6 @@ __device__ __forceinline__ void solve(Acc& a, const float (&s2)[NZ], float ridge
     for (int i = 0; i < NZ; ++i) theta[i] *= dsc[i];
 }
 
-// FP64 Cholesky re-solve of the equilibrated FP32 system (rarely taken; kept
-// out of line so that its arrays do not burden the callers' registers).
-__device__ __noinline__ void solve_fp64(const float (&A)[NG], const float (&b)[NZ], float (&th)[NZ])
-{
-    double L[NG];
-    double dinv[NZ];
-    for (int j = 0; j < NZ; ++j) {
-        double sj = (double)A[tri(j, j)];
-        for (int k = 0; k < j; ++k) sj -= L[tri(j, k)] * L[tri(j, k)];
-        sj = sj > 1e-300 ? sj : 1e-300;
-        const double l = sqrt(sj);
-        L[tri(j, j)] = l;
-        dinv[j] = 1.0 / l;
-        for (int i = j + 1; i < NZ; ++i) {
-            double v = (double)A[tri(i, j)];
-            for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
-            L[tri(i, j)] = v * dinv[j];
-        }
-    }
-    double z[NZ], x[NZ];
-    for (int i = 0; i < NZ; ++i) {
-        double v = (double)b[i];
-        for (int k = 0; k < i; ++k) v -= L[tri(i, k)] * z[k];
-        z[i] = v * dinv[i];
-    }
-    for (int i = NZ - 1; i >= 0; --i) {
-        double v = z[i];
-        for (int k = i + 1; k < NZ; ++k) v -= L[tri(k, i)] * x[k];
-        x[i] = v * dinv[i];
-    }
-    for (int i = 0; i < NZ; ++i) th[i] = (float)x[i];
-}
-
-// Mixed-form solve: FP32 Cholesky of the equilibrated system plus one step of
-// iterative refinement (the residual taken against the unfactored matrix),
-// and an FP64 Cholesky re-solve when the condition number estimated from the
-// factor's diagonal, (max L_ii / min L_ii)^2, exceeds 1e6.  Returns 1 if the
-// FP64 path ran.
-__device__ __forceinline__ int solve_mixed_inl(Acc& a, const float (&s2)[NZ], float ridge,
-                                        float (&theta)[NZ])
-{
-    const float W = a.G[0];
-#pragma unroll
-    for (int j = 1; j < NZ; ++j) a.G[tri(j, j)] = fmaf(ridge * W, s2[j], a.G[tri(j, j)]);
-    float dsc[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) dsc[i] = rsqrtf(a.G[tri(i, i)]);
-    float A[NG], b[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) A[tri(i, j)] = a.G[tri(i, j)] * (dsc[i] * dsc[j]);
-        b[i] = a.B[i] * dsc[i];
-    }
-    // factor into a.G
-    float inv[NZ];
-    float lmin = 3.4e38f, lmax = 0.0f;
-#pragma unroll
-    for (int j = 0; j < NZ; ++j) {
-        float sj = A[tri(j, j)];
-#pragma unroll
-        for (int k = 0; k < j; ++k) sj = fmaf(-a.G[tri(j, k)], a.G[tri(j, k)], sj);
-        sj = fmaxf(sj, 1e-20f);
-        const float l = sqrtf(sj);
-        lmin = fminf(lmin, l);
-        lmax = fmaxf(lmax, l);
-        a.G[tri(j, j)] = l;
-        inv[j] = 1.0f / l;
-#pragma unroll
-        for (int i = j + 1; i < NZ; ++i) {
-            float v = A[tri(i, j)];
-#pragma unroll
-            for (int k = 0; k < j; ++k) v = fmaf(-a.G[tri(i, k)], a.G[tri(j, k)], v);
-            a.G[tri(i, j)] = v * inv[j];
-        }
-    }
-    auto llt_solve = [&](const float (&rhs)[NZ], float (&x)[NZ]) {
-        float z[NZ];
-#pragma unroll
-        for (int i = 0; i < NZ; ++i) {
-            float v = rhs[i];
-#pragma unroll
-            for (int k = 0; k < i; ++k) v = fmaf(-a.G[tri(i, k)], z[k], v);
-            z[i] = v * inv[i];
-        }
-#pragma unroll
-        for (int i = NZ - 1; i >= 0; --i) {
-            float v = z[i];
-#pragma unroll
-            for (int k = i + 1; k < NZ; ++k) v = fmaf(-a.G[tri(k, i)], x[k], v);
-            x[i] = v * inv[i];
-        }
-    };
-    float th[NZ];
-    llt_solve(b, th);
-    // one refinement step: r = b - A th, th += (L L^T)^-1 r
-    float r[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) {
-        float v = b[i];
-#pragma unroll
-        for (int j = 0; j < NZ; ++j) v = fmaf(-A[i >= j ? tri(i, j) : tri(j, i)], th[j], v);
-        r[i] = v;
-    }
-    float dth[NZ];
-    llt_solve(r, dth);
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) th[i] += dth[i];
-    int used64 = 0;
-    const float ratio = lmax / lmin;
-    if (ratio * ratio > 1e6f) {
-        solve_fp64(A, b, th);
-        used64 = 1;
-    }
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) theta[i] = th[i] * dsc[i];
-    return used64;
-}
-
-
-// Mixed-form solve of the two-pass regression: FP32 Cholesky of the
-// equilibrated system plus one step of iterative refinement.  Returns false,
-// leaving theta unset, when the condition number estimated from the factor's
-// diagonal, (max L_ii / min L_ii)^2, exceeds 1e6: such systems are
-// accumulated again with compensated sums and solved in FP64.
-__device__ __forceinline__ bool solve_refined(Acc& a, const float (&s2)[NZ], float ridge, float (&theta)[NZ])
-{
-    const float W = a.G[0];
-#pragma unroll
-    for (int j = 1; j < NZ; ++j) a.G[tri(j, j)] = fmaf(ridge * W, s2[j], a.G[tri(j, j)]);
-    float dsc[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) dsc[i] = rsqrtf(a.G[tri(i, i)]);
-    float A[NG], b[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) A[tri(i, j)] = a.G[tri(i, j)] * (dsc[i] * dsc[j]);
-        b[i] = a.B[i] * dsc[i];
-    }
-    float inv[NZ];
-    float lmin = 3.4e38f, lmax = 0.0f;
-#pragma unroll
-    for (int j = 0; j < NZ; ++j) {
-        float sj = A[tri(j, j)];
-#pragma unroll
-        for (int k = 0; k < j; ++k) sj = fmaf(-a.G[tri(j, k)], a.G[tri(j, k)], sj);
-        sj = fmaxf(sj, 1e-20f);
-        const float l = sqrtf(sj);
-        lmin = fminf(lmin, l);
-        lmax = fmaxf(lmax, l);
-        a.G[tri(j, j)] = l;
-        inv[j] = 1.0f / l;
-#pragma unroll
-        for (int i = j + 1; i < NZ; ++i) {
-            float v = A[tri(i, j)];
-#pragma unroll
-            for (int k = 0; k < j; ++k) v = fmaf(-a.G[tri(i, k)], a.G[tri(j, k)], v);
-            a.G[tri(i, j)] = v * inv[j];
-        }
-    }
-    const float ratio = lmax / lmin;
-    if (!(ratio * ratio <= 1e6f)) return false;
-    auto llt_solve = [&](const float (&rhs)[NZ], float (&x)[NZ]) {
-        float z[NZ];
-#pragma unroll
-        for (int i = 0; i < NZ; ++i) {
-            float v = rhs[i];
-#pragma unroll
-            for (int k = 0; k < i; ++k) v = fmaf(-a.G[tri(i, k)], z[k], v);
-            z[i] = v * inv[i];
-        }
-#pragma unroll
-        for (int i = NZ - 1; i >= 0; --i) {
-            float v = z[i];
-#pragma unroll
-            for (int k = i + 1; k < NZ; ++k) v = fmaf(-a.G[tri(k, i)], x[k], v);
-            x[i] = v * inv[i];
-        }
-    };
-    float th[NZ];
-    llt_solve(b, th);
-    float r[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) {
-        float v = b[i];
-#pragma unroll
-        for (int j = 0; j < NZ; ++j) v = fmaf(-A[i >= j ? tri(i, j) : tri(j, i)], th[j], v);
-        r[i] = v;
-    }
-    float dth[NZ];
-    llt_solve(r, dth);
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) theta[i] = (th[i] + dth[i]) * dsc[i];
-    return true;
-}
-
 // Mixed-form solve of one Gram record: FP32 Cholesky of the ridged,
 // Jacobi-equilibrated system A plus one step of iterative refinement, whose
 // residual is taken against the unfactored system re-read from the record,
@@ -695,13 +498,6 @@ __device__ __forceinline__ bool solve_refined_rec(const float* __restrict__ rec,
     return true;
 }
 
-// Out-of-line copy for callers whose accumulation loop already holds the
-// register budget (the solve then runs on the call's own frame).
-__device__ __noinline__ int solve_mixed_call(Acc& a, const float (&s2)[NZ], float ridge, float (&theta)[NZ])
-{
-    return solve_mixed_inl(a, s2, ridge, theta);
-}
-
 // Eq. 1 at a fixed frame time, and the model update of Fig. 1.
 template <bool kMixed>
 __device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const float (&theta)[NZ])
@@ -751,29 +547,6 @@ __device__ __forceinline__ void emit(const WlrParams& p, int cx, int cy, const f
     p.state[N + i] = b1;
     p.state[2 * N + i] = make_float4(x[0], x[1], x[2], x[3]);
     p.state[3 * N + i] = make_float4(x[4], x[5], x[6], L);
-}
-
-// Regress one pixel from its reduced sums, then emit (both forms).  kInline:
-// the mixed-form solve is inlined rather than called.
-template <bool kMixed, bool kInline = false>
-__device__ __forceinline__ void solve_and_emit(const WlrParams& p, Acc& acc, int cx, int cy,
-                                               unsigned long long* fp64_count)
-{
-    float s2[NZ];
-    s2[0] = 0.0f;
-    s2[1] = p.s_coord * p.s_coord;
-    s2[2] = s2[1];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) s2[3 + j] = p.s_feat[j] * p.s_feat[j];
-    float theta[NZ];
-    if (kMixed) {
-        const int used64 = kInline ? solve_mixed_inl(acc, s2, p.ridge, theta)
-                                   : solve_mixed_call(acc, s2, p.ridge, theta);
-        if (used64) atomicAdd(fp64_count, 1ull);
-    } else {
-        solve(acc, s2, p.ridge, theta);
-    }
-    emit<kMixed>(p, cx, cy, theta);
 }
 
 // End of a regression launch: add this CTA's work counters, record a timeout,
