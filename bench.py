@@ -67,9 +67,9 @@ FLOP_PER_SOLVE_2 = 63472
 REGRESSION_SOURCES = ("wlr.cu", "wlr_math.cuh", "regress.cuh", "sparse_stage.cuh", "ptx.cuh", "internal.h")
 NCU_TRAFFIC = {
     # frame 4 of the adaptive precision-form run on rects1080p, unscaled:
-    # wlr_adaptive_kernel 44,734,208 read + 1,289,472 written, wlr_solve_kernel
-    # 14,652,928 read + 40,448 written
-    "ecdceb2b76cfde9b": 44734208 + 1289472 + 14652928 + 40448,
+    # wlr_adaptive_kernel 44,776,704 read + 155,648 written, wlr_solve_kernel
+    # 14,655,744 read + 41,472 written
+    "13061a17d0297224": 44776704 + 155648 + 14655744 + 41472,
 }
 
 
@@ -1064,7 +1064,8 @@ def _e2e(args, scene, wl, N, stream):
     form): every step copies a frame in (inside esim_ad_push_frame) and drains
     a frame's events into a pinned host buffer (esim_ad_events_frame), one
     frame behind the push.  The host frames are a pinned pool of 8 distinct
-    frames played forward and backward."""
+    frames from the middle of the sequence played forward and backward; the
+    same loop over the same frames held on the device is timed beside it."""
     import torch
     import paper_2303_02608_gb300 as lib
     from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, SimConfig, Simulator
@@ -1074,15 +1075,18 @@ def _e2e(args, scene, wl, N, stream):
     # just before use (a pool of every timed frame reached ~1 GB, and copies
     # from parts of such a pool were measured 5-10x slower than from its start)
     n = min(scene.cfg.frames, W + K, 8)
+    # eight consecutive frames from the middle of the sequence, where the
+    # scene's motion and flag density are those of the timed frames at large
+    t_first = max(0, scene.cfg.frames // 2 - n // 2)
     # all host frames in one pinned allocation (views per frame and plane)
-    dev0 = _storage_frames([{k: v for k, v in scene.frame(0, "cuda").items()
+    dev0 = _storage_frames([{k: v for k, v in scene.frame(t_first, "cuda").items()
                              if k in ("radiance", "normal", "albedo", "depth")}])[0]
     sizes = {k: v.numel() * v.element_size() for k, v in dev0.items()}
     per = sum(sizes.values())
     pool = torch.empty(n * per, dtype=torch.uint8, pin_memory=True)
     host = []
     for t in range(n):
-        f = scene.frame(t, "cuda")
+        f = scene.frame(t_first + t, "cuda")
         sf = _storage_frames([{k: f[k] for k in ("radiance", "normal", "albedo", "depth")}])[0]
         frame, off = {}, t * per
         for k, v in sf.items():
@@ -1125,6 +1129,24 @@ def _e2e(args, scene, wl, N, stream):
         d2h += sim.events_frame_into(W + K - 1, ev_host) * 12 + 64
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        events_e2e = (d2h - 64 * K) // 12
+        # the same loop over the same frames resident on the device (no copy
+        # in, the same drains): the device-side rate of this exact work
+        dev_pool = [{k: v.cuda() for k, v in f.items()} for f in host]
+        sim.reset()
+        for s in range(W):
+            sim.push(dev_pool[_pingpong(s, n)])
+            sim.events_into(ev_host)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for s in range(W, W + K):
+            sim.push(dev_pool[_pingpong(s, n)])
+            if s > W:
+                sim.events_frame_into(s - 1, ev_host)
+        sim.events_frame_into(W + K - 1, ev_host)
+        torch.cuda.synchronize()
+        dt_dev = time.perf_counter() - t1
+        del dev_pool
     finally:
         gc.enable()
     sim.close()
@@ -1147,7 +1169,9 @@ def _e2e(args, scene, wl, N, stream):
             "host_pool_pinned": bool(pool.is_pinned()), "host_copy_gbs": round(h2d_gbs, 1),
             "host_copy_gbs_min_frame": round(min(rates), 1),
             "push_copy_gbs_p50": round(h2d / (float(statistics.median(push_ms)) * 1e-3) / 1e9, 1),
-            "frames_in_pool": n, "warmup": W,
+            "frames_in_pool": n, "pool": f"frames {t_first}-{t_first + n - 1}, played forward and backward",
+            "events_per_step": round(events_e2e / K, 1),
+            "same_frames_on_device_ms_per_step": round(dt_dev * 1e3 / K, 3), "warmup": W,
             "form": "precision, pinned host FP16/BF16 frames; events of frame s read after frame s + 1 is pushed"}
 
 
