@@ -222,14 +222,16 @@ def _frames_timed(W, K, F):
     return f"{W % F}-{F - 1}, then 0-{(W + K - 1) % F} with a reset ({K} steps)"
 
 
-def _timed_run(sim, frames, W, K, stream, drain_every=8, sink=None, profile=True):
+def _timed_run(sim, frames, W, K, stream, sink=None, profile=True):
     """W untimed warm-up steps, then exactly K timed steps (frame index wraps
-    with a reset to frame 0).  Events are drained into the device buffer
-    `sink` every `drain_every` steps (that drain synchronises, as a consumer
-    would).  Returns (ms, profile, events) where the profile carries the
-    regression work counted inside the timed region and, with `profile`, the
-    per-kernel CUDA-event times (whose event records add their own gaps, so
-    the step time is taken from a pass without them)."""
+    with a reset to frame 0).  Every step reads the previous frame's events
+    into the device buffer `sink`, as a consumer would, through
+    esim_ad_events_frame: the host waits for that frame's event writer only,
+    while the frame just pushed runs; the last drain closes the timed region.
+    Returns (ms, profile, events) where the profile carries the regression
+    work counted inside the timed region and, with `profile`, the per-kernel
+    CUDA-event times (whose event records add their own gaps, so the step time
+    is taken from a pass without them)."""
     import torch
     F = len(frames)
     acc = {"nb": 0, "reg": 0, "ev": 0}
@@ -250,8 +252,8 @@ def _timed_run(sim, frames, W, K, stream, drain_every=8, sink=None, profile=True
             drain()
             sim.reset()
         sim.push(frames[idx])
-        if (s + 1) % drain_every == 0:
-            drain()
+        if idx > 0:
+            acc["ev"] += sim.events_frame_into(idx - 1, sink)
 
     for s in range(W):
         step(s, False)
@@ -467,7 +469,9 @@ def run_ours(args):
                    "width": Wd, "height": H, "radius": wl["r"], "T": wl["T"], "C": wl["C"],
                    "spp": scfg.spp, "sequence_frames": F,
                    "frames_timed": _frames_timed(args.warmup, K, n_gen),
-                   "l2": "inputs larger than L2: each step reads a distinct frame of the sequence"},
+                   "l2": "inputs larger than L2: each step reads a distinct frame of the sequence",
+                   "drain": "each step reads the previous frame's events into a device buffer "
+                            "(esim_ad_events_frame); the last frame's drain closes the timed region"},
         "exhaustive": form("mixed_exhaustive"),
         "fp32_form": {"adaptive": form("fp32_adaptive"), "exhaustive": form("fp32_exhaustive")},
         "speedup_adaptive_vs_exhaustive": round(value / rate("mixed_exhaustive"), 3),
@@ -481,7 +485,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = _e2e(args, scene, wl, N, stream)
+        line["e2e"] = _e2e(args, wl, N, stream, sframes)
     if rank == 0 and not args.no_paper_density:
         line["paper_density"] = _paper_density(args, dev, stream, fp32_peak, sink)
     if rank == 0 and not args.no_diff:
@@ -1049,129 +1053,108 @@ def _dequantised_cpu(sf):
             "depth": q[3].contiguous(), "albedo": q[4:7].contiguous()}
 
 
-def _pingpong(s: int, n: int) -> int:
-    """Frame index of step s over n frames played forward then backward
-    (0, 1, .., n-1, n-2, .., 1, 0, 1, ..): the motion reverses instead of
-    jumping back, so every step keeps the sequence's flag density."""
-    if n < 2:
-        return 0
-    p = s % (2 * n - 2)
-    return p if p < n else 2 * n - 2 - p
-
-
-def _e2e(args, scene, wl, N, stream):
+def _e2e(args, wl, N, stream, sframes):
     """Same metric through the public API with pinned host buffers (precision
-    form): every step copies a frame in (inside esim_ad_push_frame) and drains
-    a frame's events into a pinned host buffer (esim_ad_events_frame), one
-    frame behind the push.  The host frames are a pinned pool of 8 distinct
-    frames from the middle of the sequence played forward and backward; the
-    same loop over the same frames held on the device is timed beside it."""
+    form), over the headline's own frames played forward: every step copies
+    its frame in from its own pinned host buffer (inside esim_ad_push_frame)
+    and drains a frame's events into a pinned host buffer (esim_ad_events_frame),
+    one frame behind the push.  The same loop over the same frames held on the
+    device is timed beside it, so the difference is the cost of the copies."""
+    import gc
     import torch
     import paper_2303_02608_gb300 as lib
     from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, SimConfig, Simulator
     W = max(args.warmup, 8)   # pinned pages and copy paths settle over the first steps
-    K = min(args.steps, args.e2e_steps)
-    # a pool of 8 distinct frames, cycled: 265 MB of pinned memory, allocated
-    # just before use (a pool of every timed frame reached ~1 GB, and copies
-    # from parts of such a pool were measured 5-10x slower than from its start)
-    n = min(scene.cfg.frames, W + K, 8)
-    # eight consecutive frames from the middle of the sequence, where the
-    # scene's motion and flag density are those of the timed frames at large
-    t_first = max(0, scene.cfg.frames // 2 - n // 2)
-    # all host frames in one pinned allocation (views per frame and plane)
-    dev0 = _storage_frames([{k: v for k, v in scene.frame(t_first, "cuda").items()
-                             if k in ("radiance", "normal", "albedo", "depth")}])[0]
-    sizes = {k: v.numel() * v.element_size() for k, v in dev0.items()}
-    per = sum(sizes.values())
-    pool = torch.empty(n * per, dtype=torch.uint8, pin_memory=True)
+    K = min(args.steps, args.e2e_steps, len(sframes) - W)
+    # one pinned buffer per frame and plane, filled before the timed region
     host = []
-    for t in range(n):
-        f = scene.frame(t_first + t, "cuda")
-        sf = _storage_frames([{k: f[k] for k in ("radiance", "normal", "albedo", "depth")}])[0]
-        frame, off = {}, t * per
-        for k, v in sf.items():
-            view = pool[off:off + sizes[k]].view(v.dtype).view(v.shape)
-            view.copy_(v)
-            frame[k] = view
-            off += sizes[k]
+    for t in range(W + K):
+        frame = {}
+        for k, v in sframes[t].items():
+            h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+            h.copy_(v)
+            frame[k] = h
         host.append(frame)
-    Wd, H = scene.cfg.width, scene.cfg.height
-    sim = Simulator(SimConfig(width=Wd, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
-                              mode=ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=1 << 24,
-                              radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
-                              precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE), stream)
-    # the events land in a pinned host buffer of the caller's (the step's result read)
-    ev_host = torch.empty((1 << 22) * 12, dtype=torch.uint8, pin_memory=True)
-    for s in range(W):
-        sim.push(host[_pingpong(s, n)])
-        sim.events_into(ev_host)
+    # one untimed pass of host-to-device copies over every buffer: the first
+    # DMA read of newly pinned pages was measured up to 5x slower (0.92 ms for
+    # a 33 MB frame against 0.18 ms), once per page; a caller's frame buffers
+    # are reused, so the timed steps read warm ones
+    scratch = {k: torch.empty_like(v) for k, v in sframes[0].items()}
+    for frame in host:
+        for k, v in frame.items():
+            scratch[k].copy_(v, non_blocking=True)
     torch.cuda.synchronize()
-    import gc
-    gc.collect()
-    gc.disable()   # no collector pauses inside the timed loop
-    try:
-        # one frame of lookahead: step s pushes frame s (its host-to-device
-        # copy lands while frame s - 1 computes) and then reads frame s - 1's
-        # events (esim_ad_events_frame waits for that frame's writer only);
-        # the last step's read closes the timed region
-        t0 = time.perf_counter()
-        d2h = 0
-        step_ms, push_ms = [], []
-        for s in range(W, W + K):
-            ts = time.perf_counter()
-            sim.push(host[_pingpong(s, n)])
-            tm = time.perf_counter()
-            if s > W:
-                d2h += sim.events_frame_into(s - 1, ev_host) * 12 + 64
-            te = time.perf_counter()
-            push_ms.append((tm - ts) * 1e3)
-            step_ms.append((te - ts) * 1e3)
-        d2h += sim.events_frame_into(W + K - 1, ev_host) * 12 + 64
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        events_e2e = (d2h - 64 * K) // 12
-        # the same loop over the same frames resident on the device (no copy
-        # in, the same drains): the device-side rate of this exact work
-        dev_pool = [{k: v.cuda() for k, v in f.items()} for f in host]
-        sim.reset()
+    del scratch
+    H, Wd = sframes[0]["radiance"].shape
+    ev_host = torch.empty((1 << 22) * 12, dtype=torch.uint8, pin_memory=True)
+
+    def run(frames):
+        sim = Simulator(SimConfig(width=Wd, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
+                                  mode=ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=1 << 24,
+                                  radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
+                                  precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE), stream)
         for s in range(W):
-            sim.push(dev_pool[_pingpong(s, n)])
+            sim.push(frames[s])
             sim.events_into(ev_host)
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for s in range(W, W + K):
-            sim.push(dev_pool[_pingpong(s, n)])
-            if s > W:
-                sim.events_frame_into(s - 1, ev_host)
-        sim.events_frame_into(W + K - 1, ev_host)
-        torch.cuda.synchronize()
-        dt_dev = time.perf_counter() - t1
-        del dev_pool
-    finally:
-        gc.enable()
-    sim.close()
+        gc.collect()
+        gc.disable()   # no collector pauses inside the timed loop
+        try:
+            # one frame of lookahead: step s pushes frame s (a host frame's copy
+            # lands while frame s - 1 computes) and then reads frame s - 1's
+            # events (esim_ad_events_frame waits for that frame's writer only);
+            # the last step's read closes the timed region
+            d2h, events = 0, 0
+            step_ms, push_ms = [], []
+            t0 = time.perf_counter()
+            for s in range(W, W + K):
+                ts = time.perf_counter()
+                sim.push(frames[s])
+                tm = time.perf_counter()
+                if s > W:
+                    n = sim.events_frame_into(s - 1, ev_host)
+                    events += n
+                    d2h += n * 12 + 64
+                te = time.perf_counter()
+                push_ms.append((tm - ts) * 1e3)
+                step_ms.append((te - ts) * 1e3)
+            n = sim.events_frame_into(W + K - 1, ev_host)
+            events += n
+            d2h += n * 12 + 64
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        finally:
+            gc.enable()
+        sim.close()
+        return dt, d2h, events, step_ms, push_ms
+
+    dt, d2h, events, step_ms, push_ms = run(host)
+    dt_dev = run(sframes)[0]
     h2d = sum(v.numel() * v.element_size() for v in host[0].values())
-    # the host side's own copy rate from every frame of this pool, for reading the number
+    # the host side's own copy rate from a sample of the frames, for reading the number
     probe = torch.empty(h2d, dtype=torch.uint8, device="cuda")
-    torch.cuda.synchronize()
     rates = []
-    for t in range(n):
+    for t in range(0, W + K, max(1, (W + K) // 16)):
+        torch.cuda.synchronize()
         tc = time.perf_counter()
-        probe.copy_(pool[t * h2d:(t + 1) * h2d], non_blocking=True)
+        off = 0
+        for v in host[t].values():
+            nb = v.numel() * v.element_size()
+            probe[off:off + nb].copy_(v.view(-1).view(torch.uint8), non_blocking=True)
+            off += nb
         torch.cuda.synchronize()
         rates.append(h2d / (time.perf_counter() - tc) / 1e9)
-    h2d_gbs = float(statistics.median(rates))
-    del probe
+    del probe, host
     return {"value": round(N * K / dt, 1), "unit": UNIT, "steps": K, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": int(d2h / K), "ms_per_step": round(dt * 1e3 / K, 3),
             "step_ms_p50": round(float(statistics.median(step_ms)), 3),
             "step_ms_max": round(float(max(step_ms)), 3), "push_ms_p50": round(float(statistics.median(push_ms)), 3),
-            "host_pool_pinned": bool(pool.is_pinned()), "host_copy_gbs": round(h2d_gbs, 1),
-            "host_copy_gbs_min_frame": round(min(rates), 1),
-            "push_copy_gbs_p50": round(h2d / (float(statistics.median(push_ms)) * 1e-3) / 1e9, 1),
-            "frames_in_pool": n, "pool": f"frames {t_first}-{t_first + n - 1}, played forward and backward",
-            "events_per_step": round(events_e2e / K, 1),
-            "same_frames_on_device_ms_per_step": round(dt_dev * 1e3 / K, 3), "warmup": W,
+            "frames": f"{W}-{W + K - 1} of the sequence, forward, each from its own pinned buffer "
+                      f"(after {W} warm-up frames; every buffer read once by an untimed copy first)",
+            "events_per_step": round(events / K, 1),
+            "same_frames_on_device_ms_per_step": round(dt_dev * 1e3 / K, 3),
+            "host_copy_gbs": round(float(statistics.median(rates)), 1), "host_copy_gbs_min": round(min(rates), 1),
+            "push_copy_gbs_p50": round(h2d / (float(statistics.median(push_ms)) * 1e-3) / 1e9, 1), "warmup": W,
             "form": "precision, pinned host FP16/BF16 frames; events of frame s read after frame s + 1 is pushed"}
 
 
@@ -1228,7 +1211,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rects1080p")
-    ap.add_argument("--e2e-steps", type=int, default=117)
+    ap.add_argument("--e2e-steps", type=int, default=1 << 30)
     ap.add_argument("--event-capacity", type=int, default=1 << 27)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -27,11 +27,3 @@ def test_second_order_flop_constants():
     assert bench.FLOP_PER_SOLVE_2 == solve
     assert trailing == 2 * 55 * 56 * 57 // 6
 
-
-def test_pingpong_frame_order():
-    import bench
-    assert [bench._pingpong(s, 4) for s in range(12)] == [0, 1, 2, 3, 2, 1, 0, 1, 2, 3, 2, 1]
-    assert [bench._pingpong(s, 1) for s in range(3)] == [0, 0, 0]
-    seq = [bench._pingpong(s, 8) for s in range(40)]
-    assert all(abs(a - b) == 1 for a, b in zip(seq, seq[1:]))   # never a jump
-
