@@ -183,71 +183,102 @@ __global__ void __launch_bounds__(kTilePix, 2) fwd_kernel(AdjParams p)
     }
 }
 
-// Per centre: g_alpha * v' for the radiance gather, and the centre's share of
+// Per centre: g_alpha v' for the radiance gather, and the centre's share of
 // the bandwidth gradient (sum over its window of g_alpha (d alpha/d w_i) w_i u_ij^2).
-__global__ void __launch_bounds__(kTilePix, 2) bwd_center_kernel(AdjParams p)
+// Each thread takes kCtrRows centres stacked in one column, so every neighbour
+// record it loads (32 bytes) serves each of them whose window holds it; a
+// 128-thread CTA covers one 32 x 8 tile.
+constexpr int kCtrRows = 2;
+constexpr int kCtrThreads = kTilePix / kCtrRows;
+
+__global__ void __launch_bounds__(kCtrThreads, 4) bwd_center_kernel(AdjParams p)
 {
     const size_t N = (size_t)p.W * p.H;
     const int f = blockIdx.y;
     const int cx = (blockIdx.x % p.tiles_x) * kTileX + (threadIdx.x & 31);
-    const int cy = (blockIdx.x / p.tiles_x) * kTileY + (threadIdx.x >> 5);
-    const bool inside = cx < p.W && cy < p.H;
+    const int cy0 = (blockIdx.x / p.tiles_x) * kTileY + kCtrRows * (threadIdx.x >> 5);
+    float sf[7], s_c, s_px;
+    scales(p, sf, s_c, s_px);
     float gb[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (inside) {
-        float sf[7], s_c, s_px;
-        scales(p, sf, s_c, s_px);
-        const size_t ci = (size_t)cy * p.W + cx;
-        const float ga = p.g_alpha[(size_t)f * N + ci];
-        const float* sv = p.saved + (size_t)f * 20 * N + ci;
-        float th[NZ], v[NZ];
+    float ga[kCtrRows], lvpt[kCtrRows], th[kCtrRows][NZ], v[kCtrRows][NZ], cf[kCtrRows][7];
+    bool active[kCtrRows];
+    bool any = false;
 #pragma unroll
-        for (int k = 0; k < NZ; ++k) {
-            th[k] = sv[(size_t)k * N];
-            v[k] = sv[(size_t)(NZ + k) * N];
+    for (int k = 0; k < kCtrRows; ++k) {
+        const int cy = cy0 + k;
+        active[k] = false;
+        ga[k] = 0.0f;
+        lvpt[k] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) th[k][i] = v[k][i] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) cf[k][j] = 0.0f;
+        if (cx >= p.W || cy >= p.H) continue;
+        const size_t ci = (size_t)cy * p.W + cx;
+        ga[k] = p.g_alpha[(size_t)f * N + ci];
+        const float* sv = p.saved + (size_t)f * 20 * N + ci;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            th[k][i] = sv[(size_t)i * N];
+            v[k][i] = sv[(size_t)(NZ + i) * N];
         }
         float4* g = p.gv + (size_t)f * 3 * N + ci;
-        g[0] = make_float4(ga * v[0], ga * v[1], ga * v[2], ga * v[3]);
-        g[N] = make_float4(ga * v[4], ga * v[5], ga * v[6], ga * v[7]);
-        g[2 * N] = make_float4(ga * v[8], ga * v[9], 0.0f, 0.0f);
-        if (ga != 0.0f) {
-            // lambda v^T P theta in natural units
-            float vpt = (s_c * s_c) * (v[1] * th[1] + v[2] * th[2]);
+        g[0] = make_float4(ga[k] * v[k][0], ga[k] * v[k][1], ga[k] * v[k][2], ga[k] * v[k][3]);
+        g[N] = make_float4(ga[k] * v[k][4], ga[k] * v[k][5], ga[k] * v[k][6], ga[k] * v[k][7]);
+        g[2 * N] = make_float4(ga[k] * v[k][8], ga[k] * v[k][9], 0.0f, 0.0f);
+        if (ga[k] == 0.0f) continue;
+        // lambda v^T P theta in natural units
+        float vpt = (s_c * s_c) * (v[k][1] * th[k][1] + v[k][2] * th[k][2]);
 #pragma unroll
-            for (int j = 0; j < 7; ++j) vpt = fmaf(sf[j] * sf[j], v[3 + j] * th[3 + j], vpt);
-            const float lvpt = p.ridge * vpt;
-            const float4 c0 = p.packed[(size_t)f * 2 * N + ci];
-            const float4 c1 = p.packed[((size_t)f * 2 + 1) * N + ci];
-            const float cf[7] = {c0.y * sf[0], c0.z * sf[1], c0.w * sf[2], c1.x * sf[3],
-                                 c1.y * sf[4], c1.z * sf[5], c1.w * sf[6]};
-            const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
-            const int dylo = max(-p.r, -cy), dyhi = min(p.r, p.H - 1 - cy);
-            for (int tau = max(0, f - p.T + 1); tau <= f; ++tau) {
-                const float4* P0 = p.packed + (size_t)tau * 2 * N + ci;
-                const float4* P1 = P0 + N;
-                for (int oy = dylo; oy <= dyhi; ++oy) {
-                    const float u2 = (float)oy * s_px;
-                    for (int ox = dxlo; ox <= dxhi; ++ox) {
-                        const float u1 = (float)ox * s_px;
-                        const int d = oy * p.W + ox;
-                        const float4 h0 = __ldg(P0 + d), h1 = __ldg(P1 + d);
-                        const float fv[7] = {h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+        for (int j = 0; j < 7; ++j) vpt = fmaf(sf[j] * sf[j], v[k][3 + j] * th[k][3 + j], vpt);
+        lvpt[k] = p.ridge * vpt;
+        const float4 c0 = p.packed[(size_t)f * 2 * N + ci];
+        const float4 c1 = p.packed[((size_t)f * 2 + 1) * N + ci];
+        cf[k][0] = c0.y * sf[0];
+        cf[k][1] = c0.z * sf[1];
+        cf[k][2] = c0.w * sf[2];
+        cf[k][3] = c1.x * sf[3];
+        cf[k][4] = c1.y * sf[4];
+        cf[k][5] = c1.z * sf[5];
+        cf[k][6] = c1.w * sf[6];
+        active[k] = true;
+        any = true;
+    }
+    if (any) {
+        // neighbours (cx + ox, ny) inside the image, in the window of some centre row
+        const int dxlo = max(-p.r, -cx), dxhi = min(p.r, p.W - 1 - cx);
+        const int nylo = max(0, cy0 - p.r), nyhi = min(p.H - 1, cy0 + kCtrRows - 1 + p.r);
+        for (int tau = max(0, f - p.T + 1); tau <= f; ++tau) {
+            const float4* P0 = p.packed + (size_t)tau * 2 * N;
+            const float4* P1 = P0 + N;
+            for (int ny = nylo; ny <= nyhi; ++ny) {
+                for (int ox = dxlo; ox <= dxhi; ++ox) {
+                    const float u1 = (float)ox * s_px;
+                    const size_t ni = (size_t)ny * p.W + cx + ox;
+                    const float4 h0 = __ldg(P0 + ni), h1 = __ldg(P1 + ni);
+                    const float fv[7] = {h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+                    for (int k = 0; k < kCtrRows; ++k) {
+                        const int oy = ny - (cy0 + k);
+                        if (!active[k] || oy < -p.r || oy > p.r) continue;
+                        const float u2 = (float)oy * s_px;
                         float u[7];
                         float en = -fmaf(u1, u1, u2 * u2);
 #pragma unroll
                         for (int j = 0; j < 7; ++j) {
-                            u[j] = fmaf(fv[j], sf[j], -cf[j]);
+                            u[j] = fmaf(fv[j], sf[j], -cf[k][j]);
                             en = fmaf(-u[j], u[j], en);
                         }
                         const float w = ex2_approx(en);
-                        float fit = th[0] + th[1] * u1 + th[2] * u2;
-                        float vz = v[0] + v[1] * u1 + v[2] * u2;
+                        float fit = th[k][0] + th[k][1] * u1 + th[k][2] * u2;
+                        float vz = v[k][0] + v[k][1] * u1 + v[k][2] * u2;
 #pragma unroll
                         for (int j = 0; j < 7; ++j) {
-                            fit = fmaf(th[3 + j], u[j], fit);
-                            vz = fmaf(v[3 + j], u[j], vz);
+                            fit = fmaf(th[k][3 + j], u[j], fit);
+                            vz = fmaf(v[k][3 + j], u[j], vz);
                         }
-                        const float dadw = fmaf(vz, h0.x - fit, -lvpt);
-                        const float c = ga * dadw * w;
+                        const float dadw = fmaf(vz, h0.x - fit, -lvpt[k]);
+                        const float c = ga[k] * dadw * w;
 #pragma unroll
                         for (int j = 0; j < 7; ++j) gb[j] = fmaf(c, u[j] * u[j], gb[j]);
                     }
@@ -256,11 +287,11 @@ __global__ void __launch_bounds__(kTilePix, 2) bwd_center_kernel(AdjParams p)
         }
     }
     // block tree sum in a fixed order -> one partial per block
-    __shared__ float red[kTilePix][8];
+    __shared__ float red[kCtrThreads][8];
 #pragma unroll
     for (int j = 0; j < 7; ++j) red[threadIdx.x][j] = gb[j];
     __syncthreads();
-    for (int s = kTilePix / 2; s > 0; s >>= 1) {
+    for (int s = kCtrThreads / 2; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s)
 #pragma unroll
             for (int j = 0; j < 7; ++j) red[threadIdx.x][j] += red[threadIdx.x + s][j];
@@ -291,67 +322,95 @@ __global__ void __launch_bounds__(kTilePix) bwd_bandwidth_kernel(AdjParams p, in
 
 // Per source pixel q of frame tau: dL/dy = sum over centres c (|c - q| <= r) of
 // frames t in [tau, tau + T - 1] of g_alpha_t(c) w v'_t(c)^T u, then dL/dE.
+// Each thread gathers for kSrcRows sources stacked in one column, so every
+// centre record it loads (two feature records and three g_alpha v' records,
+// 80 bytes) serves each of those sources whose window holds it: 2.8 pairs per
+// load at r = 3 instead of one.  A CTA covers 32 columns x 32 rows.
+constexpr int kSrcRows = 4;
+constexpr int kSrcTileY = kSrcRows * (kTilePix / 32);
+
 __global__ void __launch_bounds__(kTilePix, 2) bwd_source_kernel(AdjParams p)
 {
     const size_t N = (size_t)p.W * p.H;
     const int tau = blockIdx.y;
     const int qx = (blockIdx.x % p.tiles_x) * kTileX + (threadIdx.x & 31);
-    const int qy = (blockIdx.x / p.tiles_x) * kTileY + (threadIdx.x >> 5);
-    if (qx >= p.W || qy >= p.H) return;
+    const int qy0 = (blockIdx.x / p.tiles_x) * kSrcTileY + kSrcRows * (threadIdx.x >> 5);
+    if (qx >= p.W || qy0 >= p.H) return;
+    const int nrow = min(kSrcRows, p.H - qy0);
     float sf[7], s_c, s_px;
     scales(p, sf, s_c, s_px);
-    const size_t qi = (size_t)qy * p.W + qx;
-    const float4 q0 = p.packed[(size_t)tau * 2 * N + qi];
-    const float4 q1 = p.packed[((size_t)tau * 2 + 1) * N + qi];
-    const float qf[7] = {q0.y * sf[0], q0.z * sf[1], q0.w * sf[2], q1.x * sf[3], q1.y * sf[4],
-                         q1.z * sf[5], q1.w * sf[6]};
-    // centres c = q - o: the neighbour offset of q seen from c is o
+    float qf[kSrcRows][7], gy[kSrcRows];
+#pragma unroll
+    for (int s = 0; s < kSrcRows; ++s) {
+        gy[s] = 0.0f;
+        const size_t qi = (size_t)(qy0 + min(s, nrow - 1)) * p.W + qx;
+        const float4 q0 = p.packed[(size_t)tau * 2 * N + qi];
+        const float4 q1 = p.packed[((size_t)tau * 2 + 1) * N + qi];
+        qf[s][0] = q0.y * sf[0];
+        qf[s][1] = q0.z * sf[1];
+        qf[s][2] = q0.w * sf[2];
+        qf[s][3] = q1.x * sf[3];
+        qf[s][4] = q1.y * sf[4];
+        qf[s][5] = q1.z * sf[5];
+        qf[s][6] = q1.w * sf[6];
+    }
+    // centres c = q - o (o the neighbour offset of q seen from c) inside the
+    // image: columns qx - ox, rows cy with |qy - cy| <= r for some source row
     const int oxlo = max(-p.r, qx - (p.W - 1)), oxhi = min(p.r, qx);
-    const int oylo = max(-p.r, qy - (p.H - 1)), oyhi = min(p.r, qy);
-    float gy = 0.0f;
+    const int cylo = max(0, qy0 - p.r), cyhi = min(p.H - 1, qy0 + nrow - 1 + p.r);
     const int t1 = min(p.F - 1, tau + p.T - 1);
     for (int t = tau; t <= t1; ++t) {
         const float4* C0 = p.packed + (size_t)t * 2 * N;
         const float4* C1 = C0 + N;
         const float4* G = p.gv + (size_t)t * 3 * N;
-        for (int oy = oylo; oy <= oyhi; ++oy) {
-            const float u2 = (float)oy * s_px;
+        for (int cy = cylo; cy <= cyhi; ++cy) {
             for (int ox = oxlo; ox <= oxhi; ++ox) {
                 const float u1 = (float)ox * s_px;
-                const size_t ci = (size_t)(qy - oy) * p.W + (qx - ox);
+                const size_t ci = (size_t)cy * p.W + (qx - ox);
                 const float4 c0 = __ldg(C0 + ci), c1 = __ldg(C1 + ci);
-                const float cfv[7] = {c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-                float u[7];
-                float en = -fmaf(u1, u1, u2 * u2);
-#pragma unroll
-                for (int j = 0; j < 7; ++j) {
-                    u[j] = fmaf(-cfv[j], sf[j], qf[j]);
-                    en = fmaf(-u[j], u[j], en);
-                }
-                const float w = ex2_approx(en);
                 const float4 g0 = __ldg(G + ci), g1 = __ldg(G + N + ci), g2 = __ldg(G + 2 * N + ci);
-                float vz = g0.x + g0.y * u1 + g0.z * u2;
-                vz = fmaf(g0.w, u[0], vz);
-                vz = fmaf(g1.x, u[1], vz);
-                vz = fmaf(g1.y, u[2], vz);
-                vz = fmaf(g1.z, u[3], vz);
-                vz = fmaf(g1.w, u[4], vz);
-                vz = fmaf(g2.x, u[5], vz);
-                vz = fmaf(g2.y, u[6], vz);
-                gy = fmaf(w, vz, gy);
+                const float cfv[7] = {c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int s = 0; s < kSrcRows; ++s) {
+                    const int oy = qy0 + s - cy;   // the same for the whole warp
+                    if (s >= nrow || oy < -p.r || oy > p.r) continue;
+                    const float u2 = (float)oy * s_px;
+                    float u[7];
+                    float en = -fmaf(u1, u1, u2 * u2);
+#pragma unroll
+                    for (int j = 0; j < 7; ++j) {
+                        u[j] = fmaf(-cfv[j], sf[j], qf[s][j]);
+                        en = fmaf(-u[j], u[j], en);
+                    }
+                    const float w = ex2_approx(en);
+                    float vz = g0.x + g0.y * u1 + g0.z * u2;
+                    vz = fmaf(g0.w, u[0], vz);
+                    vz = fmaf(g1.x, u[1], vz);
+                    vz = fmaf(g1.y, u[2], vz);
+                    vz = fmaf(g1.z, u[3], vz);
+                    vz = fmaf(g1.w, u[4], vz);
+                    vz = fmaf(g2.x, u[5], vz);
+                    vz = fmaf(g2.y, u[6], vz);
+                    gy[s] = fmaf(w, vz, gy[s]);
+                }
             }
         }
     }
     const float* rad = p.radiance + (size_t)tau * (p.rgb ? 3 : 1) * N;
     float* grad = p.g_radiance + (size_t)tau * (p.rgb ? 3 : 1) * N;
-    if (p.rgb) {
-        const float Y = 0.2126f * rad[qi] + 0.7152f * rad[N + qi] + 0.0722f * rad[2 * N + qi];
-        const float gY = gy / (Y + p.log_eps);
-        grad[qi] = 0.2126f * gY;
-        grad[N + qi] = 0.7152f * gY;
-        grad[2 * N + qi] = 0.0722f * gY;
-    } else {
-        grad[qi] = gy / (rad[qi] + p.log_eps);
+#pragma unroll
+    for (int s = 0; s < kSrcRows; ++s) {
+        if (s >= nrow) break;
+        const size_t qi = (size_t)(qy0 + s) * p.W + qx;
+        if (p.rgb) {
+            const float Y = 0.2126f * rad[qi] + 0.7152f * rad[N + qi] + 0.0722f * rad[2 * N + qi];
+            const float gY = gy[s] / (Y + p.log_eps);
+            grad[qi] = 0.2126f * gY;
+            grad[N + qi] = 0.7152f * gY;
+            grad[2 * N + qi] = 0.0722f * gY;
+        } else {
+            grad[qi] = gy[s] / (rad[qi] + p.log_eps);
+        }
     }
 }
 
@@ -454,8 +513,9 @@ extern "C" esim_ad_status esim_ad_wlr_backward(const esim_ad_wlr_desc* d, const 
     p.g_bandwidth = g_bandwidth;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const dim3 grid(L.n_tiles, d->sequence);
-    bwd_center_kernel<<<grid, kTilePix, 0, s>>>(p);
+    bwd_center_kernel<<<grid, kCtrThreads, 0, s>>>(p);
     bwd_bandwidth_kernel<<<1, kTilePix, 0, s>>>(p, L.n_blocks);
-    bwd_source_kernel<<<grid, kTilePix, 0, s>>>(p);
+    const dim3 grid_src(L.tiles_x * ((d->height + kSrcTileY - 1) / kSrcTileY), d->sequence);
+    bwd_source_kernel<<<grid_src, kTilePix, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? ESIM_AD_OK : ESIM_AD_ECUDA;
 }
