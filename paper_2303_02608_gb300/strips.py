@@ -10,13 +10,21 @@ k+1, and receives the neighbours' rows into its halo; the older frames' halo
 rows are already in every ring from their own frames.  That is 2 r W records
 of the new frame per internal boundary (32 bytes each in the FP32 ring, 16 in
 the mixed one: about 0.86 MB per boundary at 1920 wide, r = 7, FP32).  The
-test, the regression and the emission are pixel-local, so each rank then runs
-them on its owned rows only; the event lists, each in (row, column, repeat)
-order, concatenate in rank order into the whole image's canonical order.
+test, the regression and the emission are pixel-local, so an owned pixel's
+results depend on the held rows only; the owned rows' event lists, each in
+(row, column, repeat) order, concatenate in rank order into the whole image's
+canonical order.
 
 The exchange is written against torch.distributed point-to-point calls (NCCL
 between GPUs; gloo on CPU for the tests), on records laid out
 [planes][rows][width] with the halo rows first and last.
+
+StripSimulator is one rank's simulator: a context over its held rows, fed
+the held rows of each frame (its own rows plus the halo rows that the
+exchange delivers), whose results are kept for the owned rows only.  The
+halo rows are converted, tested and regressed like the others (their windows
+are clipped at the strip's edge, so their results are discarded); that costs
+2 r rows of extra work per internal boundary.
 """
 from __future__ import annotations
 
@@ -81,3 +89,56 @@ def merge_events(per_rank: list, row_offsets: list):
     # frame-major: rank order already gives row order within a frame
     order = np.argsort(allev["frame"], kind="stable")
     return allev[order]
+
+
+def held_frame(frame: dict, rows: dict) -> dict:
+    """The held rows [lo - top, hi + bottom) of a whole frame's planes
+    ([C][H][W] or [H][W] tensors), each made contiguous."""
+    a, b = rows["held"]
+    return {k: v[..., a:b, :].contiguous() for k, v in frame.items() if v is not None}
+
+
+class StripSimulator:
+    """Rank `rank` of `world` in the strip split of one sequence of cfg.height
+    rows: a Simulator over the held rows, reporting the owned rows.
+
+    push() takes the held rows of a frame (held_frame() cuts them out of a
+    whole frame; a multi-GPU run assembles them from its own rows and the halo
+    exchange).  events() returns the owned rows' events with y relative to the
+    first owned row (merge_events() with offsets lo joins the ranks);
+    denoised() the owned rows of alpha and of the flags."""
+
+    def __init__(self, cfg, world: int, rank: int, stream=None):
+        from dataclasses import replace
+        from . import Simulator
+        self.rows = strip_rows(cfg.height, world, rank, cfg.radius)
+        a, b = self.rows["held"]
+        self.cfg = replace(cfg, height=b - a)
+        self.sim = Simulator(self.cfg, stream)
+        self._own = (self.rows["top"], self.rows["top"] + self.rows["hi"] - self.rows["lo"])
+
+    def close(self):
+        self.sim.close()
+
+    def push(self, held: dict) -> None:
+        self.sim.push(held)
+
+    def events(self):
+        ev = self.sim.events()
+        r0, r1 = self._own
+        keep = (ev["y"] >= r0) & (ev["y"] < r1)
+        out = ev[keep]
+        out["y"] = out["y"] - r0
+        return out
+
+    def denoised(self):
+        alpha, flags = self.sim.denoised()
+        r0, r1 = self._own
+        return alpha[r0:r1], flags[r0:r1]
+
+    def set_state(self, l_last, beta, xc) -> None:
+        """Per-pixel model of the held rows from whole-image arrays
+        ([H*W], [H*W][7], [H*W][7], as Simulator.get_state returns them)."""
+        a, b = self.rows["held"]
+        W = self.cfg.width
+        self.sim.set_state(l_last[a * W:b * W], beta[a * W:b * W], xc[a * W:b * W])

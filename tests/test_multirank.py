@@ -115,3 +115,79 @@ def test_strip_rows_and_event_merge():
     key = m["frame"].astype(np.int64) * 1000 + m["y"].astype(np.int64) * 10 + m["x"]
     assert np.all(np.diff(key) > 0) and len(m) == 5 and set(m["y"]) == {0, 4, 1, 5, 7}
 
+
+
+class _WindowContext:
+    """Stand-in for a simulation context on the CPU: alpha is the mean of
+    channel 0 over each pixel's (2r+1)^2 window clipped at the held rows'
+    edges (a pixel-local function of its window, as the regression is), and
+    a pixel emits one event of polarity sign(alpha - 0.5) when
+    |alpha - 0.5| > 0.015."""
+
+    def __init__(self, cfg, stream=None):
+        self.cfg = cfg
+        self.ev = []
+        self.t = 0
+
+    def close(self):
+        pass
+
+    def push(self, frame):
+        import numpy as np
+        from paper_2303_02608_gb300 import EVENT_DTYPE
+        x = frame["radiance"][0].numpy().astype(np.float64)
+        H, W = x.shape
+        assert (H, W) == (self.cfg.height, self.cfg.width)
+        r = self.cfg.radius
+        a = np.zeros_like(x)
+        for y in range(H):
+            for c in range(W):
+                a[y, c] = x[max(0, y - r):y + r + 1, max(0, c - r):c + r + 1].mean()
+        self.alpha = torch.from_numpy(a)
+        ys, xs = np.nonzero(np.abs(a - 0.5) > 0.015)
+        ev = np.zeros(len(ys), EVENT_DTYPE)
+        ev["frame"], ev["x"], ev["y"] = self.t, xs, ys
+        ev["polarity"] = np.sign(a[ys, xs] - 0.5)
+        self.ev.append(ev)
+        self.t += 1
+
+    def events(self):
+        import numpy as np
+        out = np.concatenate(self.ev)
+        self.ev = []
+        return out
+
+    def denoised(self):
+        return self.alpha, torch.ones_like(self.alpha, dtype=torch.uint8)
+
+
+@pytest.mark.parametrize("world,H,r", [(2, 37, 3), (3, 40, 5), (4, 29, 7)])
+def test_strip_simulators_reproduce_the_whole_frame(world, H, r, monkeypatch):
+    """StripSimulator's row bookkeeping on the CPU, with a stand-in context
+    whose results are pixel-local functions of clipped windows: the held
+    rows cut from each frame, the owned rows kept, and the merged events,
+    equal the whole frame's for every split."""
+    import numpy as np
+    import paper_2303_02608_gb300 as m
+    from paper_2303_02608_gb300 import SimConfig
+    from paper_2303_02608_gb300.strips import StripSimulator, held_frame, merge_events
+    monkeypatch.setattr(m, "Simulator", _WindowContext)
+    W = 13
+    cfg = SimConfig(width=W, height=H, radius=r)
+    full = m.Simulator(cfg)
+    strips = [StripSimulator(cfg, world, k) for k in range(world)]
+    g = torch.Generator().manual_seed(3)
+    for t in range(3):
+        fr = {"radiance": torch.rand(3, H, W, generator=g), "depth": torch.rand(H, W, generator=g)}
+        full.push(fr)
+        for s in strips:
+            s.push(held_frame(fr, s.rows))
+        a_f, _ = full.denoised()
+        for s in strips:
+            a_s, f_s = s.denoised()
+            assert torch.equal(a_s, a_f[s.rows["lo"]:s.rows["hi"]])
+    whole = full.events()
+    merged = merge_events([s.events() for s in strips], [s.rows["lo"] for s in strips])
+    assert len(whole) > 0
+    for f in ("frame", "x", "y", "polarity"):
+        assert np.array_equal(merged[f], whole[f]), f
