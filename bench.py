@@ -568,7 +568,7 @@ def _paper_density(args, dev, stream, fp32_peak, sink):
     return out
 
 
-def _batching(dev, fp32_peak, warmup=10, steps=12, prof_steps=4):
+def _batching(dev, fp32_peak, warmup=10, steps=12, prof_steps=4, n_seq=48):
     """The batching workload: 48 sequences (resolutions from {256^2, 640x480,
     1280x720, 1920x1080}, 32-128 frames, 2-16 spp, 15x15x5 window, C = 0.15),
     stepped together through the batch API (one graph per step), against the
@@ -576,11 +576,12 @@ def _batching(dev, fp32_peak, warmup=10, steps=12, prof_steps=4):
     before each step's timed region.  The warm-up covers the start step and
     the nine autotuning steps (tile shape x lanes per pixel), so the timed
     steps replay the tuned graph; a few more steps with per-kernel timing give
-    the regression's FP32 roofline."""
+    the regression's FP32 roofline.  n_seq < 48 takes the first n_seq of
+    those sequences (a small case for profiling)."""
     import torch
     from paper_2303_02608_gb300 import Batch, SimConfig, Simulator
     from scenes import Scene, batch_configs
-    cfgs = batch_configs(48, seed=0)
+    cfgs = batch_configs(48, seed=0)[:n_seq]
     scenes = [Scene(c) for c in cfgs]
     sims = [SimConfig(width=c.width, height=c.height, radius=7, frames=5, contrast=0.15,
                       event_capacity=1 << 24) for c in cfgs]
@@ -634,7 +635,7 @@ def _batching(dev, fp32_peak, warmup=10, steps=12, prof_steps=4):
     wlr_ms = prof["ms"]["wlr_emit"]
     ach = (nb * FLOP_PER_NEIGHBOUR + rg * FLOP_PER_SOLVE) / (wlr_ms * 1e-3) / 1e12
     ach145 = (nb * 145 + rg * 1000) / (wlr_ms * 1e-3) / 1e12
-    return {"workload": "48 sequences, resolutions {256^2, 640x480, 1280x720, 1920x1080}, 32-128 frames, "
+    return {"workload": f"{n_seq} sequences, resolutions {{256^2, 640x480, 1280x720, 1920x1080}}, 32-128 frames, "
                         "2-16 spp, 15x15x5 window, C=0.15, fp32",
             "value": round(px_total / (t_batch * 1e-3), 1), "unit": UNIT, "steps": steps,
             "steps_timed": f"{warmup}-{warmup + steps - 1}",
@@ -1221,18 +1222,28 @@ def main():
     ap.add_argument("--no-render", action="store_true")
     ap.add_argument("--no-paper-density", action="store_true")
     ap.add_argument("--no-second-order", action="store_true")
-    ap.add_argument("--form", choices=["second-order"], default=None,
+    ap.add_argument("--form", choices=["second-order", "differentiation", "batching"], default=None,
                     help="run only that form's measurement and print its JSON object")
+    ap.add_argument("--batch-sequences", type=int, default=48,
+                    help="with --form batching: the first N of the 48 sequences")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
-    elif args.form == "second-order":
+    elif args.form is not None:
+        if args.form == "batching" and not 1 <= args.batch_sequences <= 48:
+            ap.error("--batch-sequences must be in 1..48")
         import torch
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        print(json.dumps(_second_order(dev, _fp32_peak(dev), warmup=args.warmup)), flush=True)
+        if args.form == "second-order":
+            out = _second_order(dev, _fp32_peak(dev), warmup=args.warmup)
+        elif args.form == "differentiation":
+            out = _differentiation(dev, _fp32_peak(dev))
+        else:
+            out = _batching(dev, _fp32_peak(dev), n_seq=args.batch_sequences)
+        print(json.dumps(out), flush=True)
     else:
         run_ours(args)
 
