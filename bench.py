@@ -415,7 +415,7 @@ def run_ours(args):
         wlr_ms = prof["ms"]["wlr_emit"]
         flops = prof["neighbours_timed"] * FLOP_PER_NEIGHBOUR + prof["regressions_timed"] * FLOP_PER_SOLVE
         ach = flops / n_launch / (wlr_ms * 1e-3 / n_launch) / 1e12
-        # the same time at the survey's rounder count of 145 flop per neighbour
+        # the same time at a rounder count of 145 flop per neighbour (and 1000 per solve)
         ach145 = (prof["neighbours_timed"] * 145 + prof["regressions_timed"] * 1000) / (wlr_ms * 1e-3) / 1e12
         return {"achieved": round(ach, 3), "frac": round(ach / fp32_peak, 4),
                 "frac_at_145_per_neighbour": round(ach145 / fp32_peak, 4),
