@@ -41,7 +41,7 @@ WORKLOADS = {
                           "over a textured background (6-px cells) panning 1.7 x 0.7 px/frame"),
 }
 
-# Algorithmic FP32 work of the regression (counted from the method, see DESIGN):
+# Algorithmic FP32 work of the regression, counted from the method (Eqs. 3-5):
 # per (pixel, neighbour) pair: 7 scaled feature differences (14), squared
 # distance (18), exp (1), w*z and w*y (10), Gram update 55 entries (100),
 # right-hand side 10 entries (19) -> 162 flop; per regressed pixel, the ridge,
@@ -651,6 +651,57 @@ def _batching(dev, fp32_peak, warmup=10, steps=12, prof_steps=4, n_seq=48):
             "graph_per_step": True}
 
 
+def _strips(dev, n_strips=8, warmup=3, steps=20, workload="rects1080p"):
+    """The strip split's per-rank work, measured on one GPU.  The headline's
+    adaptive precision-form frames are cut into n_strips strips of rows, each
+    with its r-row halo (StripSimulator), and every strip's context is timed
+    alone over the same frames as the whole frame's context, through the same
+    loop as the headline (previous frame's events drained into a device
+    buffer each step).  With one strip per GPU the slowest strip bounds the
+    per-frame time of an n_strips-GPU run, before the halo exchange (2 r W
+    ring records of the new frame per internal boundary per frame), which
+    needs more than one GPU and is not in these times."""
+    import torch
+    import paper_2303_02608_gb300 as lib
+    from paper_2303_02608_gb300 import SimConfig, Simulator
+    from paper_2303_02608_gb300.strips import StripSimulator, held_frame
+    from scenes import Scene
+    wl = WORKLOADS[workload]
+    scene = Scene(rank_scene(wl["scene"], 0))
+    W, H = scene.cfg.width, scene.cfg.height
+    sframes = _storage_frames(_gen_frames(scene, warmup + steps, dev))
+    stream = torch.cuda.current_stream()
+    cap = 1 << 22
+    sink = torch.empty(cap * 12, dtype=torch.uint8, device=dev)
+    cfg = SimConfig(width=W, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
+                    mode=lib.ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=cap,
+                    radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
+                    precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE)
+    whole = Simulator(cfg, stream)
+    ms_whole, _, ev_whole = _timed_run(whole, sframes, warmup, steps, stream, sink=sink, profile=False)
+    whole.close()
+    per = []
+    for k in range(n_strips):
+        s = StripSimulator(cfg, n_strips, k, stream)
+        held = [held_frame(f, s.rows) for f in sframes]
+        torch.cuda.synchronize()
+        ms, _, ev = _timed_run(s.sim, held, warmup, steps, stream, sink=sink, profile=False)
+        a, b = s.rows["held"]
+        per.append({"owned_rows": [s.rows["lo"], s.rows["hi"]], "held_rows": b - a,
+                    "ms_per_frame": round(ms / steps, 4), "events_held_rows": ev})
+        s.close()
+        del held
+    slowest = max(p["ms_per_frame"] for p in per)
+    return {"workload": f"{workload}: {wl['desc']}; adaptive, precision form; {n_strips} strips of rows",
+            "frames_timed": _frames_timed(warmup, steps, scene.cfg.frames),
+            "whole_frame_ms_per_frame": round(ms_whole / steps, 4),
+            "strips": per, "slowest_strip_ms_per_frame": slowest,
+            "projected_speedup": round(ms_whole / steps / slowest, 3),
+            "halo_rows_extra": round(sum(p["held_rows"] for p in per) / H - 1.0, 4),
+            "events_whole_frame": ev_whole,
+            "exchange": "not measured (one GPU): 2 r W records of the new frame per internal boundary"}
+
+
 def _events_to_counts(sink, n, counts):
     """Accumulate n 12-byte event records (frame, x | y << 16, polarity) from
     the device buffer `sink` into the signed count map counts [F][H][W]."""
@@ -1222,8 +1273,9 @@ def main():
     ap.add_argument("--no-render", action="store_true")
     ap.add_argument("--no-paper-density", action="store_true")
     ap.add_argument("--no-second-order", action="store_true")
-    ap.add_argument("--form", choices=["second-order", "differentiation", "batching"], default=None,
+    ap.add_argument("--form", choices=["second-order", "differentiation", "batching", "strips"], default=None,
                     help="run only that form's measurement and print its JSON object")
+    ap.add_argument("--strips", type=int, default=8, help="with --form strips: the number of strips")
     ap.add_argument("--batch-sequences", type=int, default=48,
                     help="with --form batching: the first N of the 48 sequences")
     args = ap.parse_args()
@@ -1241,6 +1293,8 @@ def main():
             out = _second_order(dev, _fp32_peak(dev), warmup=args.warmup)
         elif args.form == "differentiation":
             out = _differentiation(dev, _fp32_peak(dev))
+        elif args.form == "strips":
+            out = _strips(dev, n_strips=args.strips, warmup=args.warmup)
         else:
             out = _batching(dev, _fp32_peak(dev), n_seq=args.batch_sequences)
         print(json.dumps(out), flush=True)
