@@ -1,6 +1,7 @@
-"""Host arithmetic behind the benchmark's second-order roofline: the count of
-(pixel, neighbour) pairs of a dense sequence with clipped windows against brute
-force, and the per-unit flop constants against their itemised definitions."""
+"""Host logic of the benchmark: the count of (pixel, neighbour) pairs of a
+dense sequence with clipped windows against brute force, the second-order
+per-unit flop constants against their itemised definitions, the argument
+checks that run before any GPU work, and the timed-frames label."""
 import itertools
 
 import pytest
@@ -27,3 +28,23 @@ def test_second_order_flop_constants():
     assert bench.FLOP_PER_SOLVE_2 == solve
     assert trailing == 2 * 55 * 56 * 57 // 6
 
+
+@pytest.mark.parametrize("argv", [["--form", "batching", "--batch-sequences", "0"],
+                                  ["--form", "batching", "--batch-sequences", "49"],
+                                  ["--warmup", "2"]])
+def test_bench_rejects_bad_arguments_before_any_gpu_work(argv, monkeypatch, capsys):
+    import sys
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    with pytest.raises(SystemExit) as e:
+        bench.main()
+    assert e.value.code == 2
+    assert "error" in capsys.readouterr().err
+
+
+def test_frames_timed_label():
+    import bench
+    assert bench._frames_timed(3, 20, 240) == "3-22"
+    assert bench._frames_timed(5, 20, 240) == "5-24"
+    assert bench._frames_timed(3, 237, 240) == "3-239"
+    assert bench._frames_timed(3, 240, 240).startswith("3-239, then 0-2 with a reset")
