@@ -660,7 +660,10 @@ def _strips(dev, n_strips=8, warmup=3, steps=20, workload="rects1080p"):
     buffer each step).  With one strip per GPU the slowest strip bounds the
     per-frame time of an n_strips-GPU run, before the halo exchange (2 r W
     ring records of the new frame per internal boundary per frame), which
-    needs more than one GPU and is not in these times."""
+    needs more than one GPU and is not in these times.  A second, profiled
+    pass over the same frames gives each context's per-kernel device time
+    per frame (their sum against the step time separates the GPU's work from
+    per-step costs outside the kernels)."""
     import torch
     import paper_2303_02608_gb300 as lib
     from paper_2303_02608_gb300 import SimConfig, Simulator
@@ -677,8 +680,14 @@ def _strips(dev, n_strips=8, warmup=3, steps=20, workload="rects1080p"):
                     mode=lib.ESIM_AD_ADAPTIVE, rgb=wl["rgb"], event_capacity=cap,
                     radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
                     precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE)
+    def kernel_ms(sim, frames):
+        sim.reset()
+        _, prof, _ = _timed_run(sim, frames, warmup, steps, stream, sink=sink, profile=True)
+        return {k: round(v / steps, 4) for k, v in prof["ms"].items()}
+
     whole = Simulator(cfg, stream)
     ms_whole, _, ev_whole = _timed_run(whole, sframes, warmup, steps, stream, sink=sink, profile=False)
+    kms_whole = kernel_ms(whole, sframes)
     whole.close()
     per = []
     for k in range(n_strips):
@@ -688,13 +697,15 @@ def _strips(dev, n_strips=8, warmup=3, steps=20, workload="rects1080p"):
         ms, _, ev = _timed_run(s.sim, held, warmup, steps, stream, sink=sink, profile=False)
         a, b = s.rows["held"]
         per.append({"owned_rows": [s.rows["lo"], s.rows["hi"]], "held_rows": b - a,
-                    "ms_per_frame": round(ms / steps, 4), "events_held_rows": ev})
+                    "ms_per_frame": round(ms / steps, 4), "events_held_rows": ev,
+                    "kernel_ms_per_frame": kernel_ms(s.sim, held)})
         s.close()
         del held
     slowest = max(p["ms_per_frame"] for p in per)
     return {"workload": f"{workload}: {wl['desc']}; adaptive, precision form; {n_strips} strips of rows",
             "frames_timed": _frames_timed(warmup, steps, scene.cfg.frames),
             "whole_frame_ms_per_frame": round(ms_whole / steps, 4),
+            "whole_frame_kernel_ms_per_frame": kms_whole,
             "strips": per, "slowest_strip_ms_per_frame": slowest,
             "projected_speedup": round(ms_whole / steps / slowest, 3),
             "halo_rows_extra": round(sum(p["held_rows"] for p in per) / H - 1.0, 4),
