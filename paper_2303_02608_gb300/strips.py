@@ -4,12 +4,12 @@ One process per GPU simulates a horizontal strip of the image: rank k owns
 rows [lo_k, hi_k) (the rows split as evenly as possible) and keeps, in its own
 ring, r extra rows above and below (the halo) so that every window of an owned
 pixel is local.  Per frame the only exchange is the halo of the new frame:
-after each rank has converted its own rows into ring records, rank k sends
-its first r owned rows up to rank k-1 and its last r owned rows down to rank
-k+1, and receives the neighbours' rows into its halo; the older frames' halo
-rows are already in every ring from their own frames.  That is 2 r W records
-of the new frame per internal boundary (32 bytes each in the FP32 ring, 16 in
-the mixed one: about 0.86 MB per boundary at 1920 wide, r = 7, FP32).  The
+rank k sends its first r owned rows up to rank k-1 and its last r owned rows
+down to rank k+1, and receives the neighbours' rows into its halo; the older
+frames' halo rows are already in every ring from their own frames.  That is
+2 r W pixels of the new frame per internal boundary, as input planes (16 bytes
+per pixel in the precision form's FP16/BF16 storage formats, 40 in FP32) or
+as ring records (16 or 32 bytes).  The
 test, the regression and the emission are pixel-local, so an owned pixel's
 results depend on the held rows only; the owned rows' event lists, each in
 (row, column, repeat) order, concatenate in rank order into the whole image's
