@@ -713,6 +713,47 @@ def _strips(dev, n_strips=8, warmup=3, steps=20, workload="rects1080p"):
             "exchange": "not measured (one GPU): 2 r W records of the new frame per internal boundary"}
 
 
+def _kernel_mix(dev, n_frames=6, workload="rects1080p"):
+    """The driver of the pass-1 instruction-mix captures: frames 0..n_frames-1
+    of the workload through four simulators in turn (precision exhaustive,
+    FP32 exhaustive, precision adaptive, FP32 adaptive), each frame's events
+    drained before the next push.  Returns each simulator's (pixel,
+    neighbour) count per frame, the unit the captured instruction counts are
+    divided by."""
+    import torch
+    import paper_2303_02608_gb300 as lib
+    from paper_2303_02608_gb300 import ESIM_AD_ADAPTIVE, ESIM_AD_EXHAUSTIVE, SimConfig, Simulator
+    from scenes import Scene
+    wl = WORKLOADS[workload]
+    scene = Scene(rank_scene(wl["scene"], 0))
+    frames = _gen_frames(scene, n_frames, dev)
+    sframes = _storage_frames(frames)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    W, H = scene.cfg.width, scene.cfg.height
+    out = {"workload": f"{workload}: {wl['desc']}; frames 0-{n_frames - 1}"}
+    for name, mode, mixed, fr in (("mixed_exhaustive", ESIM_AD_EXHAUSTIVE, True, sframes),
+                                  ("fp32_exhaustive", ESIM_AD_EXHAUSTIVE, False, frames),
+                                  ("mixed_adaptive", ESIM_AD_ADAPTIVE, True, sframes),
+                                  ("fp32_adaptive", ESIM_AD_ADAPTIVE, False, frames)):
+        extra = dict(radiance_fmt=lib.ESIM_AD_LOGLUMA_F16, feature_fmt=lib.ESIM_AD_FEAT_BF16,
+                     precision=lib.ESIM_AD_MIXED, feature_scale=FSCALE) if mixed else {}
+        sim = Simulator(SimConfig(width=W, height=H, radius=wl["r"], frames=wl["T"], contrast=wl["C"],
+                                  mode=mode, rgb=wl["rgb"], event_capacity=1 << 22, **extra), stream)
+        sim.profile(True)
+        last, per = 0, []
+        for f in fr:
+            sim.push(f)
+            sim.events()
+            p = sim.profile()
+            per.append(p["neighbours"] - last)
+            last = p["neighbours"]
+        sim.close()
+        torch.cuda.synchronize()
+        out[name] = {"neighbours_per_frame": per}
+    return out
+
+
 def _events_to_counts(sink, n, counts):
     """Accumulate n 12-byte event records (frame, x | y << 16, polarity) from
     the device buffer `sink` into the signed count map counts [F][H][W]."""
@@ -1284,7 +1325,8 @@ def main():
     ap.add_argument("--no-render", action="store_true")
     ap.add_argument("--no-paper-density", action="store_true")
     ap.add_argument("--no-second-order", action="store_true")
-    ap.add_argument("--form", choices=["second-order", "differentiation", "batching", "strips"], default=None,
+    ap.add_argument("--form", choices=["second-order", "differentiation", "batching", "strips", "kernel-mix"],
+                    default=None,
                     help="run only that form's measurement and print its JSON object")
     ap.add_argument("--strips", type=int, default=8, help="with --form strips: the number of strips")
     ap.add_argument("--batch-sequences", type=int, default=48,
@@ -1306,6 +1348,8 @@ def main():
             out = _differentiation(dev, _fp32_peak(dev))
         elif args.form == "strips":
             out = _strips(dev, n_strips=args.strips, warmup=args.warmup)
+        elif args.form == "kernel-mix":
+            out = _kernel_mix(dev)
         else:
             out = _batching(dev, _fp32_peak(dev), n_seq=args.batch_sequences)
         print(json.dumps(out), flush=True)
