@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY: the independent reference the CUDA path is checked
 against.  Only the tests, the smoke check and the benchmark's CPU-baseline leg
 use it; the library never does.  The arithmetic lives in ``esim_oracle.c``
 (plain C, double precision, OpenMP over pixels); this module compiles it with
-gcc and marshals numpy arrays through ctypes.
+gcc and marshals numpy arrays through ctypes.  ESIM_ORACLE_LIB, when set,
+names another build of esim_oracle.c to load instead (the mutation tests load
+deliberately broken copies this way, to show that the pins catch them).
 """
 from __future__ import annotations
 
@@ -51,7 +53,7 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(os.environ.get("ESIM_ORACLE_LIB") or build())
         P = ctypes.c_void_p
         lib.or_create.restype = P
         lib.or_create.argtypes = [ctypes.POINTER(_Cfg)]

@@ -118,6 +118,44 @@ def test_linear_field_reproduced_exactly():
         np.testing.assert_allclose(theta[3:], g[2:], atol=5e-5)
 
 
+def test_model_replaced_at_events_and_kept_otherwise():
+    """Fig. 1: the model (beta, x^c) is kept from a pixel's last event.  With
+    feature-linear fields (reproduced exactly), frame 1 raises every pixel's
+    alpha by more than C: each pixel emits, and its model becomes frame 1's
+    fit (beta = g1, x^c = the frame-1 features).  Frame 2 changes one slope
+    and one feature slightly (|Delta L| < C): no event, and the model stays
+    frame 1's although frame 2 was regressed too (exhaustive mode)."""
+    rng = np.random.default_rng(11)
+    r, H, W, C = 3, 8, 9, 0.2
+    o = Oracle(OracleConfig(W, H, radius=r, frames=1, channels=0, mode=EXHAUSTIVE, contrast=C, ridge=1e-12))
+    g0 = rng.uniform(-0.05, 0.05, 7)
+    g1 = rng.uniform(-0.05, 0.05, 7)
+    g2 = g1 - 0.001 * np.eye(7)[3]                       # depth slope moved
+    n0, a0, d0 = _random_features(rng, H, W)
+    n1, a1, d1 = _random_features(rng, H, W)
+    F0, F1 = _feat_stack(n0, a0, d0), _feat_stack(n1, a1, d1)
+    a2 = a1.copy()
+    a2[0] += 0.01                                        # albedo red moved
+    F2 = _feat_stack(n1, a2, d1)
+    o.push(frame(0.1 + np.tensordot(g0, F0, 1), n0, a0, d0))
+    alpha0 = o.outputs()["alpha"]
+    o.push(frame(1.1 + np.tensordot(g1, F1, 1), n1, a1, d1))
+    out1 = o.outputs()
+    assert np.all(out1["nev"] >= 1)
+    st = o.state()
+    np.testing.assert_allclose(st["beta"][:, :2], 0.0, atol=5e-5)
+    np.testing.assert_allclose(st["beta"][:, 2:], np.tile(g1, (H * W, 1)), atol=5e-5)
+    np.testing.assert_array_equal(st["xc"], F1.reshape(7, -1).T)
+    np.testing.assert_allclose(st["l_last"], (alpha0 + out1["nev"] * C).ravel(), atol=1e-12)
+    o.push(frame(1.1 + np.tensordot(g2, F2, 1), n1, a2, d1))
+    out2 = o.outputs()
+    assert np.all(out2["flag"] == 1) and np.all(out2["nev"] == 0)
+    st2 = o.state()
+    np.testing.assert_array_equal(st2["beta"], st["beta"])
+    np.testing.assert_array_equal(st2["xc"], st["xc"])
+    np.testing.assert_array_equal(st2["l_last"], st["l_last"])
+
+
 def test_constant_and_shift():
     """Constant y gives alpha = const, beta = 0 for any ridge; adding k to y
     shifts alpha by k and leaves beta (ridge acts on beta only)."""
