@@ -107,3 +107,116 @@ def test_pins_catch_the_mutant(tmp_path, source, what, old, new):
     assert source.count(old) == 1, f"mutation site not unique or missing: {what}"
     rc, tail = _pins(_build(tmp_path, source.replace(old, new), "mutant"))
     assert rc != 0, f"the pins did not catch: {what}"
+
+
+# ---------------------------------------------------------------- numpy oracles
+# The second-order and evaluation oracles are Python modules: a mutated copy
+# replaces the module in a child pytest run (a plugin loads it as
+# oracle.<name> before the pins are collected).
+
+PY_MUTANTS = {
+    "wlr2": ("test_wlr2_pins.py", [
+        ("squares d_a^2 left out of the quadratic terms",
+         "PAIRS = [(a, b) for a in range(ND) for b in range(a, ND)]",
+         "PAIRS = [(a, b) for a in range(ND) for b in range(a + 1, ND)]"),
+        ("linear terms left out of the design row",
+         "np.ones(d.shape[:-1] + (1,)), d, quad", "np.ones(d.shape[:-1] + (1,)), 0 * d, quad"),
+        ("Gaussian exponent without the 1/2 (Eq. 5)",
+         "w = np.exp(-0.5 * np.sum((d / hb) ** 2, axis=-1)) * valid",
+         "w = np.exp(-np.sum((d / hb) ** 2, axis=-1)) * valid"),
+        ("clipped neighbours not masked out",
+         "w = np.exp(-0.5 * np.sum((d / hb) ** 2, axis=-1)) * valid",
+         "w = np.exp(-0.5 * np.sum((d / hb) ** 2, axis=-1))"),
+        ("temporal window one frame too long",
+         "taus = np.arange(t - frames + 1, t + 1)", "taus = np.arange(t - frames, t + 1)"),
+        ("coordinate offset not divided by r",
+         "d[..., 0] = (qx - cx[:, None]) / radius", "d[..., 0] = (qx - cx[:, None])"),
+        ("dy regressor built from the x offset",
+         "d[..., 1] = (qy - cy[:, None]) / radius", "d[..., 1] = (qx - cx[:, None]) / radius"),
+        ("ridge not scaled by the weight sum W",
+         "np.sqrt(ridge * W)[:, None]", "np.sqrt(ridge)"),
+        ("ridge on the intercept instead of the last coefficient",
+         "ridge_rows[:, np.arange(NZ - 1), np.arange(1, NZ)]",
+         "ridge_rows[:, np.arange(NZ - 1), np.arange(0, NZ - 1)]"),
+        ("luminance weights on the wrong channels",
+         "LUMA = np.array([0.2126, 0.7152, 0.0722])", "LUMA = np.array([0.2126, 0.0722, 0.7152])"),
+        ("log epsilon dropped",
+         "return np.log(Y + log_eps)", "return np.log(Y)"),
+        ("feature bandwidths ignored",
+         "hb = np.array([h, h] + [h * float(b) for b in bandwidth])", "hb = np.array([h, h] + [h for b in bandwidth])"),
+        ("back substitution against the wrong column",
+         "R[:NZ, :NZ], R[:NZ, NZ])", "R[:NZ, :NZ], R[:NZ, NZ - 1])"),
+        ("listed centres read as (t, x, y)",
+         "cen[k, 2], cen[k, 1], radius, frames)", "cen[k, 1], cen[k, 2], radius, frames)"),
+    ]),
+    "quality": ("test_quality_pins.py", [
+        ("events matched against the opposite polarity",
+         "r, _ = event_points(ref_counts, p)", "r, _ = event_points(ref_counts, -p)"),
+        ("time axis not normalised by F",
+         "pts = np.stack([x / W, y / H, t / F], axis=1)", "pts = np.stack([x / W, y / H, t], axis=1)"),
+        ("x and y normalised by the wrong sides",
+         "pts = np.stack([x / W, y / H, t / F], axis=1)", "pts = np.stack([x / H, y / W, t / F], axis=1)"),
+        ("ESIM crossings rounded instead of floored",
+         "n = np.floor(np.abs(dl) / C).astype(np.int64)", "n = np.round(np.abs(dl) / C).astype(np.int64)"),
+        ("ESIM reference reset to the frame instead of moved by p n C",
+         "return counts, l_last + counts * C", "return counts, y.copy()"),
+        ("event multiplicities ignored",
+         "return pts, np.abs(counts[sel]).astype(np.int64)", "return pts, np.ones(len(pts), np.int64)"),
+        ("F-score without the factor 2",
+         "Fs.append(2 * p * r / (p + r) if p + r > 0 else 0.0)", "Fs.append(p * r / (p + r) if p + r > 0 else 0.0)"),
+        ("chamfer distance not squared",
+         "cd = (float((wg * dg ** 2).sum()) / ng", "cd = (float((wg * dg).sum()) / ng"),
+        ("recall normalised by the generated count",
+         "r = float(wr[dr < tau].sum()) / nr if nr else 0.0", "r = float(wr[dr < tau].sum()) / ng if ng else 0.0"),
+        ("Rec.709 weights on the wrong channels",
+         "REC709 = (0.2126, 0.7152, 0.0722)", "REC709 = (0.7152, 0.2126, 0.0722)"),
+    ]),
+}
+
+_PLUGIN = '''import importlib.util, os, sys
+
+
+def pytest_configure(config):
+    import oracle
+    name = os.environ["ESIM_MUTANT_MODULE"]
+    spec = importlib.util.spec_from_file_location(name, os.environ["ESIM_MUTANT_FILE"])
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[name] = mod
+    spec.loader.exec_module(mod)
+    setattr(oracle, name.rsplit(".", 1)[1], mod)
+'''
+
+
+def _py_pins(tmp, module, pins, source):
+    (tmp / "esim_mutant_plugin.py").write_text(_PLUGIN)
+    path = tmp / f"{module}_copy.py"
+    path.write_text(source)
+    env = dict(os.environ, ESIM_MUTANT_MODULE=f"oracle.{module}", ESIM_MUTANT_FILE=str(path),
+               PYTHONPATH=os.pathsep.join([str(tmp)] + [p for p in [os.environ.get("PYTHONPATH")] if p]),
+               OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-p", "esim_mutant_plugin",
+                        os.path.join(ROOT, "tests", pins), "-x", "-q", "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, (r.stdout + r.stderr).strip().splitlines()[-1:]
+
+
+def _py_source(module):
+    with open(os.path.join(ORACLE, f"{module}.py")) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("module", sorted(PY_MUTANTS))
+def test_unmutated_python_oracle_copy_passes_the_pins(tmp_path, module):
+    rc, tail = _py_pins(tmp_path, module, PY_MUTANTS[module][0], _py_source(module))
+    assert rc == 0, tail
+
+
+_PY_CASES = [(m, w, o, n) for m in sorted(PY_MUTANTS) for (w, o, n) in PY_MUTANTS[m][1]]
+
+
+@pytest.mark.parametrize("module,what,old,new", _PY_CASES, ids=[f"{c[0]}: {c[1]}" for c in _PY_CASES])
+def test_python_oracle_pins_catch_the_mutant(tmp_path, module, what, old, new):
+    src = _py_source(module)
+    assert src.count(old) == 1, f"mutation site not unique or missing: {what}"
+    rc, tail = _py_pins(tmp_path, module, PY_MUTANTS[module][0], src.replace(old, new))
+    assert rc != 0, f"the pins did not catch: {what}"

@@ -41,6 +41,21 @@ def test_identical_sets_are_perfect():
     c = rng.integers(-2, 3, size=(4, 5, 6)) * (rng.random((4, 5, 6)) < 0.3)
     q = Q.quality(c, c, [1e-9, 0.1])
     assert q["precision"] == [1.0, 1.0] and q["recall"] == [1.0, 1.0] and q["chamfer"] == 0.0
+    assert q["fscore"] == [1.0, 1.0]
+
+
+def test_fscore_is_the_harmonic_mean():
+    """F = 2 P R / (P + R): three generated ON events of which one lies on the
+    only reference event gives P = 1/3, R = 1, F = 1/2."""
+    F, H, W = 6, 8, 8
+    gen = np.zeros((F, H, W), np.int64)
+    ref = np.zeros((F, H, W), np.int64)
+    gen[1, 2, 2] = 1
+    gen[4, 7, 7] = 2          # far from the reference event, counted twice
+    ref[1, 2, 2] = 1
+    q = Q.quality(gen, ref, [1e-6])
+    assert q["precision"] == [pytest.approx(1 / 3)] and q["recall"] == [1.0]
+    assert q["fscore"] == [pytest.approx(0.5)]
 
 
 def test_polarity_is_respected_and_distances_are_normalised():

@@ -84,11 +84,18 @@ def test_quadratic_field_is_reproduced():
     alpha = O.wlr2(rad, feat, radius=r, frames=T, ridge=1e-13, log_eps=eps)
     n_side = lambda c, n: min(n, c + r + 1) - max(0, c - r)
     checked = 0
+    cen = []
     for t, cy, cx in itertools.product(range(1, F), range(H), range(W)):
         if n_side(cy, H) * n_side(cx, W) * T >= 80:
             assert alpha[t, cy, cx] == pytest.approx(y[t, cy, cx], abs=1e-7)
             checked += 1
+            if cx != cy:
+                cen.append((t, cy, cx))
     assert checked > 50
+    # the listed-centres path, (t, y, x) per centre, reproduces the field too
+    cen = cen[::3]
+    a_c = O.wlr2(rad, feat, radius=r, frames=T, ridge=1e-13, log_eps=eps, centres=cen)
+    np.testing.assert_allclose(a_c, [y[t, cy, cx] for t, cy, cx in cen], rtol=0, atol=1e-7)
 
 
 def test_infinite_ridge_gives_the_weighted_mean():
@@ -174,16 +181,22 @@ def test_agrees_with_the_first_order_oracle_where_both_are_exact():
     b = [0.7, 1.3, 0.9, 1.6, 0.8, 1.2, 1.0]
 
     def first_order(rad, ridge):
-        o = Oracle(OracleConfig(W, H, radius=r, frames=T, channels=1, mode=EXHAUSTIVE, bandwidth=b, ridge=ridge))
+        o = Oracle(OracleConfig(W, H, radius=r, frames=T, channels=rad.shape[1], mode=EXHAUSTIVE, bandwidth=b,
+                                ridge=ridge))
         out = []
         for t in range(F):
-            o.push({"radiance": rad[t, 0].astype(np.float32), "normal": feat[t, 0:3].astype(np.float32),
+            o.push({"radiance": rad[t].astype(np.float32), "normal": feat[t, 0:3].astype(np.float32),
                     "depth": feat[t, 3].astype(np.float32), "albedo": feat[t, 4:7].astype(np.float32)})
             out.append(o.outputs()["alpha"])
         return np.stack(out)
 
     a1 = first_order(rad_w, 1e14)
     a2 = O.wlr2(rad_w, feat, bandwidth=b, radius=r, frames=T, ridge=1e14)
+    np.testing.assert_allclose(a2, a1, rtol=0, atol=1e-9)
+    # RGB radiance: each oracle forms its own Rec.709 luminance
+    rad_rgb = rng.uniform(0.2, 2.0, size=(F, 3, H, W)).astype(np.float32).astype(np.float64)
+    a1 = first_order(rad_rgb, 1e14)
+    a2 = O.wlr2(rad_rgb, feat, bandwidth=b, radius=r, frames=T, ridge=1e14)
     np.testing.assert_allclose(a2, a1, rtol=0, atol=1e-9)
     # a field linear in the feature: both reproduce it (to the float32 rounding of the radiance)
     yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
