@@ -110,11 +110,31 @@ def test_pins_catch_the_mutant(tmp_path, source, what, old, new):
 
 
 # ---------------------------------------------------------------- numpy oracles
-# The second-order and evaluation oracles are Python modules: a mutated copy
-# replaces the module in a child pytest run (a plugin loads it as
+# The second-order, evaluation and renderer oracles are Python modules: a
+# mutated copy replaces the module in a child pytest run (a plugin loads it as
 # oracle.<name> before the pins are collected).
 
 PY_MUTANTS = {
+    "render": ("test_render_pins.py", [
+        ("geometry term without 1/pi",
+         "g = ((cs * cl) * area) / (f32(3.14159274) * d2)", "g = ((cs * cl) * area) / d2"),
+        ("geometry term without the light's cosine",
+         "g = ((cs * cl) * area) / (f32(3.14159274) * d2)", "g = (cs * area) / (f32(3.14159274) * d2)"),
+        ("light sampled on the floor plane",
+         "np.full(n_pix, f32(sc.box[1]), f32)", "np.full(n_pix, f32(-sc.box[1]), f32)"),
+        ("image rows flipped",
+         "syp = (f32(1.0) - ((py + _unit(jit[1])) / f32(H)) * f32(2.0)) * tany",
+         "syp = (((py + _unit(jit[1])) / f32(H)) * f32(2.0) - f32(1.0)) * tany"),
+        ("variance of the mean divided by n^2 instead of n (n - 1)",
+         "/ (nf * (nf - f32(1.0)))", "/ (nf * nf)"),
+        ("path throughput not attenuated by the albedo",
+         "thr = [thr[c] * a[c] for c in range(3)]", "thr = [thr[c] for c in range(3)]"),
+        ("floor and ceiling normals swapped",
+         "nwy = [0, 0, 1, -1, 0]", "nwy = [0, 0, -1, 1, 0]"),
+        ("directly seen emitter at half radiance",
+         "L[c] = np.where(alive & light, L[c] + Le[c], L[c])",
+         "L[c] = np.where(alive & light, L[c] + f32(0.5) * Le[c], L[c])"),
+    ]),
     "wlr2": ("test_wlr2_pins.py", [
         ("squares d_a^2 left out of the quadratic terms",
          "PAIRS = [(a, b) for a in range(ND) for b in range(a, ND)]",

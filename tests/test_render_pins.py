@@ -72,3 +72,50 @@ def test_second_interaction_only_adds_light():
     sc2 = cornell(width=40, height=30, spp=2, max_bounces=2)
     r1, r2 = R.render(sc1, 2)["radiance"], R.render(sc2, 2)["radiance"]
     assert np.all(r2 >= r1) and (r2 > r1).mean() > 0.5
+
+
+def _scaled_albedos(sc, k):
+    import dataclasses
+    return dataclasses.replace(
+        sc, wall_albedo=tuple(tuple(k * c for c in a) for a in sc.wall_albedo),
+        back_albedo2=tuple(k * c for c in sc.back_albedo2),
+        spheres=[Sphere(s.center, s.velocity, s.radius, tuple(k * c for c in s.albedo)) for s in sc.spheres])
+
+
+def test_second_interaction_is_quadratic_in_albedo():
+    """Halving every albedo (same geometry, same random numbers) halves the
+    light that reaches the camera after one surface interaction and quarters
+    what arrives after two: the path throughput carries the first surface's
+    albedo into the second interaction's direct light."""
+    import dataclasses
+    sc = cornell(width=40, height=30, spp=2, max_bounces=2)
+
+    def parts(s):
+        one = R.render(dataclasses.replace(s, max_bounces=1), 2)["radiance"].astype(np.float64)
+        two = R.render(s, 2)["radiance"].astype(np.float64)
+        return one, two - one
+
+    d_full, x_full = parts(sc)
+    d_half, x_half = parts(_scaled_albedos(sc, 0.5))
+    m = x_full > 1e-3 * x_full.max()
+    assert m.mean() > 0.3
+    np.testing.assert_allclose(4 * x_half[m], x_full[m], rtol=1e-4)
+    seen = d_full == d_half             # the emitter seen directly does not scale
+    lit = ~seen & (d_full > 1e-3 * d_full.max())
+    assert lit.mean() > 0.3
+    np.testing.assert_allclose(2 * d_half[lit], d_full[lit], rtol=1e-5)
+
+
+def test_variance_of_two_samples():
+    """The variance output is the unbiased variance of the pixel mean.  With
+    two samples it is (Y0 - Y1)^2 / 4 = (Y0 - mean)^2, where Y0 is the
+    one-sample render (sample 0 draws the same random numbers in both) and
+    mean the two-sample render, Y the Rec.709 luminance."""
+    r1 = R.render(cornell(width=40, height=30, spp=1), 4)
+    r2 = R.render(cornell(width=40, height=30, spp=2), 4)
+    lum = lambda r: 0.2126 * r[0].astype(np.float64) + 0.7152 * r[1] + 0.0722 * r[2]
+    y0, mean = lum(r1["radiance"]), lum(r2["radiance"])
+    expect = (y0 - mean) ** 2
+    assert (expect > 1e-6 * mean.max() ** 2).mean() > 0.3
+    tol = 2e-6 * (mean ** 2 + expect) + 1e-12
+    assert np.all(np.abs(r2["variance"] - expect) <= tol)
