@@ -110,9 +110,10 @@ def test_pins_catch_the_mutant(tmp_path, source, what, old, new):
 
 
 # ---------------------------------------------------------------- numpy oracles
-# The second-order, evaluation and renderer oracles are Python modules: a
-# mutated copy replaces the module in a child pytest run (a plugin loads it as
-# oracle.<name> before the pins are collected).
+# The second-order, evaluation and renderer oracles and the differentiation
+# form's FP64 reference are Python modules: a mutated copy replaces the module
+# in a child pytest run (a plugin loads it under the module's name before the
+# pins are collected).
 
 PY_MUTANTS = {
     "render": ("test_render_pins.py", [
@@ -134,6 +135,26 @@ PY_MUTANTS = {
         ("directly seen emitter at half radiance",
          "L[c] = np.where(alive & light, L[c] + Le[c], L[c])",
          "L[c] = np.where(alive & light, L[c] + f32(0.5) * Le[c], L[c])"),
+    ]),
+    "wlr_reference": ("test_adjoint_pins.py", [
+        ("sqrt(w) with the Gaussian's full exponent",
+         "sw = torch.exp(-0.25 * (((d / hb.view(9, 1, 1)) ** 2).sum(0))) * valid[sl]",
+         "sw = torch.exp(-0.5 * (((d / hb.view(9, 1, 1)) ** 2).sum(0))) * valid[sl]"),
+        ("coordinate offset not divided by r",
+         "d[0] = ox / r", "d[0] = ox"),
+        ("normal-equation ridge not scaled by W",
+         "+ ridge * wv.sum(-1)[..., None, None] * P", "+ ridge * P"),
+        ("least-squares ridge rows not scaled by W",
+         "torch.sqrt(ridge * Wsum)[..., None, None]", "torch.sqrt(ridge + 0 * Wsum)[..., None, None]"),
+        ("temporal window one frame too long",
+         "for tau in range(max(0, t - T + 1), t + 1):", "for tau in range(max(0, t - T), t + 1):"),
+        ("clipped offsets not masked",
+         "** 2).sum(0))) * valid[sl]", "** 2).sum(0)))"),
+        ("loss summed instead of averaged",
+         "return ((alpha - log_luminance(clean, eps)) ** 2).mean()",
+         "return ((alpha - log_luminance(clean, eps)) ** 2).sum()"),
+        ("Rec.709 weights on the wrong channels",
+         "REC709 = (0.2126, 0.7152, 0.0722)", "REC709 = (0.0722, 0.7152, 0.2126)"),
     ]),
     "wlr2": ("test_wlr2_pins.py", [
         ("squares d_a^2 left out of the quadratic terms",
@@ -193,25 +214,32 @@ PY_MUTANTS = {
     ]),
 }
 
-_PLUGIN = '''import importlib.util, os, sys
+_PLUGIN = '''import importlib, importlib.util, os, sys
 
 
 def pytest_configure(config):
-    import oracle
     name = os.environ["ESIM_MUTANT_MODULE"]
+    pkg = importlib.import_module(name.rsplit(".", 1)[0]) if "." in name else None
     spec = importlib.util.spec_from_file_location(name, os.environ["ESIM_MUTANT_FILE"])
     mod = importlib.util.module_from_spec(spec)
     sys.modules[name] = mod
     spec.loader.exec_module(mod)
-    setattr(oracle, name.rsplit(".", 1)[1], mod)
+    if pkg is not None:
+        setattr(pkg, name.rsplit(".", 1)[1], mod)
 '''
+
+
+# the differentiation form's FP64 autograd reference is a test module, not
+# part of oracle/
+TOP_LEVEL = {"wlr_reference": os.path.join(ROOT, "tests", "wlr_reference.py")}
 
 
 def _py_pins(tmp, module, pins, source):
     (tmp / "esim_mutant_plugin.py").write_text(_PLUGIN)
     path = tmp / f"{module}_copy.py"
     path.write_text(source)
-    env = dict(os.environ, ESIM_MUTANT_MODULE=f"oracle.{module}", ESIM_MUTANT_FILE=str(path),
+    name = module if module in TOP_LEVEL else f"oracle.{module}"
+    env = dict(os.environ, ESIM_MUTANT_MODULE=name, ESIM_MUTANT_FILE=str(path),
                PYTHONPATH=os.pathsep.join([str(tmp)] + [p for p in [os.environ.get("PYTHONPATH")] if p]),
                OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-p", "esim_mutant_plugin",
@@ -221,7 +249,7 @@ def _py_pins(tmp, module, pins, source):
 
 
 def _py_source(module):
-    with open(os.path.join(ORACLE, f"{module}.py")) as f:
+    with open(TOP_LEVEL.get(module, os.path.join(ORACLE, f"{module}.py"))) as f:
         return f.read()
 
 
