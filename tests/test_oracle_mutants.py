@@ -91,22 +91,6 @@ def _pins(lib):
     return r.returncode, (r.stdout + r.stderr).strip().splitlines()[-1:]
 
 
-@pytest.fixture(scope="module")
-def source():
-    with open(os.path.join(ORACLE, "esim_oracle.c")) as f:
-        return f.read()
-
-
-def test_unmutated_copy_passes_the_pins(tmp_path, source):
-    rc, tail = _pins(_build(tmp_path, source, "original"))
-    assert rc == 0, tail
-
-
-@pytest.mark.parametrize("what,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_the_mutant(tmp_path, source, what, old, new):
-    assert source.count(old) == 1, f"mutation site not unique or missing: {what}"
-    rc, tail = _pins(_build(tmp_path, source.replace(old, new), "mutant"))
-    assert rc != 0, f"the pins did not catch: {what}"
 
 
 # ---------------------------------------------------------------- numpy oracles
@@ -248,14 +232,68 @@ def _py_pins(tmp, module, pins, source):
     return r.returncode, (r.stdout + r.stderr).strip().splitlines()[-1:]
 
 
-def _py_source(module):
-    with open(TOP_LEVEL.get(module, os.path.join(ORACLE, f"{module}.py"))) as f:
+# ---------------------------------------------------------------- the runs
+# Every case (each unmutated copy and each mutant) is one child process.  Run
+# serially (no xdist worker), the module's first test starts them all, up to
+# eight at a time, and each test then reads its own outcome.
+
+def _source(module):
+    path = os.path.join(ORACLE, "esim_oracle.c") if module == "c" else \
+        TOP_LEVEL.get(module, os.path.join(ORACLE, f"{module}.py"))
+    with open(path) as f:
         return f.read()
 
 
+def _cases():
+    out = {("c", None): ("c", _source("c"))}
+    for what, old, new in MUTANTS:
+        out[("c", what)] = ("c", _source("c").replace(old, new))
+    for m, (_, muts) in PY_MUTANTS.items():
+        out[(m, None)] = (m, _source(m))
+        for what, old, new in muts:
+            out[(m, what)] = (m, _source(m).replace(old, new))
+    return out
+
+
+def _run(tmp, module, text):
+    if module == "c":
+        return _pins(_build(tmp, text, "copy"))
+    return _py_pins(tmp, module, PY_MUTANTS[module][0], text)
+
+
+@pytest.fixture(scope="module")
+def outcome(tmp_path_factory):
+    cases = _cases()
+    done = {}
+    if not os.environ.get("PYTEST_XDIST_WORKER"):
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
+            futs = {k: ex.submit(_run, tmp_path_factory.mktemp("case"), *v) for k, v in cases.items()}
+            done = {k: f.result() for k, f in futs.items()}
+
+    def get(module, what=None):
+        key = (module, what)
+        if key not in done:
+            done[key] = _run(tmp_path_factory.mktemp("case"), *cases[key])
+        return done[key]
+    return get
+
+
+def test_unmutated_copy_passes_the_pins(outcome):
+    rc, tail = outcome("c")
+    assert rc == 0, tail
+
+
+@pytest.mark.parametrize("what,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_the_mutant(outcome, what, old, new):
+    assert _source("c").count(old) == 1, f"mutation site not unique or missing: {what}"
+    rc, tail = outcome("c", what)
+    assert rc != 0, f"the pins did not catch: {what}"
+
+
 @pytest.mark.parametrize("module", sorted(PY_MUTANTS))
-def test_unmutated_python_oracle_copy_passes_the_pins(tmp_path, module):
-    rc, tail = _py_pins(tmp_path, module, PY_MUTANTS[module][0], _py_source(module))
+def test_unmutated_python_oracle_copy_passes_the_pins(outcome, module):
+    rc, tail = outcome(module)
     assert rc == 0, tail
 
 
@@ -263,8 +301,7 @@ _PY_CASES = [(m, w, o, n) for m in sorted(PY_MUTANTS) for (w, o, n) in PY_MUTANT
 
 
 @pytest.mark.parametrize("module,what,old,new", _PY_CASES, ids=[f"{c[0]}: {c[1]}" for c in _PY_CASES])
-def test_python_oracle_pins_catch_the_mutant(tmp_path, module, what, old, new):
-    src = _py_source(module)
-    assert src.count(old) == 1, f"mutation site not unique or missing: {what}"
-    rc, tail = _py_pins(tmp_path, module, PY_MUTANTS[module][0], src.replace(old, new))
+def test_python_oracle_pins_catch_the_mutant(outcome, module, what, old, new):
+    assert _source(module).count(old) == 1, f"mutation site not unique or missing: {what}"
+    rc, tail = outcome(module, what)
     assert rc != 0, f"the pins did not catch: {what}"
