@@ -66,6 +66,23 @@ def _sincos_turns(u):
     return c.astype(f32), s.astype(f32)
 
 
+def _cosine_direction(n, uz, uphi):
+    """Cosine-weighted direction about the unit normal n (three float32 arrays)
+    from two uniform numbers: sin^2 of the polar angle uz, azimuth 2 pi uphi,
+    in the orthonormal basis of Duff et al. (2017)."""
+    cph, sph = _sincos_turns(uphi)
+    rr = np.sqrt(uz)
+    lz = np.sqrt(np.maximum(f32(1.0) - uz, f32(0.0)))
+    lx, ly = rr * cph, rr * sph
+    sg = np.where(n[2] >= 0, f32(1.0), f32(-1.0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        aa = f32(-1.0) / (sg + n[2])
+    bb = (n[0] * n[1]) * aa
+    t1 = [f32(1.0) + (sg * (n[0] * n[0])) * aa, sg * bb, -(sg * n[0])]
+    t2 = [bb, sg + (n[1] * n[1]) * aa, -n[1]]
+    return [(t1[i] * lx + t2[i] * ly) + n[i] * lz for i in range(3)]
+
+
 def _hit_spheres(sc, ctr, o, d, eps):
     t_best = np.full(o[0].shape, INF, f32)
     kind = np.full(o[0].shape, -1, np.int64)
@@ -202,18 +219,7 @@ def render(sc, frame: int) -> dict:
                 L[c] = np.where(lit, L[c] + ((thr[c] * a[c]) * Le[c]) * g, L[c])
             if b + 1 >= sc.max_bounces:
                 break
-            cph, sph = _sincos_turns(_unit(r[3]))
-            uz = _unit(r[2])
-            rr = np.sqrt(uz)
-            lz = np.sqrt(np.maximum(f32(1.0) - uz, f32(0.0)))
-            lx, ly = rr * cph, rr * sph
-            sg = np.where(n[2] >= 0, f32(1.0), f32(-1.0))
-            with np.errstate(divide="ignore", invalid="ignore"):
-                aa = f32(-1.0) / (sg + n[2])
-            bb = (n[0] * n[1]) * aa
-            t1 = [f32(1.0) + (sg * (n[0] * n[0])) * aa, sg * bb, -(sg * n[0])]
-            t2 = [bb, sg + (n[1] * n[1]) * aa, -n[1]]
-            d = [(t1[i] * lx + t2[i] * ly) + n[i] * lz for i in range(3)]
+            d = _cosine_direction(n, _unit(r[2]), _unit(r[3]))
             o = x
             thr = [thr[c] * a[c] for c in range(3)]
             if not alive.any():

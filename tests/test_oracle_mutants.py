@@ -119,6 +119,14 @@ PY_MUTANTS = {
         ("directly seen emitter at half radiance",
          "L[c] = np.where(alive & light, L[c] + Le[c], L[c])",
          "L[c] = np.where(alive & light, L[c] + f32(0.5) * Le[c], L[c])"),
+        ("bounce radius uz instead of sqrt(uz)",
+         "rr = np.sqrt(uz)", "rr = uz"),
+        ("bounce directions uniform in solid angle instead of cosine-weighted",
+         "rr = np.sqrt(uz)\n    lz = np.sqrt(np.maximum(f32(1.0) - uz, f32(0.0)))",
+         "rr = np.sqrt(np.maximum(f32(1.0) - (f32(1.0) - uz) * (f32(1.0) - uz), f32(0.0)))\n"
+         "    lz = f32(1.0) - uz"),
+        ("tangent basis with the wrong sign",
+         "aa = f32(-1.0) / (sg + n[2])", "aa = f32(1.0) / (sg + n[2])"),
     ]),
     "wlr_reference": ("test_adjoint_pins.py", [
         ("sqrt(w) with the Gaussian's full exponent",

@@ -119,3 +119,28 @@ def test_variance_of_two_samples():
     assert (expect > 1e-6 * mean.max() ** 2).mean() > 0.3
     tol = 2e-6 * (mean ** 2 + expect) + 1e-12
     assert np.all(np.abs(r2["variance"] - expect) <= tol)
+
+
+def test_cosine_weighted_directions():
+    """The bounce directions are unit vectors in the normal's hemisphere with
+    the moments of the cosine-weighted density p = cos(theta) / pi:
+    E[cos theta] = 2/3, E[cos^2 theta] = 1/2, and no mean tangential drift,
+    for wall normals (both signs of n_z) and arbitrary sphere normals."""
+    rng = np.random.default_rng(5)
+    N = 1 << 18
+    uz = (rng.integers(0, 1 << 24, N) * 5.9604644775390625e-8).astype(np.float32)
+    up = (rng.integers(0, 1 << 24, N) * 5.9604644775390625e-8).astype(np.float32)
+    normals = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    v = rng.normal(size=(4, 3))
+    normals += [tuple(x / np.linalg.norm(x)) for x in v]
+    for nv in normals:
+        n = [np.full(N, np.float32(c), np.float32) for c in nv]
+        d = np.stack(R._cosine_direction(n, uz, up)).astype(np.float64)
+        assert np.abs(np.linalg.norm(d, axis=0) - 1).max() < 1e-5
+        c = np.asarray(nv, np.float64) @ d
+        assert c.min() > -1e-6
+        se = 1 / np.sqrt(N)
+        assert abs(c.mean() - 2 / 3) < 5 * se * np.sqrt(1 / 2 - 4 / 9)
+        assert abs((c ** 2).mean() - 1 / 2) < 5 * se * np.sqrt(1 / 3 - 1 / 4)
+        tang = d - np.outer(np.asarray(nv, np.float64), c)
+        assert np.abs(tang.mean(axis=1)).max() < 5 * se
